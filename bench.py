@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the far-field occ-FMM-K exchange build on GB300.
+
+Workload (default): the 150-carbon zig-zag alkane chain C150H302 with the
+synthetic s/p basis (C: 2s1p, H: 2s, 3 primitives, log-uniform exponents in
+[0.1, 50]), 1354 AOs, nocc = 601 Loewdin-orthonormalised random orbitals,
+octree to ~8 atoms per leaf (depth 6), lmax = 2, FP64 contractions.  One
+"step" = one occk_farfield_K call (steps a-e: C on the device -> K^ff, E^ff).
+
+Prints ONE JSON line on rank 0.  `value` = seconds per far-field K build for
+the whole job (lower is better); with N GPUs each rank builds its own replica
+(replicas only, weak scaling).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("far-field K_ri build time (s) & TFLOP/s at stated error vs FP64 oracle, "
+          "learned/mixed vs plain")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--ncarbon", type=int, default=150)
+    p.add_argument("--lmax", type=int, default=2)
+    p.add_argument("--prec", default="fp64")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-cols", type=int, default=2)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic FLOPs per stage (real form; the symmetric half of O^{ij} in a)
+# ---------------------------------------------------------------------------
+def stage_flops(tree_info, rowoff, nocc, L, depth, level_off, nent, nm2m, nl2l, nm2l):
+    nc = (L + 1) ** 2
+    tl = sum((2 * l + 1) * (l + 1) ** 2 for l in range(L + 1))
+    P = nocc * nocc
+    S = [rowoff[k + 1] - rowoff[k] for k in range(len(rowoff) - 1)]
+    return {
+        "a_half": 2.0 * nent * nocc * nc,
+        "a_full": sum(2.0 * s * nc * nocc * (nocc + 1) / 2 for s in S),
+        "b_m2m": 2.0 * tl * P * nm2m,
+        "c_m2l": 2.0 * nc * nc * P * nm2l,
+        "d_l2l": 2.0 * tl * P * nl2l,
+        "e_l2p": sum(2.0 * s * nc * nocc * nocc for s in S),
+        "reduce": 0.0,
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.p = None
+        self.dev = device_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, n in enumerate(names):
+                if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel)
+        if not rec:
+            return None
+        src = os.path.join(ROOT, "paper_1708_05353_gb300", "csrc", rec["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != rec["source_sha"]:
+            return None
+        return rec["bytes_per_launch"] * rec.get("scale_to_bench", 1.0)
+    except Exception:
+        return None
+
+
+def cpu_baseline(system, L, ncols):
+    """The FP64 oracle, as it stands, on a bounded sample: all of step a0 and
+    the AO->MO half transform, plus K for `ncols` occupied columns; the full
+    build time is extrapolated linearly in the number of columns."""
+    import numpy as np
+    from oracle import fmm
+    from oracle import tree as otree
+    t0 = time.perf_counter()
+    tr = otree.build_tree(system.basis, system.depth, system.target_atoms_per_leaf)
+    Op = fmm.pair_multipoles(system.basis, tr, L)
+    W = fmm.half_transform(system.basis, tr, Op, system.C, L)
+    t1 = time.perf_counter()
+    cols = list(range(ncols))
+    fmm.farfield(system, L=L, tree=tr, i_subset=cols)
+    t2 = time.perf_counter()
+    # farfield() repeats step a0 and the half transform; subtract them once
+    t_cols = max((t2 - t1) - (t1 - t0), 1e-3)
+    est = (t1 - t0) + t_cols * system.nocc / ncols
+    del W, Op
+    return {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle FP64 on {system.name} L={L}: tree + pair multipoles + half transform "
+                       f"({t1 - t0:.1f} s) and K for {ncols} of {system.nocc} columns "
+                       f"({t_cols:.1f} s), extrapolated linearly to all columns"),
+            "blas_threads": os.environ.get("OMP_NUM_THREADS", "default")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1708_05353_gb300 import inputs
+    system = inputs.alkane(args.ncarbon, lmax=args.lmax)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(system, args.lmax, args.cpu_cols)
+        if k >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": system.name, "nao": system.basis.nao,
+                                            "nocc": system.nocc, "lmax": args.lmax},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1708_05353_gb300 import inputs, occk
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    system = inputs.alkane(args.ncarbon, lmax=args.lmax)
+    L = args.lmax
+    ctx = occk.Context(local)
+    tree = occk.Tree(ctx, system.basis, depth=system.depth,
+                     target_atoms_per_leaf=system.target_atoms_per_leaf)
+    info = tree.info()
+    tree.pair_multipoles(L)
+    C = torch.tensor(system.C, dtype=torch.float64, device=dev)
+    Cf = occk.fortran(C)
+    K = occk.empty_fortran(system.basis.nao, system.nocc, torch.float64, dev)
+    Ex = torch.empty((), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        occk.farfield_K(ctx, tree, Cf, prec=args.prec, K=K, Ex=Ex)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, events around each
+    ctx.set_timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    stage_ms = {k: 0.0 for k in occk.STAGES}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+        for n, v in ctx.timings().items():
+            stage_ms[n] += v
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+    t_step = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
+    ms_max = float(t_step.item())
+
+    # ---- end-to-end: host C (pinned) -> device -> K, E back to host
+    Ch = torch.tensor(system.C.T.copy(), dtype=torch.float64).pin_memory()   # [nocc, nao] = column-major C
+    Kh = torch.empty((system.nocc, system.basis.nao), dtype=torch.float64).pin_memory()
+    Eh = torch.empty((), dtype=torch.float64).pin_memory()
+    Cd = torch.empty((system.nocc, system.basis.nao), dtype=torch.float64, device=dev)
+    e2e_ev = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Cd.copy_(Ch, non_blocking=True)
+        occk.farfield_K(ctx, tree, Cd.t(), prec=args.prec, K=K, Ex=Ex)
+        Kh.copy_(K.t(), non_blocking=True)
+        Eh.copy_(Ex, non_blocking=True)
+        b.record(stream)
+        if k >= args.warmup:
+            e2e_ev.append((a, b))
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / len(e2e_ev)
+    t_e2e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_max = float(t_e2e.item())
+
+    # ---- roofline of the dominant kernel
+    lo = tree.export("level_off")
+    D = info["depth"]
+    nm2m = int(lo[D + 1] - lo[3]) if D >= 3 else 0
+    flops = stage_flops(info, tree.export("leaf_rowoff"), system.nocc, L, D, lo, info["nentry"],
+                        nm2m, nm2m, info["nm2l"])
+    total_flops = sum(flops.values())
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    peak_prec = "fp64" if args.prec == "fp64" else "fp32"
+    peak = ctx.probe_fma_peak(peak_prec)
+    kernel_names = {"a_half": "k_half", "a_full": "k_full", "b_m2m": "k_translate(M2M)",
+                    "c_m2l": "k_translate(M2L)", "d_l2l": "k_translate(L2L)", "e_l2p": "k_l2p",
+                    "reduce": "k_reduce_K"}
+    achieved = flops[dom] / (stage_ms[dom] * 1e-3)
+    roof = {"bound": "alu", "kernel": kernel_names[dom], "stage": dom,
+            "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic_for(kernel_names[dom]),
+            "peak_source": f"measured {peak_prec.upper()} FMA rate (occk_probe_fma_peak, all SMs)",
+            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stage_tflops": {k: round(flops[k] / max(stage_ms[k], 1e-9) / 1e9, 4) for k in flops}}
+
+    nlaunch = 7 + 2 * max(D - 2, 0)
+    result = {
+        "metric": METRIC,
+        "value": ms_max * 1e-3 / world,
+        "unit": "s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else args.prec,
+        "data": "synthetic",
+        "config": {"workload": system.name, "nao": system.basis.nao, "nocc": system.nocc,
+                   "lmax": L, "depth": D, "nbox": info["nbox"], "nm2l": info["nm2l"],
+                   "precision": args.prec, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "tflops": total_flops / (ms_max * 1e-3) / 1e12,
+        "algorithmic_gflop_per_step": total_flops / 1e9,
+        "wall_s_timed_region": t_wall,
+        "e2e": {"value": e2e_max * 1e-3 / world, "unit": "s",
+                "h2d_bytes_per_step": int(system.basis.nao * system.nocc * 8),
+                "d2h_bytes_per_step": int(system.basis.nao * system.nocc * 8 + 8)},
+        "gpu_launches": nlaunch * args.steps,
+        "roofline": roof,
+        "clocks": clk,
+        "energy": float(Ex.item()),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(system, L, args.cpu_cols)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * occk.h -- C ABI of the far-field occupied-orbital FMM exchange (occ-FMM-K)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The library computes the far-field part of the occupied exchange block
+ *     K_ri = 2 sum_j (rj|ji)                          (paper, Eq. occex)
+ * for AO index r and occupied orbitals i, j, with the multipole machinery of
+ * Le & Shiozaki, "Occupied-orbital fast multipole method for efficient exact
+ * exchange evaluation" (arXiv:1708.05353), Sec. II:
+ *   (a) AO-pair multipoles transformed to occupied pairs   (Eq. motrans)
+ *   (b) occupied M2M up the box hierarchy                  (Eq. fmm1, per ij)
+ *   (c) occupied M2L over interaction lists                (Eq. fmmex / fmm2)
+ *   (d) occupied L2L down the hierarchy                    (Eq. fmm3, per ij)
+ *   (e) K^ff_ri = 2 sum_j sum_lm O^{rj,X}_lm Mcal^{ij}_lm(X) (Eq. kri; the factor
+ *       2 of Eq. occex is applied) and E^ff_x = -1/2 sum_ri C_ri K^ff_ri.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns occk_status: 0 on success, a negative code on
+ *     failure.  No C++ exception crosses the ABI.  The message of the last
+ *     failure on a context is available from occk_last_error().
+ *   - Units: bohr and hartree.  AO order is shell order; a p shell contributes
+ *     Cartesian (x, y, z) in that order.  Only s (l = 0) and p (l = 1) shells.
+ *   - The caller owns every buffer it passes; the library never frees caller
+ *     memory.  The library owns what it allocates (context workspaces, tree
+ *     data) and releases it in occk_destroy / occk_tree_destroy.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued asynchronously on it.
+ *   - One context per host thread; a context and its trees belong to one
+ *     device.
+ */
+#ifndef OCCK_H
+#define OCCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int occk_status;
+#define OCCK_OK               0
+#define OCCK_ERR_ARG         -1   /* null pointer, bad size, bad enum */
+#define OCCK_ERR_SHAPE       -2   /* inconsistent dimensions (nocc, ld, lmax) */
+#define OCCK_ERR_CUDA        -3   /* a CUDA runtime call failed */
+#define OCCK_ERR_OOM         -4   /* device or host allocation failed */
+#define OCCK_ERR_TIMEOUT     -5   /* a bounded device wait gave up */
+#define OCCK_ERR_UNSUPPORTED -6   /* l > 1 shells, lmax out of range, no device */
+#define OCCK_ERR_STATE       -7   /* call order violated (e.g. no multipoles) */
+
+typedef struct occk_ctx  occk_ctx;    /* opaque: device, workspaces, MLP, tuning */
+typedef struct occk_tree occk_tree;   /* opaque: boxes, lists, pair multipoles, operators */
+
+/* Contracted s/p Gaussian basis (paper, Sec. II: AO basis functions phi_r;
+ * contracted shells as used in the paper's implementation).  All arrays are
+ * host memory, read during occk_build_tree only. */
+typedef struct {
+    int natom;
+    const double* xyz;          /* [natom][3] atom positions, bohr */
+    int nshell;
+    const int* shell_atom;      /* [nshell] atom of each shell */
+    const int* shell_l;         /* [nshell] 0 (s) or 1 (p) */
+    const int* shell_nprim;     /* [nshell] primitives per shell, >= 1 */
+    const double* exps;         /* [sum nprim] exponents, shell-major */
+    const double* coefs;        /* [sum nprim] coefficients of NORMALISED
+                                   primitives; each contracted function is
+                                   renormalised to unit self-overlap */
+} occk_basis;
+
+/* Box-hierarchy parameters (paper, Sec. II: depth N_s, well-separatedness). */
+typedef struct {
+    int depth;                       /* subdivisions D >= 1; 0 => choose D in
+                                        1..12 whose mean atoms per non-empty
+                                        leaf is closest to target */
+    double target_atoms_per_leaf;    /* used when depth == 0 (e.g. 8) */
+    int ws_boxes;                    /* must be 1: nearest-neighbour boxes are
+                                        near field */
+    double pair_thresh;              /* shell-pair screen (default 1e-14): keep
+                                        (a,b) if max_pq |c_p c_q| (2 sqrt(a_p a_q)
+                                        /(a_p+a_q))^1.5 exp(-mu_pq R_ab^2) > thresh */
+} occk_tree_params;
+
+typedef enum {
+    OCCK_FP64 = 0,     /* all steps in FP64 (DFMA) */
+    OCCK_FP32 = 1,     /* all contractions in FP32 FMA; K, E reduced in FP64 */
+    OCCK_TF32 = 2,     /* (a),(c),(e) on tensor cores, TF32 inputs, FP32 accumulate */
+    OCCK_BF16 = 3,     /* (a),(c),(e) on tensor cores, BF16 inputs, FP32 accumulate */
+    OCCK_FP16 = 4,     /* (a),(c),(e) on tensor cores, FP16 inputs, FP32 accumulate */
+    OCCK_BF16X3 = 5,   /* BF16 hi/lo split, three products (hi*hi + hi*lo + lo*hi) */
+    OCCK_FP16X2 = 6    /* FP16 hi/lo split of one operand, two products */
+} occk_precision;
+
+typedef struct {
+    int nao, natom, nshell, depth;
+    int nbox;                  /* non-empty boxes, all levels */
+    int nleaf;                 /* non-empty leaf boxes */
+    int npair;                 /* kept shell pairs */
+    int nentry;                /* ordered AO-pair entries (both orders) */
+    int nrow;                  /* sum over leaves of |S_B| (AOs touched per leaf) */
+    int nm2l;                  /* M2L edges (target, source), all levels */
+    int lmax;                  /* rank of the last occk_pair_multipoles, -1 if none */
+    double x0[3];              /* root cube min corner */
+    double side;               /* root cube side */
+} occk_tree_info;
+
+/* Context.  device >= 0 binds CUDA device `device`; device = -1 makes a
+ * host-only context that can build and query trees but runs no kernel
+ * (occk_pair_multipoles / occk_farfield_K then fail with UNSUPPORTED). */
+occk_status occk_create(occk_ctx** out, int device);
+void occk_destroy(occk_ctx* ctx);
+const char* occk_last_error(const occk_ctx* ctx);
+
+/* Build the box hierarchy on the host (paper, Sec. II: "hierarchy of boxes",
+ * interaction list = non-neighbouring boxes of the same level whose parents
+ * are the parent's neighbours).  Steps: screen shell pairs (a <= b); pair
+ * centre = sum_pq w_pq P_pq / sum_pq w_pq with w_pq = exp(-mu_pq R_ab^2) (the
+ * whole pair goes to one box: "X is unique to each pair r, s"); root cube =
+ * bounding box of the centres widened by 1e-6 of its largest extent; leaf
+ * index floor((x - x0)/h), clamped; empty boxes dropped; boxes ordered by
+ * (level, ix, iy, iz).  Floating-point decisions use IEEE double without
+ * contraction, so the integer tree is reproducible.  Host work only; with a
+ * device context it also uploads the tree.  *out is owned by the caller and
+ * released with occk_tree_destroy. */
+occk_status occk_build_tree(occk_ctx* ctx, const occk_basis* basis,
+                            const occk_tree_params* params, occk_tree** out);
+void occk_tree_destroy(occk_tree* tree);
+occk_status occk_query(const occk_tree* tree, occk_tree_info* info);
+
+/* Copy one integer/real array of the tree to host memory (for checking the
+ * tree against an independent implementation).  `bytes` must equal the
+ * array's size exactly, else OCCK_ERR_SHAPE.
+ *   OCCK_TREE_LEVEL_OFF  int32 [depth+2]       first box of each level
+ *   OCCK_TREE_BOX_KEY    int32 [nbox][3]       integer box coordinates
+ *   OCCK_TREE_PARENT     int32 [nbox]          parent box (-1 for the root)
+ *   OCCK_TREE_CENTRE     double [nbox][3]      box centres
+ *   OCCK_TREE_M2L        int32 [nm2l][2]       (target, source) sorted
+ *   OCCK_TREE_PAIRS      int32 [npair][3]      (shell a, shell b, leaf box)
+ *   OCCK_TREE_PAIR_CENTRE double [npair][3]
+ *   OCCK_TREE_LEAF_AOS   int32 [nrow]          S_B of each leaf, leaves in order
+ *   OCCK_TREE_LEAF_ROWOFF int32 [nleaf+1]      offsets into LEAF_AOS */
+enum {
+    OCCK_TREE_LEVEL_OFF = 0, OCCK_TREE_BOX_KEY = 1, OCCK_TREE_PARENT = 2,
+    OCCK_TREE_CENTRE = 3, OCCK_TREE_M2L = 4, OCCK_TREE_PAIRS = 5,
+    OCCK_TREE_PAIR_CENTRE = 6, OCCK_TREE_LEAF_AOS = 7, OCCK_TREE_LEAF_ROWOFF = 8
+};
+occk_status occk_tree_export(const occk_tree* tree, int what, void* host_out, size_t bytes);
+
+/* Step a0, once per geometry and rank (paper, Sec. II, the AO multipole
+ * integrals O^{rs,X}_lm = int phi_r O_lm(r - X) phi_s about the centre X of
+ * the leaf box that owns the pair; and the translation operators built from
+ * the scaled solid harmonics O_lm, M_lm of Sec. I).  Computes, in FP64 on the
+ * device: every kept pair's multipoles up to rank lmax (0 <= lmax <= 12), and
+ * the real-form M2M, M2L and L2L matrices for every offset used by the tree.
+ * Results stay on the device, owned by the tree.  Asynchronous on `stream`. */
+occk_status occk_pair_multipoles(occk_ctx* ctx, occk_tree* tree, int lmax, void* stream);
+
+/* Per-edge multipole ranks for M2L (lmax_policy = 1 of occk_farfield_K):
+ * ranks[e] in [0, lmax] for every M2L edge e in OCCK_TREE_M2L order; the
+ * edge operator keeps output and input ranks <= ranks[e]; M2M and L2L keep
+ * the tree's lmax.  Host array, copied.  n must equal nm2l. */
+occk_status occk_set_edge_lmax(occk_ctx* ctx, occk_tree* tree, const int* ranks, int n);
+
+/* The far-field exchange, steps (a)-(e) (paper, Sec. II, from "First, for each
+ * box at the lowest level ..." to Eq. kri):
+ *   C_dev  [nao x nocc] column-major FP64 device, leading dimension ldc >= nao
+ *   K_dev  [nao x nocc] column-major FP64 device output, ldk >= nao; holds
+ *          K^ff_ri = 2 sum_j sum_lm O^{rj,X}_lm Mcal^{ij}_lm(X) on return
+ *   Ex_dev FP64 device scalar output (nullable): E^ff = -1/2 sum_ri C_ri K_ri
+ *   Ex_host FP64 host output (nullable); when non-null the call synchronises
+ *          `stream` before returning (do not pass it during graph capture)
+ *   prec   arithmetic of the contractions (occk_precision)
+ *   lmax_policy 0 = the tree's lmax on every edge; 1 = per-edge ranks from
+ *          occk_set_edge_lmax (falls back to 0 when none were set)
+ * Requires occk_pair_multipoles on this tree.  Workspaces are owned by the
+ * context and grow on demand (allocation happens outside any timed loop on
+ * the first call with a given shape). */
+occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tree, int nocc,
+                            const double* C_dev, int ldc, int prec, int lmax_policy,
+                            double* K_dev, int ldk, double* Ex_dev, double* Ex_host,
+                            void* stream);
+
+/* Intermediate results of the last occk_farfield_K on this context, copied to
+ * host memory, for step-by-step checking (synchronises `stream`).
+ *   OCCK_DBG_PAIR_MULT  double [nvals][nc]      pair multipoles (real form)
+ *   OCCK_DBG_OBOX       double [nbox][nc][nocc*nocc]  occupied multipoles
+ *   OCCK_DBG_MBOX       double [nbox][nc][nocc*nocc]  local expansions
+ * Real form of a rank-L expansion, nc = (L+1)^2 reals: for each l, Re m=0,
+ * then (Re, Im) for m = 1..l (components with m < 0 follow from
+ * X_{l,-m} = (-1)^m conj X_{lm}).  Levels 0-1 are zero (no M2L there).
+ * FP32 runs are widened to double. */
+enum { OCCK_DBG_PAIR_MULT = 0, OCCK_DBG_OBOX = 1, OCCK_DBG_MBOX = 2 };
+occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* tree, int what,
+                             void* host_out, size_t bytes, void* stream);
+
+/* Opt-in stage timers (CUDA events recorded on the call's stream between
+ * stages).  on != 0 enables them for later occk_farfield_K calls on this
+ * context.  occk_get_timings synchronises on the last recorded event and
+ * writes the durations (ms) of the last call's stages to ms[0..OCCK_NSTAGE-1]:
+ *   0 (a) C transpose + AO->MO half transform   1 (a) full transform O^{ij}
+ *   2 (b) M2M   3 (c) M2L   4 (d) L2L   5 (e) L2P   6 K reduction + energy
+ * n must be >= OCCK_NSTAGE. */
+#define OCCK_NSTAGE 7
+occk_status occk_set_timing(occk_ctx* ctx, int on);
+occk_status occk_get_timings(occk_ctx* ctx, float* ms, int n);
+
+/* Sustained FMA throughput of this device for one arithmetic (prec =
+ * OCCK_FP64 or OCCK_FP32), measured by a dependent-chain FMA kernel over all
+ * SMs; *flops receives FLOP/s (2 per FMA).  Synchronises `stream`.  A
+ * measurement aid for roofline reporting, not part of the exchange path. */
+occk_status occk_probe_fma_peak(occk_ctx* ctx, int prec, double* flops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCCK_H */

@@ -30,6 +30,16 @@ import math
 import numpy as np
 
 
+# The C library's exp: pair centres are compared bit for bit with the host
+# implementation, and a centre that lies exactly on a box face (the middle of
+# a symmetric molecule) must round the same way on both sides.
+_exp = np.frompyfunc(math.exp, 1, 1)
+
+
+def _exp_f64(x):
+    return _exp(x).astype(np.float64)
+
+
 def shell_pairs(basis, thresh: float = 1e-14):
     """Screened shell pairs (a <= b) and their centres, in (a, b) order."""
     poff = basis.shell_prim_offset
@@ -56,7 +66,7 @@ def shell_pairs(basis, thresh: float = 1e-14):
             cb = basis.coefs[ib]
             pp = ea + eb
             mu = ea * eb / pp
-            w = np.exp(-mu * R2)
+            w = _exp_f64(-mu * R2)
             t = 2.0 * np.sqrt(ea * eb) / pp
             e = np.abs(ca * cb) * (t * np.sqrt(t)) * w
             est = np.where(ok, np.maximum(est, e), est)

@@ -1,0 +1,794 @@
+// Host side of the occ-FMM-K library: contexts, the box hierarchy, the ABI.
+//
+// Compiled with -ffp-contract=off: every floating-point decision that feeds
+// the integer tree (pair screening, pair centres, box indices) is a plain IEEE
+// double expression evaluated in a fixed order, so the tree is reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#include "occk_internal.h"
+
+using occk::OpDesc;
+using occk::PairDesc;
+
+namespace {
+
+occk_status fail(occk_ctx* ctx, occk_status code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+occk_status cuda_fail(occk_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, OCCK_ERR_CUDA, m);
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+    *dst = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)dst, v.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+cudaError_t ensure(occk::DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) b.bytes = bytes;
+    return e;
+}
+
+void free_tree_device(occk_tree* t) {
+    auto& d = t->dev;
+    dfree(d.row_ptr); dfree(d.ent_col); dfree(d.ent_val);
+    dfree(d.leaf_rowoff); dfree(d.leaf_aos); dfree(d.ao_row_ptr); dfree(d.ao_rows);
+    dfree(d.child_ptr); dfree(d.child_list); dfree(d.m2m_op);
+    dfree(d.m2l_ptr); dfree(d.m2l_src); dfree(d.m2l_op);
+    dfree(d.m2l_lmax_full); dfree(d.m2l_lmax_edge); dfree(d.parent);
+    dfree(d.pairs); dfree(d.prim_exp); dfree(d.prim_coef);
+    dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.opdesc);
+    dfree(d.l2l_op);
+}
+
+inline long long ifloor_clamp(double v, long long n) {
+    double f = std::floor(v);
+    long long k = (long long)f;
+    if (k < 0) k = 0;
+    if (k > n - 1) k = n - 1;
+    return k;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Context
+// ===========================================================================
+
+extern "C" occk_status occk_create(occk_ctx** out, int device) {
+    if (!out) return OCCK_ERR_ARG;
+    *out = nullptr;
+    occk_ctx* c = new (std::nothrow) occk_ctx();
+    if (!c) return OCCK_ERR_OOM;
+    c->device = device;
+    if (device >= 0) {
+        int n = 0;
+        cudaError_t e = cudaGetDeviceCount(&n);
+        if (e != cudaSuccess || device >= n) {
+            delete c;
+            return OCCK_ERR_UNSUPPORTED;
+        }
+        e = cudaSetDevice(device);
+        if (e != cudaSuccess) {
+            delete c;
+            return OCCK_ERR_CUDA;
+        }
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    }
+    *out = c;
+    return OCCK_OK;
+}
+
+extern "C" void occk_destroy(occk_ctx* c) {
+    if (!c) return;
+    if (c->device >= 0) {
+        cudaSetDevice(c->device);
+        for (int k = 0; k <= OCCK_NSTAGE; ++k)
+            if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+        for (occk::DevBuf* b : {&c->ct, &c->w, &c->obox, &c->mbox, &c->kb, &c->part, &c->edev,
+                                &c->scratch}) {
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+        }
+    }
+    delete c;
+}
+
+extern "C" const char* occk_last_error(const occk_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+// ===========================================================================
+// Tree
+// ===========================================================================
+
+namespace {
+
+struct Key3 {
+    long long x, y, z;
+    bool operator<(const Key3& o) const {
+        return std::tie(x, y, z) < std::tie(o.x, o.y, o.z);
+    }
+    bool operator==(const Key3& o) const { return x == o.x && y == o.y && z == o.z; }
+};
+
+inline long long cheb(const Key3& a, const Key3& b) {
+    long long dx = std::llabs(a.x - b.x), dy = std::llabs(a.y - b.y), dz = std::llabs(a.z - b.z);
+    return std::max(dx, std::max(dy, dz));
+}
+
+}  // namespace
+
+extern "C" occk_status occk_build_tree(occk_ctx* ctx, const occk_basis* bs,
+                                       const occk_tree_params* prm, occk_tree** out) {
+    if (!ctx || !bs || !prm || !out) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (bs->natom <= 0 || bs->nshell <= 0 || !bs->xyz || !bs->shell_atom || !bs->shell_l ||
+        !bs->shell_nprim || !bs->exps || !bs->coefs)
+        return fail(ctx, OCCK_ERR_ARG, "basis: empty or null arrays");
+    if (prm->ws_boxes != 1)
+        return fail(ctx, OCCK_ERR_UNSUPPORTED, "only ws_boxes = 1 (nearest neighbours excluded)");
+    if (prm->depth < 0 || prm->depth > 20)
+        return fail(ctx, OCCK_ERR_ARG, "depth out of range");
+    if (prm->depth == 0 && !(prm->target_atoms_per_leaf > 0))
+        return fail(ctx, OCCK_ERR_ARG, "target_atoms_per_leaf must be > 0 when depth = 0");
+
+    occk_tree* t = new (std::nothrow) occk_tree();
+    if (!t) return fail(ctx, OCCK_ERR_OOM, "host allocation");
+    t->device = ctx->device;
+    const int ns = bs->nshell;
+    t->natom = bs->natom;
+    t->nshell = ns;
+    t->shell_l.resize(ns);
+    t->shell_nprim.resize(ns);
+    t->shell_prim_off.resize(ns + 1);
+    t->shell_ao_off.resize(ns + 1);
+    t->shell_xyz.resize(3 * ns);
+    t->shell_prim_off[0] = 0;
+    t->shell_ao_off[0] = 0;
+    for (int s = 0; s < ns; ++s) {
+        int a = bs->shell_atom[s];
+        int l = bs->shell_l[s];
+        int np = bs->shell_nprim[s];
+        if (a < 0 || a >= bs->natom || np < 1) {
+            delete t;
+            return fail(ctx, OCCK_ERR_ARG, "basis: bad shell_atom or shell_nprim");
+        }
+        if (l != 0 && l != 1) {
+            delete t;
+            return fail(ctx, OCCK_ERR_UNSUPPORTED, "only s and p shells are supported");
+        }
+        t->shell_l[s] = l;
+        t->shell_nprim[s] = np;
+        t->shell_prim_off[s + 1] = t->shell_prim_off[s] + np;
+        t->shell_ao_off[s + 1] = t->shell_ao_off[s] + (l == 0 ? 1 : 3);
+        for (int k = 0; k < 3; ++k) t->shell_xyz[3 * s + k] = bs->xyz[3 * a + k];
+    }
+    t->nao = t->shell_ao_off[ns];
+    const int nprim = t->shell_prim_off[ns];
+    for (int p = 0; p < nprim; ++p) {
+        if (!(bs->exps[p] > 0)) {
+            delete t;
+            return fail(ctx, OCCK_ERR_ARG, "basis: exponents must be positive");
+        }
+    }
+
+    // ---- primitive coefficients with primitive and contracted normalisation
+    t->prim_exp.assign(bs->exps, bs->exps + nprim);
+    t->prim_coef.resize(nprim);
+    for (int s = 0; s < ns; ++s) {
+        int o = t->shell_prim_off[s], np = t->shell_nprim[s], l = t->shell_l[s];
+        std::vector<double> d(np);
+        for (int p = 0; p < np; ++p) {
+            double a = bs->exps[o + p];
+            double n = std::pow(2.0 * a / M_PI, 0.75);
+            if (l == 1) n = n * 2.0 * std::sqrt(a);
+            d[p] = bs->coefs[o + p] * n;
+        }
+        double self = 0.0;
+        for (int p = 0; p < np; ++p)
+            for (int q = 0; q < np; ++q) {
+                double pq = bs->exps[o + p] + bs->exps[o + q];
+                double v = std::pow(M_PI / pq, 1.5);
+                if (l == 1) v = v / (2.0 * pq);
+                self += d[p] * d[q] * v;
+            }
+        double inv = 1.0 / std::sqrt(self);
+        for (int p = 0; p < np; ++p) t->prim_coef[o + p] = d[p] * inv;
+    }
+
+    // ---- screened shell pairs (a <= b) and their centres
+    const double thresh = prm->pair_thresh;
+    std::vector<double> cen;
+    for (int a = 0; a < ns; ++a) {
+        const double* A = &t->shell_xyz[3 * a];
+        for (int b = a; b < ns; ++b) {
+            const double* B = &t->shell_xyz[3 * b];
+            double dx = A[0] - B[0], dy = A[1] - B[1], dz = A[2] - B[2];
+            double R2 = dx * dx + dy * dy + dz * dz;
+            double est = 0.0, sw = 0.0, swx[3] = {0.0, 0.0, 0.0};
+            int oa = t->shell_prim_off[a], ob = t->shell_prim_off[b];
+            for (int p = 0; p < t->shell_nprim[a]; ++p) {
+                for (int q = 0; q < t->shell_nprim[b]; ++q) {
+                    double ea = bs->exps[oa + p], eb = bs->exps[ob + q];
+                    double ca = bs->coefs[oa + p], cb = bs->coefs[ob + q];
+                    double pp = ea + eb;
+                    double mu = ea * eb / pp;
+                    double w = std::exp(-mu * R2);
+                    double tt = 2.0 * std::sqrt(ea * eb) / pp;
+                    double e = std::fabs(ca * cb) * (tt * std::sqrt(tt)) * w;
+                    est = std::max(est, e);
+                    sw = sw + w;
+                    for (int k = 0; k < 3; ++k) {
+                        double P = (ea * A[k] + eb * B[k]) / pp;
+                        swx[k] = swx[k] + w * P;
+                    }
+                }
+            }
+            if (est > thresh) {
+                t->pair_a.push_back(a);
+                t->pair_b.push_back(b);
+                for (int k = 0; k < 3; ++k) cen.push_back(swx[k] / sw);
+            }
+        }
+    }
+    const int npair = (int)t->pair_a.size();
+    if (npair == 0) {
+        delete t;
+        return fail(ctx, OCCK_ERR_ARG, "no shell pair passes the screen");
+    }
+    t->pair_centre = cen;
+
+    // ---- root cube
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = cen[k];
+        hi[k] = cen[k];
+    }
+    for (int i = 1; i < npair; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], cen[3 * i + k]);
+            hi[k] = std::max(hi[k], cen[3 * i + k]);
+        }
+    double extent = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    double delta = extent > 0 ? 1e-6 * extent : 1e-6;
+    for (int k = 0; k < 3; ++k) t->x0[k] = lo[k] - delta;
+    t->side = extent + 2.0 * delta;
+
+    // ---- depth
+    int D = prm->depth;
+    if (D <= 0) {
+        double best_err = -1.0;
+        int best_D = 1;
+        for (int d = 1; d <= 12; ++d) {
+            long long n = 1LL << d;
+            double h = t->side / (double)n;
+            std::set<Key3> occ;
+            for (int i = 0; i < bs->natom; ++i) {
+                Key3 kk;
+                kk.x = ifloor_clamp((bs->xyz[3 * i + 0] - t->x0[0]) / h, n);
+                kk.y = ifloor_clamp((bs->xyz[3 * i + 1] - t->x0[1]) / h, n);
+                kk.z = ifloor_clamp((bs->xyz[3 * i + 2] - t->x0[2]) / h, n);
+                occ.insert(kk);
+            }
+            double mean = (double)bs->natom / (double)occ.size();
+            double err = std::fabs(mean - prm->target_atoms_per_leaf);
+            if (best_err < 0 || err < best_err) {
+                best_err = err;
+                best_D = d;
+            }
+        }
+        D = best_D;
+    }
+    t->depth = D;
+    const long long nD = 1LL << D;
+    const double hD = t->side / (double)nD;
+    std::vector<Key3> leafkey(npair);
+    for (int i = 0; i < npair; ++i) {
+        leafkey[i].x = ifloor_clamp((cen[3 * i + 0] - t->x0[0]) / hD, nD);
+        leafkey[i].y = ifloor_clamp((cen[3 * i + 1] - t->x0[1]) / hD, nD);
+        leafkey[i].z = ifloor_clamp((cen[3 * i + 2] - t->x0[2]) / hD, nD);
+    }
+
+    // ---- boxes per level, ordered (level, ix, iy, iz)
+    t->level_off.assign(1, 0);
+    std::vector<std::map<Key3, int>> index(D + 1);
+    std::vector<Key3> keys;
+    std::vector<int> level;
+    for (int lev = 0; lev <= D; ++lev) {
+        std::set<Key3> u;
+        int sh = D - lev;
+        for (auto& k : leafkey) u.insert(Key3{k.x >> sh, k.y >> sh, k.z >> sh});
+        for (auto& k : u) {
+            index[lev][k] = (int)keys.size();
+            keys.push_back(k);
+            level.push_back(lev);
+        }
+        t->level_off.push_back((int)keys.size());
+    }
+    const int nbox = (int)keys.size();
+    t->h.resize(D + 1);
+    for (int lev = 0; lev <= D; ++lev) t->h[lev] = t->side / (double)(1LL << lev);
+    t->box_key.resize(3 * nbox);
+    t->parent.assign(nbox, -1);
+    t->centre.resize(3 * nbox);
+    for (int b = 0; b < nbox; ++b) {
+        t->box_key[3 * b + 0] = (int)keys[b].x;
+        t->box_key[3 * b + 1] = (int)keys[b].y;
+        t->box_key[3 * b + 2] = (int)keys[b].z;
+        int lev = level[b];
+        if (lev > 0) t->parent[b] = index[lev - 1][Key3{keys[b].x >> 1, keys[b].y >> 1, keys[b].z >> 1}];
+        const long long kk[3] = {keys[b].x, keys[b].y, keys[b].z};
+        for (int k = 0; k < 3; ++k)
+            t->centre[3 * b + k] = t->x0[k] + ((double)kk[k] + 0.5) * t->h[lev];
+    }
+
+    // ---- interaction lists, levels 2..D
+    for (int lev = 2; lev <= D; ++lev) {
+        int lo_ = t->level_off[lev], hi_ = t->level_off[lev + 1];
+        for (int a = lo_; a < hi_; ++a) {
+            Key3 pa{keys[a].x >> 1, keys[a].y >> 1, keys[a].z >> 1};
+            for (int c = lo_; c < hi_; ++c) {
+                Key3 pc{keys[c].x >> 1, keys[c].y >> 1, keys[c].z >> 1};
+                if (cheb(pa, pc) <= 1 && cheb(keys[a], keys[c]) > 1) {
+                    t->m2l_tgt.push_back(a);
+                    t->m2l_src.push_back(c);
+                }
+            }
+        }
+    }
+
+    // ---- pair -> leaf, leaf AO sets
+    const int leaf0 = t->level_off[D];
+    const int nleaf = t->level_off[D + 1] - leaf0;
+    t->pair_leaf.resize(npair);
+    std::vector<std::set<int>> aoset(nleaf);
+    for (int i = 0; i < npair; ++i) {
+        int leaf = index[D][leafkey[i]];
+        t->pair_leaf[i] = leaf;
+        int a = t->pair_a[i], b = t->pair_b[i];
+        for (int r = t->shell_ao_off[a]; r < t->shell_ao_off[a + 1]; ++r) aoset[leaf - leaf0].insert(r);
+        for (int r = t->shell_ao_off[b]; r < t->shell_ao_off[b + 1]; ++r) aoset[leaf - leaf0].insert(r);
+    }
+    t->leaf_rowoff.assign(1, 0);
+    std::vector<std::map<int, int>> localrow(nleaf);
+    for (int B = 0; B < nleaf; ++B) {
+        for (int r : aoset[B]) {
+            localrow[B][r] = (int)t->leaf_aos.size() - t->leaf_rowoff[B];
+            t->leaf_aos.push_back(r);
+        }
+        t->leaf_rowoff.push_back((int)t->leaf_aos.size());
+    }
+    const int nrow = (int)t->leaf_aos.size();
+
+    // ---- ordered AO-pair entries (row r, column s, value row)
+    std::vector<std::vector<std::pair<int, int>>> rows(nrow);
+    int vo = 0;
+    for (int i = 0; i < npair; ++i) {
+        int a = t->pair_a[i], b = t->pair_b[i];
+        int B = t->pair_leaf[i] - leaf0;
+        int na = t->shell_ao_off[a + 1] - t->shell_ao_off[a];
+        int nb = t->shell_ao_off[b + 1] - t->shell_ao_off[b];
+        for (int ia = 0; ia < na; ++ia)
+            for (int ib = 0; ib < nb; ++ib) {
+                int r = t->shell_ao_off[a] + ia, s = t->shell_ao_off[b] + ib;
+                int v = vo + ia * nb + ib;
+                rows[t->leaf_rowoff[B] + localrow[B][r]].push_back({s, v});
+                if (a != b) rows[t->leaf_rowoff[B] + localrow[B][s]].push_back({r, v});
+            }
+        vo += na * nb;
+    }
+    t->nvals = vo;
+    t->row_ptr.assign(1, 0);
+    for (int r = 0; r < nrow; ++r) {
+        for (auto& e : rows[r]) {
+            t->ent_col.push_back(e.first);
+            t->ent_val.push_back(e.second);
+        }
+        t->row_ptr.push_back((int)t->ent_col.size());
+    }
+    // AO -> rows
+    std::vector<std::vector<int>> aorows(t->nao);
+    for (int r = 0; r < nrow; ++r) aorows[t->leaf_aos[r]].push_back(r);
+    t->ao_row_ptr.assign(1, 0);
+    for (int r = 0; r < t->nao; ++r) {
+        for (int x : aorows[r]) t->ao_rows.push_back(x);
+        t->ao_row_ptr.push_back((int)t->ao_rows.size());
+    }
+
+    // ---- translation schedule: distinct operators per (kind, level, offset)
+    std::map<std::tuple<int, int, int, int, int>, int> opid;
+    auto get_op = [&](int kind, int lev, int ox, int oy, int oz) {
+        auto key = std::make_tuple(kind, lev, ox, oy, oz);
+        auto it = opid.find(key);
+        if (it != opid.end()) return it->second;
+        OpDesc d{};
+        d.kind = kind;
+        if (kind == 2) {
+            d.d[0] = (double)ox * t->h[lev];
+            d.d[1] = (double)oy * t->h[lev];
+            d.d[2] = (double)oz * t->h[lev];
+        } else {
+            d.d[0] = ((double)ox - 0.5) * t->h[lev];
+            d.d[1] = ((double)oy - 0.5) * t->h[lev];
+            d.d[2] = ((double)oz - 0.5) * t->h[lev];
+        }
+        int id = (int)t->ops.size();
+        t->ops.push_back(d);
+        opid[key] = id;
+        return id;
+    };
+    t->m2m_op.assign(nbox, -1);
+    t->l2l_op.assign(nbox, -1);
+    std::vector<std::vector<int>> ch(nbox);
+    for (int lev = 3; lev <= D; ++lev)
+        for (int c = t->level_off[lev]; c < t->level_off[lev + 1]; ++c) {
+            int ox = (int)(keys[c].x & 1), oy = (int)(keys[c].y & 1), oz = (int)(keys[c].z & 1);
+            t->m2m_op[c] = get_op(0, lev, ox, oy, oz);
+            t->l2l_op[c] = get_op(1, lev, ox, oy, oz);
+            ch[t->parent[c]].push_back(c);
+        }
+    t->child_ptr.assign(1, 0);
+    for (int b = 0; b < nbox; ++b) {
+        for (int c : ch[b]) t->child_list.push_back(c);
+        t->child_ptr.push_back((int)t->child_list.size());
+    }
+    const int ne = (int)t->m2l_tgt.size();
+    t->m2l_op.resize(ne);
+    t->m2l_ptr.assign(nbox + 1, 0);
+    for (int e = 0; e < ne; ++e) {
+        int a = t->m2l_tgt[e], c = t->m2l_src[e];
+        int lev = level[a];
+        t->m2l_op[e] = get_op(2, lev, (int)(keys[a].x - keys[c].x), (int)(keys[a].y - keys[c].y),
+                              (int)(keys[a].z - keys[c].z));
+        t->m2l_ptr[a + 1]++;
+    }
+    for (int b = 0; b < nbox; ++b) t->m2l_ptr[b + 1] += t->m2l_ptr[b];
+
+    // ---- device upload
+    if (ctx->device >= 0) {
+        cudaError_t e = cudaSetDevice(ctx->device);
+        auto& d = t->dev;
+        std::vector<PairDesc> pd(npair);
+        int voff = 0;
+        for (int i = 0; i < npair; ++i) {
+            int a = t->pair_a[i], b = t->pair_b[i];
+            PairDesc& p = pd[i];
+            for (int k = 0; k < 3; ++k) {
+                p.A[k] = t->shell_xyz[3 * a + k];
+                p.B[k] = t->shell_xyz[3 * b + k];
+                p.X[k] = t->centre[3 * t->pair_leaf[i] + k];
+            }
+            p.prim_a = t->shell_prim_off[a];
+            p.nprim_a = t->shell_nprim[a];
+            p.prim_b = t->shell_prim_off[b];
+            p.nprim_b = t->shell_nprim[b];
+            p.la = t->shell_l[a];
+            p.lb = t->shell_l[b];
+            p.val_off = voff;
+            voff += (p.la ? 3 : 1) * (p.lb ? 3 : 1);
+        }
+        std::vector<int> m2l_src_dev(t->m2l_src), lmfull(ne, 0);
+        if (e == cudaSuccess) e = upload(&d.row_ptr, t->row_ptr);
+        if (e == cudaSuccess) e = upload(&d.ent_col, t->ent_col);
+        if (e == cudaSuccess) e = upload(&d.ent_val, t->ent_val);
+        if (e == cudaSuccess) e = upload(&d.leaf_rowoff, t->leaf_rowoff);
+        if (e == cudaSuccess) e = upload(&d.leaf_aos, t->leaf_aos);
+        if (e == cudaSuccess) e = upload(&d.ao_row_ptr, t->ao_row_ptr);
+        if (e == cudaSuccess) e = upload(&d.ao_rows, t->ao_rows);
+        if (e == cudaSuccess) e = upload(&d.child_ptr, t->child_ptr);
+        if (e == cudaSuccess) e = upload(&d.child_list, t->child_list);
+        if (e == cudaSuccess) e = upload(&d.m2m_op, t->m2m_op);
+        if (e == cudaSuccess) e = upload(&d.l2l_op, t->l2l_op);
+        if (e == cudaSuccess) e = upload(&d.m2l_ptr, t->m2l_ptr);
+        if (e == cudaSuccess) e = upload(&d.m2l_src, m2l_src_dev);
+        if (e == cudaSuccess) e = upload(&d.m2l_op, t->m2l_op);
+        if (e == cudaSuccess) e = upload(&d.parent, t->parent);
+        if (e == cudaSuccess) e = upload(&d.pairs, pd);
+        if (e == cudaSuccess) e = upload(&d.prim_exp, t->prim_exp);
+        if (e == cudaSuccess) e = upload(&d.prim_coef, t->prim_coef);
+        if (e == cudaSuccess) e = upload(&d.opdesc, t->ops);
+        if (e == cudaSuccess) e = upload(&d.m2l_lmax_full, lmfull);
+        if (e != cudaSuccess) {
+            free_tree_device(t);
+            delete t;
+            return cuda_fail(ctx, e, "occk_build_tree upload");
+        }
+    }
+    *out = t;
+    return OCCK_OK;
+}
+
+extern "C" void occk_tree_destroy(occk_tree* t) {
+    if (!t) return;
+    if (t->device >= 0) {
+        cudaSetDevice(t->device);
+        free_tree_device(t);
+    }
+    delete t;
+}
+
+extern "C" occk_status occk_query(const occk_tree* t, occk_tree_info* info) {
+    if (!t || !info) return OCCK_ERR_ARG;
+    info->nao = t->nao;
+    info->natom = t->natom;
+    info->nshell = t->nshell;
+    info->depth = t->depth;
+    info->nbox = (int)t->parent.size();
+    info->nleaf = (int)t->leaf_rowoff.size() - 1;
+    info->npair = (int)t->pair_a.size();
+    info->nentry = (int)t->ent_col.size();
+    info->nrow = (int)t->leaf_aos.size();
+    info->nm2l = (int)t->m2l_tgt.size();
+    info->lmax = t->lmax;
+    for (int k = 0; k < 3; ++k) info->x0[k] = t->x0[k];
+    info->side = t->side;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_tree_export(const occk_tree* t, int what, void* out, size_t bytes) {
+    if (!t || !out) return OCCK_ERR_ARG;
+    std::vector<int> iv;
+    const void* src = nullptr;
+    size_t n = 0;
+    switch (what) {
+        case OCCK_TREE_LEVEL_OFF: src = t->level_off.data(); n = t->level_off.size() * 4; break;
+        case OCCK_TREE_BOX_KEY: src = t->box_key.data(); n = t->box_key.size() * 4; break;
+        case OCCK_TREE_PARENT: src = t->parent.data(); n = t->parent.size() * 4; break;
+        case OCCK_TREE_CENTRE: src = t->centre.data(); n = t->centre.size() * 8; break;
+        case OCCK_TREE_M2L:
+            for (size_t e = 0; e < t->m2l_tgt.size(); ++e) {
+                iv.push_back(t->m2l_tgt[e]);
+                iv.push_back(t->m2l_src[e]);
+            }
+            src = iv.data(); n = iv.size() * 4; break;
+        case OCCK_TREE_PAIRS:
+            for (size_t e = 0; e < t->pair_a.size(); ++e) {
+                iv.push_back(t->pair_a[e]);
+                iv.push_back(t->pair_b[e]);
+                iv.push_back(t->pair_leaf[e]);
+            }
+            src = iv.data(); n = iv.size() * 4; break;
+        case OCCK_TREE_PAIR_CENTRE: src = t->pair_centre.data(); n = t->pair_centre.size() * 8; break;
+        case OCCK_TREE_LEAF_AOS: src = t->leaf_aos.data(); n = t->leaf_aos.size() * 4; break;
+        case OCCK_TREE_LEAF_ROWOFF: src = t->leaf_rowoff.data(); n = t->leaf_rowoff.size() * 4; break;
+        default: return OCCK_ERR_ARG;
+    }
+    if (n != bytes) return OCCK_ERR_SHAPE;
+    if (n) std::memcpy(out, src, n);
+    return OCCK_OK;
+}
+
+// ===========================================================================
+// Pair multipoles and operators (step a0)
+// ===========================================================================
+
+extern "C" occk_status occk_pair_multipoles(occk_ctx* ctx, occk_tree* t, int lmax, void* stream) {
+    if (!ctx || !t) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (ctx->device < 0 || t->device != ctx->device)
+        return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device bound to this context or tree");
+    if (lmax < 0 || lmax > 12) return fail(ctx, OCCK_ERR_UNSUPPORTED, "lmax must be in 0..12");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    auto& d = t->dev;
+    const int nc = occk::ncomp(lmax);
+    const int nops = (int)t->ops.size();
+    dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.pair_vals, sizeof(double) * (size_t)t->nvals * nc);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d.pair_vals_f, sizeof(float) * (size_t)t->nvals * nc);
+    if (nops > 0) {
+        if (e == cudaSuccess) e = cudaMalloc((void**)&d.ops, sizeof(double) * (size_t)nops * nc * nc);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&d.ops_f, sizeof(float) * (size_t)nops * nc * nc);
+    }
+    if (e != cudaSuccess) {
+        dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f);
+        return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "pair multipole storage")
+                                              : cuda_fail(ctx, e, "occk_pair_multipoles alloc");
+    }
+    e = occk::launch_pair_multipoles(d.pairs, (int)t->pair_a.size(), d.prim_exp, d.prim_coef, lmax,
+                                     d.pair_vals, d.pair_vals_f, t->nvals, s);
+    if (e == cudaSuccess && nops > 0) e = occk::launch_gen_ops(d.opdesc, nops, lmax, d.ops, d.ops_f, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_pair_multipoles launch");
+    t->lmax = lmax;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_edge_lmax(occk_ctx* ctx, occk_tree* t, const int* ranks, int n) {
+    if (!ctx || !t || !ranks) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (n != (int)t->m2l_tgt.size()) return fail(ctx, OCCK_ERR_SHAPE, "ranks length != nm2l");
+    if (t->lmax < 0) return fail(ctx, OCCK_ERR_STATE, "call occk_pair_multipoles first");
+    for (int i = 0; i < n; ++i)
+        if (ranks[i] < 0 || ranks[i] > t->lmax) return fail(ctx, OCCK_ERR_ARG, "rank out of [0, lmax]");
+    t->edge_lmax.assign(ranks, ranks + n);
+    if (ctx->device >= 0 && n > 0) {
+        cudaSetDevice(ctx->device);
+        dfree(t->dev.m2l_lmax_edge);
+        cudaError_t e = upload(&t->dev.m2l_lmax_edge, t->edge_lmax);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_set_edge_lmax");
+    }
+    return OCCK_OK;
+}
+
+// ===========================================================================
+// Far-field K (steps a-e)
+// ===========================================================================
+
+extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int nocc,
+                                       const double* C_dev, int ldc, int prec, int lmax_policy,
+                                       double* K_dev, int ldk, double* Ex_dev, double* Ex_host,
+                                       void* stream) {
+    if (!ctx || !tc) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    occk_tree* t = const_cast<occk_tree*>(tc);
+    if (ctx->device < 0 || t->device != ctx->device)
+        return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device bound to this context or tree");
+    if (t->lmax < 0) return fail(ctx, OCCK_ERR_STATE, "call occk_pair_multipoles first");
+    if (nocc <= 0 || !C_dev || !K_dev) return fail(ctx, OCCK_ERR_ARG, "nocc <= 0 or null C/K");
+    if (ldc < t->nao || ldk < t->nao) return fail(ctx, OCCK_ERR_SHAPE, "ldc/ldk < nao");
+    if (prec != OCCK_FP64 && prec != OCCK_FP32)
+        return fail(ctx, OCCK_ERR_UNSUPPORTED, "precision not available in this build");
+    if (lmax_policy != 0 && lmax_policy != 1) return fail(ctx, OCCK_ERR_ARG, "lmax_policy must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+
+    const int L = t->lmax, nc = occk::ncomp(L), D = t->depth;
+    const int nbox = (int)t->parent.size();
+    const int first = D >= 2 ? t->level_off[2] : nbox;
+    const int nleaf = (int)t->leaf_rowoff.size() - 1;
+    const int nrow = (int)t->leaf_aos.size();
+    const size_t P = (size_t)nocc * nocc;
+    const size_t es = prec == OCCK_FP64 ? 8 : 4;
+    int max_rows = 0;
+    for (int B = 0; B < nleaf; ++B) max_rows = std::max(max_rows, t->leaf_rowoff[B + 1] - t->leaf_rowoff[B]);
+
+    size_t nstore = (size_t)(nbox - first);
+    size_t bytes_ct = es * (size_t)t->nao * nocc;
+    size_t bytes_w = es * (size_t)nc * nrow * nocc;
+    size_t bytes_box = es * nstore * nc * P;
+    size_t bytes_kb = 8 * (size_t)nrow * nocc;
+    size_t bytes_part = 8 * (size_t)(4096 + 2);
+    if ((e = ensure(ctx->ct, bytes_ct)) != cudaSuccess ||
+        (e = ensure(ctx->w, bytes_w)) != cudaSuccess ||
+        (e = ensure(ctx->obox, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
+        (e = ensure(ctx->mbox, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
+        (e = ensure(ctx->kb, bytes_kb)) != cudaSuccess ||
+        (e = ensure(ctx->part, bytes_part)) != cudaSuccess ||
+        (e = ensure(ctx->edev, 8)) != cudaSuccess) {
+        return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "far-field workspaces")
+                                              : cuda_fail(ctx, e, "workspace allocation");
+    }
+    occk::FmmArgs a{};
+    a.nao = t->nao; a.nocc = nocc; a.ldc = ldc; a.ldk = ldk; a.nc = nc; a.L = L; a.depth = D;
+    a.nbox = nbox; a.first_box = first; a.nleaf = nleaf; a.leaf0 = t->level_off[D]; a.nrow = nrow;
+    a.level_off = t->level_off.data();
+    a.prec = prec; a.C = C_dev; a.K = K_dev;
+    a.Ex_dev = Ex_dev ? Ex_dev : (double*)ctx->edev.p;
+    auto& d = t->dev;
+    a.row_ptr = d.row_ptr; a.ent_col = d.ent_col; a.ent_val = d.ent_val;
+    a.leaf_rowoff = d.leaf_rowoff; a.leaf_aos = d.leaf_aos;
+    a.ao_row_ptr = d.ao_row_ptr; a.ao_rows = d.ao_rows;
+    a.child_ptr = d.child_ptr; a.child_list = d.child_list; a.m2m_op = d.m2m_op; a.l2l_op = d.l2l_op;
+    a.parent = d.parent;
+    a.m2l_ptr = d.m2l_ptr; a.m2l_src = d.m2l_src; a.m2l_op = d.m2l_op;
+    a.m2l_lmax = (lmax_policy == 1 && d.m2l_lmax_edge) ? d.m2l_lmax_edge : nullptr;
+    a.pair_vals = prec == OCCK_FP64 ? (const void*)d.pair_vals : (const void*)d.pair_vals_f;
+    a.ops = prec == OCCK_FP64 ? (const void*)d.ops : (const void*)d.ops_f;
+    a.ct = ctx->ct.p; a.w = ctx->w.p; a.obox = ctx->obox.p; a.mbox = ctx->mbox.p;
+    a.kb = (double*)ctx->kb.p; a.part = (double*)ctx->part.p;
+    a.leaf_rowoff_host = t->leaf_rowoff.data();
+    a.max_rows = max_rows;
+    a.ev = nullptr;
+    if (ctx->timing) {
+        for (int k = 0; k <= OCCK_NSTAGE; ++k)
+            if (!ctx->ev[k]) cudaEventCreate(&ctx->ev[k]);
+        a.ev = ctx->ev;
+    }
+    e = occk::run_farfield(a, s);
+    ctx->ev_recorded = ctx->timing ? 1 : 0;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_farfield_K launch");
+    ctx->last_prec = prec;
+    ctx->last_nocc = nocc;
+    ctx->last_lmax = L;
+    ctx->last_first_box = first;
+    ctx->last_tree = t;
+    if (Ex_host) {
+        e = cudaMemcpyAsync(Ex_host, a.Ex_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "energy copy");
+    }
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* t, int what, void* out,
+                                        size_t bytes, void* stream) {
+    if (!ctx || !t || !out) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    if (what == OCCK_DBG_PAIR_MULT) {
+        if (t->lmax < 0) return fail(ctx, OCCK_ERR_STATE, "no multipoles");
+        size_t n = (size_t)t->nvals * occk::ncomp(t->lmax);
+        if (bytes != n * 8) return fail(ctx, OCCK_ERR_SHAPE, "size mismatch");
+        e = cudaMemcpy(out, t->dev.pair_vals, bytes, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "copy");
+    }
+    if (what != OCCK_DBG_OBOX && what != OCCK_DBG_MBOX) return fail(ctx, OCCK_ERR_ARG, "bad what");
+    if (ctx->last_tree != t) return fail(ctx, OCCK_ERR_STATE, "last run used another tree");
+    const int nbox = (int)t->parent.size();
+    const int nc = occk::ncomp(ctx->last_lmax);
+    const size_t P = (size_t)ctx->last_nocc * ctx->last_nocc;
+    const size_t n = (size_t)nbox * nc * P;
+    if (bytes != n * 8) return fail(ctx, OCCK_ERR_SHAPE, "size mismatch");
+    std::memset(out, 0, bytes);
+    const size_t nst = (size_t)(nbox - ctx->last_first_box) * nc * P;
+    const void* src = what == OCCK_DBG_OBOX ? ctx->obox.p : ctx->mbox.p;
+    double* dst = (double*)out + (size_t)ctx->last_first_box * nc * P;
+    if (ctx->last_prec == OCCK_FP64) {
+        e = cudaMemcpy(dst, src, nst * 8, cudaMemcpyDeviceToHost);
+    } else {
+        std::vector<float> tmp(nst);
+        e = cudaMemcpy(tmp.data(), src, nst * 4, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < nst; ++i) dst[i] = tmp[i];
+    }
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "copy");
+}
+
+extern "C" occk_status occk_probe_fma_peak(occk_ctx* ctx, int prec, double* flops, void* stream) {
+    if (!ctx || !flops) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device");
+    if (prec != OCCK_FP64 && prec != OCCK_FP32) return fail(ctx, OCCK_ERR_ARG, "prec");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = occk::probe_fma(prec, ctx->sm_count, flops, (cudaStream_t)stream);
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "probe");
+}
+
+extern "C" occk_status occk_set_timing(occk_ctx* ctx, int on) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device");
+    ctx->timing = on ? 1 : 0;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_get_timings(occk_ctx* ctx, float* ms, int n) {
+    if (!ctx || !ms) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (n < OCCK_NSTAGE) return fail(ctx, OCCK_ERR_SHAPE, "n < OCCK_NSTAGE");
+    if (!ctx->ev_recorded) return fail(ctx, OCCK_ERR_STATE, "no timed call recorded");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaEventSynchronize(ctx->ev[OCCK_NSTAGE]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event sync");
+    for (int k = 0; k < OCCK_NSTAGE; ++k) {
+        e = cudaEventElapsedTime(&ms[k], ctx->ev[k], ctx->ev[k + 1]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "elapsed");
+    }
+    return OCCK_OK;
+}

@@ -1,0 +1,160 @@
+// Internal declarations shared by the host ABI layer and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/occk.h"
+
+namespace occk {
+
+// Real form of a rank-L expansion: nc = (L+1)^2 reals, for each l: Re m=0,
+// then (Re, Im) for m = 1..l.
+inline int ncomp(int L) { return (L + 1) * (L + 1); }
+
+// One translation operator to generate: kind 0 = M2M (d = Xc - Xp),
+// 1 = L2L (d = Xc - Xp), 2 = M2L (d = X - X').
+struct OpDesc {
+    double d[3];
+    int kind;
+    int pad;
+};
+
+// Device-side shell data for pair multipoles (one record per kept shell pair).
+struct PairDesc {
+    double A[3], B[3], X[3];   // shell centres and the leaf centre
+    int prim_a, nprim_a;       // offsets into prim arrays
+    int prim_b, nprim_b;
+    int la, lb;
+    int val_off;               // first value row (na*nb rows of nc reals)
+    int pad;
+};
+
+// Workspace buffer that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace occk
+
+struct occk_tree {
+    int device = -1;
+    // ---- host copy -------------------------------------------------------
+    int natom = 0, nshell = 0, nao = 0, depth = 0;
+    double x0[3] = {0, 0, 0};
+    double side = 0;
+    std::vector<double> h;                  // [depth+1]
+    std::vector<int> level_off;             // [depth+2]
+    std::vector<int> box_key;               // [nbox*3]
+    std::vector<int> parent;                // [nbox]
+    std::vector<double> centre;             // [nbox*3]
+    std::vector<int> m2l_tgt, m2l_src;      // sorted by (tgt, src)
+    std::vector<int> pair_a, pair_b, pair_leaf;
+    std::vector<double> pair_centre;        // [npair*3]
+    std::vector<int> leaf_rowoff;           // [nleaf+1]
+    std::vector<int> leaf_aos;              // [nrow]
+    // shells
+    std::vector<double> shell_xyz;          // [nshell*3]
+    std::vector<int> shell_l, shell_prim_off, shell_nprim, shell_ao_off;
+    std::vector<double> prim_exp, prim_coef;  // coef includes primitive and contracted norm
+    // ordered AO-pair entries grouped by (leaf, local row)
+    std::vector<int> row_ptr;               // [nrow+1]
+    std::vector<int> ent_col;               // AO index s
+    std::vector<int> ent_val;               // value row in the pair-multipole array
+    int nvals = 0;                          // rows of pair multipole values
+    // AO -> rows (for the K reduction)
+    std::vector<int> ao_row_ptr;            // [nao+1]
+    std::vector<int> ao_rows;               // row ids
+    // translation schedule
+    std::vector<occk::OpDesc> ops;          // distinct operators
+    std::vector<int> m2l_op;                // per M2L edge
+    std::vector<int> m2m_op;                // per box (child), -1 if none
+    std::vector<int> l2l_op;                // per box (child), -1 if none
+    // per-level CSR for M2M (parents gather children)
+    std::vector<int> child_ptr;             // [nbox+1]
+    std::vector<int> child_list;            // children box ids
+    // M2L CSR by target box, restricted to levels 2..D
+    std::vector<int> m2l_ptr;               // [nbox+1]
+    std::vector<int> edge_lmax;             // per M2L edge (policy 1), empty if unset
+    int lmax = -1;
+
+    // ---- device copy -----------------------------------------------------
+    struct {
+        int* row_ptr = nullptr; int* ent_col = nullptr; int* ent_val = nullptr;
+        int* leaf_rowoff = nullptr; int* leaf_aos = nullptr;
+        int* ao_row_ptr = nullptr; int* ao_rows = nullptr;
+        int* child_ptr = nullptr; int* child_list = nullptr; int* m2m_op = nullptr;
+        int* l2l_op = nullptr;
+        int* m2l_ptr = nullptr; int* m2l_src = nullptr; int* m2l_op = nullptr;
+        int* m2l_lmax_full = nullptr;  // all = lmax
+        int* m2l_lmax_edge = nullptr;  // policy 1
+        int* parent = nullptr;
+        occk::PairDesc* pairs = nullptr;
+        double* prim_exp = nullptr; double* prim_coef = nullptr;
+        double* pair_vals = nullptr;   // [nvals][nc]
+        float* pair_vals_f = nullptr;
+        double* ops = nullptr;         // [nops][nc][nc]
+        float* ops_f = nullptr;
+        occk::OpDesc* opdesc = nullptr;
+    } dev;
+    int nops_alloc_lmax = -1;
+};
+
+struct occk_ctx {
+    int device = -1;
+    std::string err;
+    int sm_count = 0;
+    // workspaces
+    occk::DevBuf ct, w, obox, mbox, kb, part, edev, scratch;
+    // last run (for debug fetch)
+    int last_prec = -1, last_nocc = 0, last_lmax = -1, last_first_box = 0;
+    const occk_tree* last_tree = nullptr;
+    // stage timers
+    int timing = 0;
+    cudaEvent_t ev[OCCK_NSTAGE + 1] = {};
+    int ev_recorded = 0;
+};
+
+namespace occk {
+
+// ----- kernel launchers (kernels_*.cu) ------------------------------------
+cudaError_t launch_gen_ops(const OpDesc* d_desc, int nops, int L, double* d_out, float* d_out_f,
+                           cudaStream_t s);
+cudaError_t launch_pair_multipoles(const PairDesc* d_pairs, int npair, const double* d_exp,
+                                   const double* d_coef, int L, double* d_vals, float* d_vals_f,
+                                   int nvals, cudaStream_t s);
+
+struct FmmArgs {
+    int nao, nocc, ldc, ldk, nc, L, depth;
+    int nbox, first_box;             // boxes [first_box, nbox) are stored
+    int nleaf, leaf0, nrow;
+    const int* level_off;            // host
+    int prec;                        // OCCK_FP64 / OCCK_FP32
+    const double* C;                 // column-major
+    double* K;                       // column-major
+    double* Ex_dev;
+    // tree (device)
+    const int* row_ptr; const int* ent_col; const int* ent_val;
+    const int* leaf_rowoff; const int* leaf_aos;
+    const int* ao_row_ptr; const int* ao_rows;
+    const int* child_ptr; const int* child_list; const int* m2m_op; const int* l2l_op;
+    const int* parent;
+    const int* m2l_ptr; const int* m2l_src; const int* m2l_op; const int* m2l_lmax;
+    const void* pair_vals;           // double or float
+    const void* ops;                 // double or float
+    // workspaces
+    void* ct; void* w; void* obox; void* mbox; double* kb; double* part;
+    const int* leaf_rowoff_host;     // host copy (max rows)
+    int max_rows;
+    cudaEvent_t* ev;                 // OCCK_NSTAGE+1 events or nullptr
+};
+cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
+size_t workspace_elems_w(const FmmArgs& a);
+
+cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s);
+
+}  // namespace occk

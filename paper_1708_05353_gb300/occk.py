@@ -1,0 +1,285 @@
+"""Thin ctypes binding of ``include/occk.h`` (argument marshalling only).
+
+Every function here forwards to the C ABI of ``libocck.so``; no step of the
+far-field exchange runs in Python.  PyTorch supplies device memory and the
+current CUDA stream.  If the shared library is missing the import fails
+loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libocck.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "occk.h")
+
+OCCK_FP64, OCCK_FP32, OCCK_TF32, OCCK_BF16, OCCK_FP16, OCCK_BF16X3, OCCK_FP16X2 = range(7)
+PRECISIONS = {"fp64": OCCK_FP64, "fp32": OCCK_FP32, "tf32": OCCK_TF32, "bf16": OCCK_BF16,
+              "fp16": OCCK_FP16, "bf16x3": OCCK_BF16X3, "fp16x2": OCCK_FP16X2}
+TREE_ARRAYS = {"level_off": 0, "box_key": 1, "parent": 2, "centre": 3, "m2l": 4, "pairs": 5,
+               "pair_centre": 6, "leaf_aos": 7, "leaf_rowoff": 8}
+DBG = {"pair_mult": 0, "obox": 1, "mbox": 2}
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_SHAPE", -3: "ERR_CUDA", -4: "ERR_OOM",
+          -5: "ERR_TIMEOUT", -6: "ERR_UNSUPPORTED", -7: "ERR_STATE"}
+
+
+class OcckError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("natom", ctypes.c_int), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("nshell", ctypes.c_int), ("shell_atom", ctypes.POINTER(ctypes.c_int)),
+                ("shell_l", ctypes.POINTER(ctypes.c_int)), ("shell_nprim", ctypes.POINTER(ctypes.c_int)),
+                ("exps", ctypes.POINTER(ctypes.c_double)), ("coefs", ctypes.POINTER(ctypes.c_double))]
+
+
+class _TreeParams(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int), ("target_atoms_per_leaf", ctypes.c_double),
+                ("ws_boxes", ctypes.c_int), ("pair_thresh", ctypes.c_double)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("nao", ctypes.c_int), ("natom", ctypes.c_int), ("nshell", ctypes.c_int),
+                ("depth", ctypes.c_int), ("nbox", ctypes.c_int), ("nleaf", ctypes.c_int),
+                ("npair", ctypes.c_int), ("nentry", ctypes.c_int), ("nrow", ctypes.c_int),
+                ("nm2l", ctypes.c_int), ("lmax", ctypes.c_int), ("x0", ctypes.c_double * 3),
+                ("side", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["x0"] = list(self.x0)
+        return d
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_SIGS = {
+    "occk_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
+    "occk_destroy": (None, [_vp]),
+    "occk_last_error": (ctypes.c_char_p, [_vp]),
+    "occk_build_tree": (ctypes.c_int, [_vp, ctypes.POINTER(_Basis), ctypes.POINTER(_TreeParams),
+                                       ctypes.POINTER(_vp)]),
+    "occk_tree_destroy": (None, [_vp]),
+    "occk_query": (ctypes.c_int, [_vp, ctypes.POINTER(TreeInfo)]),
+    "occk_tree_export": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t]),
+    "occk_pair_multipoles": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "occk_set_edge_lmax": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "occk_farfield_K": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]),
+    "occk_debug_fetch": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "occk_probe_fma_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
+    "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_get_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+}
+NSTAGE = 7
+STAGES = ["a_half", "a_full", "b_m2m", "c_m2l", "d_l2l", "e_l2p", "reduce"]
+
+
+def header_functions():
+    """Names of the functions declared in include/occk.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(occk_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    ct = ctypes.c_double if dtype == np.float64 else ctypes.c_int
+    return a, a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """occk_ctx: device = -1 gives a host-only context (trees only)."""
+
+    def __init__(self, device: int = 0):
+        self._h = _vp()
+        rc = lib().occk_create(ctypes.byref(self._h), device)
+        if rc != 0:
+            raise OcckError(rc, f"occk_create(device={device})")
+        self.device = device
+
+    def check(self, rc, what):
+        if rc != 0:
+            msg = lib().occk_last_error(self._h)
+            raise OcckError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if self._h:
+            lib().occk_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_timing(self, on: bool):
+        self.check(lib().occk_set_timing(self._h, 1 if on else 0), "occk_set_timing")
+
+    def timings(self) -> dict:
+        ms = (ctypes.c_float * NSTAGE)()
+        self.check(lib().occk_get_timings(self._h, ms, NSTAGE), "occk_get_timings")
+        return dict(zip(STAGES, [float(x) for x in ms]))
+
+    def probe_fma_peak(self, prec="fp64", stream=None) -> float:
+        out = ctypes.c_double()
+        self.check(lib().occk_probe_fma_peak(self._h, PRECISIONS[prec], ctypes.byref(out),
+                                             _stream_ptr(stream)), "occk_probe_fma_peak")
+        return out.value
+
+
+class Tree:
+    """occk_tree built from a ``paper_1708_05353_gb300.inputs.Basis``."""
+
+    def __init__(self, ctx: Context, basis, depth: int = 0, target_atoms_per_leaf: float = 8.0,
+                 pair_thresh: float = 1e-14):
+        self.ctx = ctx
+        keep = []
+        xyz, pxyz = _arr(basis.xyz, np.float64)
+        sa, psa = _arr(basis.shell_atom, np.int32)
+        sl, psl = _arr(basis.shell_l, np.int32)
+        sn, psn = _arr(basis.shell_nprim, np.int32)
+        ex, pex = _arr(basis.exps, np.float64)
+        co, pco = _arr(basis.coefs, np.float64)
+        keep += [xyz, sa, sl, sn, ex, co]
+        b = _Basis(basis.natom, pxyz, basis.nshell, psa, psl, psn, pex, pco)
+        p = _TreeParams(depth, target_atoms_per_leaf, 1, pair_thresh)
+        self._h = _vp()
+        ctx.check(lib().occk_build_tree(ctx._h, ctypes.byref(b), ctypes.byref(p), ctypes.byref(self._h)),
+                  "occk_build_tree")
+
+    def close(self):
+        if self._h:
+            lib().occk_tree_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = TreeInfo()
+        self.ctx.check(lib().occk_query(self._h, ctypes.byref(inf)), "occk_query")
+        return inf.as_dict()
+
+    def export(self, what: str) -> np.ndarray:
+        inf = self.info()
+        shapes = {"level_off": ((inf["depth"] + 2,), np.int32), "box_key": ((inf["nbox"], 3), np.int32),
+                  "parent": ((inf["nbox"],), np.int32), "centre": ((inf["nbox"], 3), np.float64),
+                  "m2l": ((inf["nm2l"], 2), np.int32), "pairs": ((inf["npair"], 3), np.int32),
+                  "pair_centre": ((inf["npair"], 3), np.float64), "leaf_aos": ((inf["nrow"],), np.int32),
+                  "leaf_rowoff": ((inf["nleaf"] + 1,), np.int32)}
+        shape, dt = shapes[what]
+        out = np.zeros(shape, dtype=dt)
+        self.ctx.check(lib().occk_tree_export(self._h, TREE_ARRAYS[what], out.ctypes.data_as(_vp),
+                                              out.nbytes), "occk_tree_export")
+        return out
+
+    def pair_multipoles(self, lmax: int, stream=None):
+        self.ctx.check(lib().occk_pair_multipoles(self.ctx._h, self._h, lmax, _stream_ptr(stream)),
+                       "occk_pair_multipoles")
+
+    def set_edge_lmax(self, ranks):
+        r = np.ascontiguousarray(ranks, dtype=np.int32)
+        self.ctx.check(lib().occk_set_edge_lmax(self.ctx._h, self._h,
+                                                r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(r)),
+                       "occk_set_edge_lmax")
+
+
+def fortran(t):
+    """Column-major view of a 2-D tensor (copy only when needed)."""
+    if t.dim() == 2 and t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def empty_fortran(nrow, ncol, dtype=None, device=None):
+    import torch
+    return torch.empty((ncol, nrow), dtype=dtype or torch.float64, device=device).t()
+
+
+def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K=None, Ex=None,
+               want_energy_host: bool = False, stream=None):
+    """occk_farfield_K on torch CUDA tensors.  C: [nao, nocc] float64 (any
+    layout; a column-major copy is made if needed).  Returns (K, Ex) with K
+    column-major [nao, nocc] and Ex a 0-d device tensor (or a float when
+    want_energy_host)."""
+    import torch
+    C = fortran(C)
+    nao, nocc = C.shape
+    if K is None:
+        K = empty_fortran(nao, nocc, torch.float64, C.device)
+    if Ex is None:
+        Ex = torch.empty((), dtype=torch.float64, device=C.device)
+    eh = ctypes.c_double()
+    rc = lib().occk_farfield_K(ctx._h, tree._h, nocc, _vp(C.data_ptr()), C.stride(1),
+                               PRECISIONS[prec] if isinstance(prec, str) else int(prec), lmax_policy,
+                               _vp(K.data_ptr()), K.stride(1), _vp(Ex.data_ptr()),
+                               ctypes.byref(eh) if want_energy_host else None, _stream_ptr(stream))
+    ctx.check(rc, "occk_farfield_K")
+    return K, (eh.value if want_energy_host else Ex)
+
+
+def debug_fetch(ctx: Context, tree: Tree, what: str, nocc: int = 0, stream=None) -> np.ndarray:
+    inf = tree.info()
+    nc = (inf["lmax"] + 1) ** 2
+    if what == "pair_mult":
+        n = None
+        # number of value rows: sum over kept pairs of na*nb
+        pairs = tree.export("pairs")
+        l = _shell_l_cache.get(id(tree))
+        if l is None:
+            raise ValueError("call debug_fetch_pair_mult with shell_l")
+        n = int(sum((3 if l[a] else 1) * (3 if l[b] else 1) for a, b, _ in pairs))
+        out = np.zeros((n, nc))
+    else:
+        out = np.zeros((inf["nbox"], nc, nocc * nocc))
+    ctx.check(lib().occk_debug_fetch(ctx._h, tree._h, DBG[what], out.ctypes.data_as(_vp), out.nbytes,
+                                     _stream_ptr(stream)), "occk_debug_fetch")
+    return out
+
+
+_shell_l_cache = {}
+
+
+def debug_fetch_pair_mult(ctx: Context, tree: Tree, shell_l, stream=None) -> np.ndarray:
+    _shell_l_cache[id(tree)] = np.asarray(shell_l)
+    try:
+        return debug_fetch(ctx, tree, "pair_mult", stream=stream)
+    finally:
+        _shell_l_cache.pop(id(tree), None)
