@@ -87,7 +87,7 @@ typedef enum {
     OCCK_BF16 = 3,     /* (a),(c),(e) on tensor cores, BF16 inputs, FP32 accumulate */
     OCCK_FP16 = 4,     /* (a),(c),(e) on tensor cores, FP16 inputs, FP32 accumulate */
     OCCK_BF16X3 = 5,   /* BF16 hi/lo split, three products (hi*hi + hi*lo + lo*hi) */
-    OCCK_FP16X2 = 6    /* FP16 hi/lo split of one operand, two products */
+    OCCK_FP16X3 = 6    /* FP16 hi/lo split of both operands, three products */
 } occk_precision;
 
 typedef struct {
@@ -191,6 +191,30 @@ occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tree, int nocc,
 enum { OCCK_DBG_PAIR_MULT = 0, OCCK_DBG_OBOX = 1, OCCK_DBG_MBOX = 2 };
 occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* tree, int what,
                              void* host_out, size_t bytes, void* stream);
+
+/* Exchange energy E = -1/2 sum_ri C_ri K_ri from caller buffers, allocating
+ * no device memory.  The paper has no counterpart: this entry exists for
+ * callers that cannot let a library call cudaMalloc -- an application whose
+ * own allocator owns all device memory (a framework caching allocator or a
+ * fixed pool), or a latency-sensitive loop in which an allocation would
+ * synchronise the device.  It computes the same reduction as the energy of
+ * occk_farfield_K (FP64), with its scratch (one double per occupied column)
+ * in a file-scope __device__ array of OCCK_NOALLOC_MAX_OCC doubles (64 KB)
+ * that every GPU loading the library holds until the process exits.
+ *   C_dev [nao x nocc] column-major FP64 device, ldc >= nao
+ *   K_dev [nao x nocc] column-major FP64 device, ldk >= nao (e.g. the K of
+ *         occk_farfield_K)
+ *   E_dev FP64 device scalar output, written on `stream`
+ * nocc > OCCK_NOALLOC_MAX_OCC fails with OCCK_ERR_SHAPE (and a message in
+ * occk_last_error(ctx)); no cudaMalloc, cudaFree or allocating library call is
+ * made.  The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array and each
+ * overwrites it: calls that overlap on the GPU race and must be ordered by
+ * the caller (e.g. one stream). */
+#define OCCK_NOALLOC_MAX_OCC 8192
+occk_status occk_exchange_energy_noalloc(occk_ctx* ctx, int nao, int nocc, const double* C_dev, int ldc,
+                                         const double* K_dev, int ldk, double* E_dev, void* stream);
 
 /* Opt-in stage timers (CUDA events recorded on the call's stream between
  * stages).  on != 0 enables them for later occk_farfield_K calls on this

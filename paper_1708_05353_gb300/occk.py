@@ -17,9 +17,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libocck.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "occk.h")
 
-OCCK_FP64, OCCK_FP32, OCCK_TF32, OCCK_BF16, OCCK_FP16, OCCK_BF16X3, OCCK_FP16X2 = range(7)
+OCCK_FP64, OCCK_FP32, OCCK_TF32, OCCK_BF16, OCCK_FP16, OCCK_BF16X3, OCCK_FP16X3 = range(7)
 PRECISIONS = {"fp64": OCCK_FP64, "fp32": OCCK_FP32, "tf32": OCCK_TF32, "bf16": OCCK_BF16,
-              "fp16": OCCK_FP16, "bf16x3": OCCK_BF16X3, "fp16x2": OCCK_FP16X2}
+              "fp16": OCCK_FP16, "bf16x3": OCCK_BF16X3, "fp16x3": OCCK_FP16X3}
 TREE_ARRAYS = {"level_off": 0, "box_key": 1, "parent": 2, "centre": 3, "m2l": 4, "pairs": 5,
                "pair_centre": 6, "leaf_aos": 7, "leaf_rowoff": 8}
 DBG = {"pair_mult": 0, "obox": 1, "mbox": 2}
@@ -76,6 +76,8 @@ _SIGS = {
     "occk_debug_fetch": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "occk_probe_fma_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_exchange_energy_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                                    ctypes.c_int, _vp, _vp]),
     "occk_get_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
 }
 NSTAGE = 7
@@ -223,9 +225,15 @@ class Tree:
 
 def fortran(t):
     """Column-major view of a 2-D tensor (copy only when needed)."""
-    if t.dim() == 2 and t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+    if t.dim() == 2 and (t.stride(0) == 1 or t.shape[0] == 1) and ld(t) >= max(1, t.shape[0]):
         return t
     return t.t().contiguous().t()
+
+
+def ld(t):
+    """Leading dimension of a column-major 2-D tensor (a single column has
+    no meaningful column stride; use the row count)."""
+    return t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])
 
 
 def empty_fortran(nrow, ncol, dtype=None, device=None):
@@ -247,12 +255,29 @@ def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K
     if Ex is None:
         Ex = torch.empty((), dtype=torch.float64, device=C.device)
     eh = ctypes.c_double()
-    rc = lib().occk_farfield_K(ctx._h, tree._h, nocc, _vp(C.data_ptr()), C.stride(1),
+    rc = lib().occk_farfield_K(ctx._h, tree._h, nocc, _vp(C.data_ptr()), ld(C),
                                PRECISIONS[prec] if isinstance(prec, str) else int(prec), lmax_policy,
-                               _vp(K.data_ptr()), K.stride(1), _vp(Ex.data_ptr()),
+                               _vp(K.data_ptr()), ld(K), _vp(Ex.data_ptr()),
                                ctypes.byref(eh) if want_energy_host else None, _stream_ptr(stream))
     ctx.check(rc, "occk_farfield_K")
     return K, (eh.value if want_energy_host else Ex)
+
+
+def exchange_energy_noalloc(ctx: Context, C, K, E=None, stream=None):
+    """occk_exchange_energy_noalloc on column-major torch CUDA tensors: the
+    energy -1/2 sum C*K with its scratch in a static device array (the
+    library allocates no device memory in this call).  Returns E (0-d device
+    tensor; allocate it yourself and pass it in to avoid torch allocating)."""
+    import torch
+    C = fortran(C)
+    K = fortran(K)
+    nao, nocc = C.shape
+    if E is None:
+        E = torch.empty((), dtype=torch.float64, device=C.device)
+    ctx.check(lib().occk_exchange_energy_noalloc(ctx._h, nao, nocc, _vp(C.data_ptr()), ld(C),
+                                                 _vp(K.data_ptr()), ld(K), _vp(E.data_ptr()),
+                                                 _stream_ptr(stream)), "occk_exchange_energy_noalloc")
+    return E
 
 
 def debug_fetch(ctx: Context, tree: Tree, what: str, nocc: int = 0, stream=None) -> np.ndarray:
