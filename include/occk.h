@@ -227,6 +227,17 @@ occk_status occk_exchange_energy_noalloc(occk_ctx* ctx, int nao, int nocc, const
 occk_status occk_set_timing(occk_ctx* ctx, int on);
 occk_status occk_get_timings(occk_ctx* ctx, float* ms, int n);
 
+/* Reads the device error word of the last occk_farfield_K on this context
+ * (synchronises `stream`).  Returns OCCK_ERR_TIMEOUT if a bounded wait inside
+ * a tensor-core kernel gave up (its results are then invalid), else OK. */
+occk_status occk_device_status(occk_ctx* ctx, void* stream);
+
+/* D = A B^T on the tensor-core engine used by the mixed forms, for checking
+ * it: A [M x K], B [N x K], D [M x N], all FP32 row-major device buffers; prec
+ * one of OCCK_TF32, _BF16, _FP16, _BF16X3, _FP16X3.  Synchronises `stream`. */
+occk_status occk_debug_tc_gemm(occk_ctx* ctx, int prec, int M, int N, int K, const float* A,
+                               const float* B, float* D, void* stream);
+
 /* Sustained FMA throughput of this device for one arithmetic (prec =
  * OCCK_FP64 or OCCK_FP32), measured by a dependent-chain FMA kernel over all
  * SMs; *flops receives FLOP/s (2 per FMA).  Synchronises `stream`.  A

@@ -65,7 +65,7 @@ void free_tree_device(occk_tree* t) {
     dfree(d.m2l_lmax_full); dfree(d.m2l_lmax_edge); dfree(d.parent);
     dfree(d.pairs); dfree(d.prim_exp); dfree(d.prim_coef);
     dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.opdesc);
-    dfree(d.l2l_op);
+    dfree(d.l2l_op); dfree(d.lscale); dfree(d.box_scale);
 }
 
 inline long long ifloor_clamp(double v, long long n) {
@@ -613,6 +613,23 @@ extern "C" occk_status occk_pair_multipoles(occk_ctx* ctx, occk_tree* t, int lma
         return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "pair multipole storage")
                                               : cuda_fail(ctx, e, "occk_pair_multipoles alloc");
     }
+    {
+        // per-level scale factors for the low-precision forms
+        std::vector<float> ls(nc), bsc(t->parent.size());
+        const double sl = t->h[t->depth];
+        for (int l = 0; l <= lmax; ++l)
+            for (int c = l * l; c < (l + 1) * (l + 1); ++c) ls[c] = (float)std::pow(sl, -l);
+        for (size_t b = 0; b < bsc.size(); ++b) {
+            int lev = 0;
+            while (lev + 1 < (int)t->level_off.size() && t->level_off[lev + 1] <= (int)b) ++lev;
+            bsc[b] = (float)t->h[lev];
+        }
+        dfree(d.lscale);
+        dfree(d.box_scale);
+        if (e == cudaSuccess) e = upload(&d.lscale, ls);
+        if (e == cudaSuccess) e = upload(&d.box_scale, bsc);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scale upload");
+    }
     e = occk::launch_pair_multipoles(d.pairs, (int)t->pair_a.size(), d.prim_exp, d.prim_coef, lmax,
                                      d.pair_vals, d.pair_vals_f, t->nvals, s);
     if (e == cudaSuccess && nops > 0) e = occk::launch_gen_ops(d.opdesc, nops, lmax, d.ops, d.ops_f, s);
@@ -652,8 +669,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     if (t->lmax < 0) return fail(ctx, OCCK_ERR_STATE, "call occk_pair_multipoles first");
     if (nocc <= 0 || !C_dev || !K_dev) return fail(ctx, OCCK_ERR_ARG, "nocc <= 0 or null C/K");
     if (ldc < t->nao || ldk < t->nao) return fail(ctx, OCCK_ERR_SHAPE, "ldc/ldk < nao");
-    if (prec != OCCK_FP64 && prec != OCCK_FP32)
-        return fail(ctx, OCCK_ERR_UNSUPPORTED, "precision not available in this build");
+    if (prec < OCCK_FP64 || prec > OCCK_FP16X3) return fail(ctx, OCCK_ERR_ARG, "unknown precision");
     if (lmax_policy != 0 && lmax_policy != 1) return fail(ctx, OCCK_ERR_ARG, "lmax_policy must be 0 or 1");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -681,7 +697,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         (e = ensure(ctx->mbox, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
         (e = ensure(ctx->kb, bytes_kb)) != cudaSuccess ||
         (e = ensure(ctx->part, bytes_part)) != cudaSuccess ||
-        (e = ensure(ctx->edev, 8)) != cudaSuccess) {
+        (e = ensure(ctx->edev, 8)) != cudaSuccess ||
+        (e = ensure(ctx->scratch, 256)) != cudaSuccess) {
         return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "far-field workspaces")
                                               : cuda_fail(ctx, e, "workspace allocation");
     }
@@ -705,6 +722,11 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.kb = (double*)ctx->kb.p; a.part = (double*)ctx->part.p;
     a.leaf_rowoff_host = t->leaf_rowoff.data();
     a.max_rows = max_rows;
+    a.lscale = d.lscale;
+    a.box_scale = d.box_scale;
+    a.err_word = (int*)ctx->scratch.p;
+    e = cudaMemsetAsync(a.err_word, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error word");
     a.ev = nullptr;
     if (ctx->timing) {
         for (int k = 0; k <= OCCK_NSTAGE; ++k)
@@ -720,9 +742,12 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     ctx->last_first_box = first;
     ctx->last_tree = t;
     if (Ex_host) {
+        int werr = 0;
         e = cudaMemcpyAsync(Ex_host, a.Ex_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&werr, a.err_word, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "energy copy");
+        if (werr) return fail(ctx, OCCK_ERR_TIMEOUT, "a tensor-core wait gave up; results are invalid");
     }
     return OCCK_OK;
 }
@@ -791,4 +816,33 @@ extern "C" occk_status occk_get_timings(occk_ctx* ctx, float* ms, int n) {
         if (e != cudaSuccess) return cuda_fail(ctx, e, "elapsed");
     }
     return OCCK_OK;
+}
+
+extern "C" occk_status occk_device_status(occk_ctx* ctx, void* stream) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (ctx->device < 0 || !ctx->scratch.p) return OCCK_OK;
+    cudaSetDevice(ctx->device);
+    int werr = 0;
+    cudaError_t e = cudaMemcpyAsync(&werr, ctx->scratch.p, sizeof(int), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_device_status");
+    if (werr) return fail(ctx, OCCK_ERR_TIMEOUT, "a tensor-core wait gave up in the last call");
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_debug_tc_gemm(occk_ctx* ctx, int prec, int M, int N, int K, const float* A,
+                                          const float* B, float* D, void* stream) {
+    if (!ctx || !A || !B || !D) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device");
+    if (occk::tc_mode(prec) < 0) return fail(ctx, OCCK_ERR_ARG, "not a tensor-core precision");
+    if (M <= 0 || N <= 0 || K <= 0) return fail(ctx, OCCK_ERR_ARG, "sizes must be positive");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = ensure(ctx->scratch, 256);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch");
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(ctx->scratch.p, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = occk::tc_gemm(prec, M, N, K, A, B, D, (int*)ctx->scratch.p, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_debug_tc_gemm");
+    return occk_device_status(ctx, stream);
 }

@@ -391,8 +391,13 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         k_half<T, LMC><<<g, 128, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W);
     }
     const int leaf_store0 = a.leaf0 - a.first_box;
+    const bool tcm = sizeof(T) == 4 && tc_mode(a.prec) >= 0;
     mark(1);
-    if constexpr (sizeof(T) == 8) {
+    if (tcm) {
+        cudaError_t e2 = tc_run_a2(a.prec, a.leaf_rowoff, a.leaf_aos, (const float*)Ct, (const float*)W, nocc,
+                                   a.nrow, nc, a.nleaf, leaf_store0, a.lscale, (float*)Ob, a.err_word, s);
+        if (e2 != cudaSuccess) return e2;
+    } else if constexpr (sizeof(T) == 8) {
         constexpr int BM = 64, BK = 8, TM = 4;
         int nt = (nocc + BM - 1) / BM;
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
@@ -420,7 +425,13 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (c) M2L: every box of levels 2..D, all levels in one launch
     mark(3);
-    {
+    if (tcm && nc <= 128) {
+        int t0 = a.level_off[2], nt = a.nbox - t0;
+        cudaError_t e2 = tc_run_m2l(a.prec, (int)P, nc, a.L, a.first_box, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op,
+                                    a.m2l_lmax, (const float*)ops, (const float*)Ob, (float*)Mb, a.box_scale,
+                                    a.err_word, s);
+        if (e2 != cudaSuccess) return e2;
+    } else {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         dim3 g(pblocks, nt, nchunk);
         k_translate<T, LMC><<<g, 128, 0, s>>>(1, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
@@ -436,7 +447,11 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (e) L2P
     mark(5);
-    if constexpr (sizeof(T) == 8) {
+    if (tcm) {
+        cudaError_t e2 = tc_run_l2p(a.prec, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
+                                    a.nleaf, leaf_store0, a.max_rows, a.lscale, a.kb, a.err_word, s);
+        if (e2 != cudaSuccess) return e2;
+    } else if constexpr (sizeof(T) == 8) {
         constexpr int BM = 64, BK = 8, TM = 4;
         dim3 g((a.max_rows + BM - 1) / BM, (nocc + BM - 1) / BM, a.nleaf);
         k_l2p<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, W, Mb, nocc, a.nrow, nc,

@@ -100,6 +100,8 @@ struct occk_tree {
         double* ops = nullptr;         // [nops][nc][nc]
         float* ops_f = nullptr;
         occk::OpDesc* opdesc = nullptr;
+        float* lscale = nullptr;       // [nc] 1/s_leaf^l
+        float* box_scale = nullptr;    // [nbox]
     } dev;
     int nops_alloc_lmax = -1;
 };
@@ -151,10 +153,28 @@ struct FmmArgs {
     const int* leaf_rowoff_host;     // host copy (max rows)
     int max_rows;
     cudaEvent_t* ev;                 // OCCK_NSTAGE+1 events or nullptr
+    // tensor-core forms
+    const float* lscale;             // [nc] 1/s_leaf^l
+    const float* box_scale;          // [nbox] side of each box's level
+    int* err_word;                   // device error word (bounded waits)
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
 size_t workspace_elems_w(const FmmArgs& a);
 
 cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s);
+
+// ----- tensor-core steps (kernels_tc.cu) ------------------------------------
+int tc_mode(int prec);
+cudaError_t tc_gemm(int prec, int M, int N, int K, const float* A, const float* B, float* D, int* err,
+                    cudaStream_t s);
+cudaError_t tc_run_a2(int prec, const int* leaf_rowoff, const int* leaf_aos, const float* Ct, const float* W,
+                      int nocc, int nrow, int nc, int nleaf, int leaf_store0, const float* lscale, float* Obox,
+                      int* err, cudaStream_t s);
+cudaError_t tc_run_l2p(int prec, const int* leaf_rowoff, const float* W, const float* Mbox, int nocc, int nrow,
+                       int nc, int nleaf, int leaf_store0, int max_rows, const float* lscale, double* KB,
+                       int* err, cudaStream_t s);
+cudaError_t tc_run_m2l(int prec, int P, int nc, int L, int first_box, int tgt0, int ntgt, const int* ptr,
+                       const int* src, const int* op, const int* lmax_e, const float* ops, const float* O,
+                       float* M, const float* box_scale, int* err, cudaStream_t s);
 
 }  // namespace occk

@@ -76,6 +76,9 @@ _SIGS = {
     "occk_debug_fetch": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "occk_probe_fma_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_device_status": (ctypes.c_int, [_vp, _vp]),
+    "occk_debug_tc_gemm": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                          _vp, _vp]),
     "occk_exchange_energy_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
                                                     ctypes.c_int, _vp, _vp]),
     "occk_get_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
@@ -261,6 +264,22 @@ def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K
                                ctypes.byref(eh) if want_energy_host else None, _stream_ptr(stream))
     ctx.check(rc, "occk_farfield_K")
     return K, (eh.value if want_energy_host else Ex)
+
+
+def debug_tc_gemm(ctx: Context, prec: str, A, B, stream=None):
+    """D = A B^T on the tensor-core engine (A [M,K], B [N,K] float32 CUDA)."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    D = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float32, device=A.device)
+    ctx.check(lib().occk_debug_tc_gemm(ctx._h, PRECISIONS[prec], A.shape[0], B.shape[0], A.shape[1],
+                                       _vp(A.data_ptr()), _vp(B.data_ptr()), _vp(D.data_ptr()),
+                                       _stream_ptr(stream)), "occk_debug_tc_gemm")
+    return D
+
+
+def device_status(ctx: Context, stream=None):
+    ctx.check(lib().occk_device_status(ctx._h, _stream_ptr(stream)), "occk_device_status")
 
 
 def exchange_energy_noalloc(ctx: Context, C, K, E=None, stream=None):
