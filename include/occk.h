@@ -170,7 +170,11 @@ occk_status occk_set_edge_lmax(occk_ctx* ctx, occk_tree* tree, const int* ranks,
  *          `stream` before returning (do not pass it during graph capture)
  *   prec   arithmetic of the contractions (occk_precision)
  *   lmax_policy 0 = the tree's lmax on every edge; 1 = per-edge ranks from
- *          occk_set_edge_lmax (falls back to 0 when none were set)
+ *          occk_set_edge_lmax (falls back to 0 when none were set); 2 =
+ *          learned: after M2M the edge features feed the MLP (FP16) and the
+ *          ranks are chosen on the device for the budget of
+ *          occk_set_learned_tau (falls back to 0 without a model or when the
+ *          tree's lmax < 2)
  * Requires occk_pair_multipoles on this tree.  Workspaces are owned by the
  * context and grow on demand (allocation happens outside any timed loop on
  * the first call with a given shape). */
@@ -226,6 +230,54 @@ occk_status occk_exchange_energy_noalloc(occk_ctx* ctx, int nao, int nocc, const
 #define OCCK_NSTAGE 7
 occk_status occk_set_timing(occk_ctx* ctx, int on);
 occk_status occk_get_timings(occk_ctx* ctx, float* ms, int n);
+
+/* ---- Learned per-edge multipole rank (an addition to the paper's method) --
+ * A 3-layer MLP (OCCK_MLP_NIN -> 64 -> 64 -> OCCK_MLP_NOUT, ReLU) maps the
+ * features of an M2L edge to the predicted log10 |e_edge(L) - e_edge(10)| (Eh)
+ * of that edge's far-field energy for L = 2..9.  The network lives in the
+ * context: FP32 parameters (row-major W1 [NIN x 64], b1, W2 [64 x 64], b2,
+ * W3 [64 x NOUT], b3) and a normalisation vector [mean_x (NIN), std_x (NIN),
+ * mean_y (NOUT), std_y (NOUT)]: inputs are standardised, outputs are
+ * predicted standardised and mapped back.  Training is full-batch Adam on the
+ * mean squared error of the standardised outputs; inference is FP16. */
+#define OCCK_MLP_NIN 16
+#define OCCK_MLP_HIDDEN 64
+#define OCCK_MLP_NOUT 8
+#define OCCK_MLP_NPARAM (OCCK_MLP_NIN * 64 + 64 + 64 * 64 + 64 + 64 * OCCK_MLP_NOUT + OCCK_MLP_NOUT)
+#define OCCK_MLP_NNORM (2 * OCCK_MLP_NIN + 2 * OCCK_MLP_NOUT)
+/* He-uniform weights from a host generator seeded by `seed`, zero biases,
+ * identity normalisation; resets the Adam state. */
+occk_status occk_mlp_init(occk_ctx* ctx, uint64_t seed);
+/* Copy parameters / normalisation in (set) or out (get); host arrays of
+ * OCCK_MLP_NPARAM and OCCK_MLP_NNORM floats.  set marks the model usable. */
+occk_status occk_mlp_set(occk_ctx* ctx, const float* params, const float* norm);
+occk_status occk_mlp_get(occk_ctx* ctx, float* params, float* norm);
+/* `steps` full-batch Adam steps (learning rate lr) on X_dev [n x NIN] raw
+ * features and T_dev [n x NOUT] standardised targets (device FP32);
+ * *loss_host (nullable) receives the loss before the last step.  Synchronises. */
+occk_status occk_mlp_train(occk_ctx* ctx, const float* X_dev, const float* T_dev, int n, int steps,
+                           float lr, float* loss_host, void* stream);
+/* Loss and its gradient with respect to the parameters (grad_dev: device
+ * FP32 [OCCK_MLP_NPARAM]), without updating anything.  Synchronises. */
+occk_status occk_mlp_grad(occk_ctx* ctx, const float* X_dev, const float* T_dev, int n, float* grad_dev,
+                          float* loss_host, void* stream);
+/* FP16 inference: Y_dev [n x NOUT] = predicted log10 errors (de-standardised). */
+occk_status occk_mlp_predict(occk_ctx* ctx, const float* X_dev, int n, float* Y_dev, void* stream);
+/* Features [nm2l x NIN] of every M2L edge from the occupied multipoles of the
+ * last occk_farfield_K on this context and tree: level/depth, |R|/h, sorted
+ * |R_k|/|R|, log10 h, log10(norm_l / h^l) of target and source for l = 0, 2,
+ * 4, 6, 8, clamped to the rank (norm_l = 2-norm over m and all occupied
+ * pairs). */
+occk_status occk_edge_features(occk_ctx* ctx, const occk_tree* tree, float* F_dev, void* stream);
+/* Training labels: E_dev [nm2l x (lmax+1)] = energy of each M2L edge with its
+ * operator truncated to ranks 0..lmax, from the last occk_farfield_K (run with
+ * lmax_policy 0); exact splitting because M2M and L2L re-expand exactly. */
+occk_status occk_edge_energies(occk_ctx* ctx, const occk_tree* tree, double* E_dev, void* stream);
+/* Error budget tau (Eh) of lmax_policy 2: ranks minimise sum_e (L_e+1)^4
+ * subject to sum_e predicted err_e(L_e) <= tau.  Default 1e-6. */
+occk_status occk_set_learned_tau(occk_ctx* ctx, double tau);
+/* Ranks chosen by the last lmax_policy 2 call (host int [nm2l]). */
+occk_status occk_get_edge_ranks(occk_ctx* ctx, const occk_tree* tree, int* ranks, int n);
 
 /* Reads the device error word of the last occk_farfield_K on this context
  * (synchronises `stream`).  Returns OCCK_ERR_TIMEOUT if a bounded wait inside

@@ -79,8 +79,11 @@ def full_transform(tree, W, C, i_cols):
 
 
 def farfield(system_or_basis, C=None, L=None, tree=None, i_subset=None,
-             lmax_edges=None, pair_thresh=1e-14, return_parts=False):
-    """Far-field K^ff (n_AO x |I|) and E^ff for the columns in ``i_subset``."""
+             lmax_edges=None, pair_thresh=1e-14, return_parts=False, Opair=None, W=None):
+    """Far-field K^ff (n_AO x |I|) and E^ff for the columns in ``i_subset``.
+
+    ``Opair`` / ``W`` may carry step 0 and the first half of step 1 from an
+    earlier call on the same tree, rank and C (they do not depend on I)."""
     if hasattr(system_or_basis, "basis"):
         sysm = system_or_basis
         basis, C = sysm.basis, sysm.C if C is None else C
@@ -99,8 +102,10 @@ def farfield(system_or_basis, C=None, L=None, tree=None, i_subset=None,
     nbox = tree["nbox"]
     lo_leaf = tree["level_off"][D]
 
-    Opair = pair_multipoles(basis, tree, L)
-    W = half_transform(basis, tree, Opair, C, L)
+    if Opair is None:
+        Opair = pair_multipoles(basis, tree, L)
+    if W is None:
+        W = half_transform(basis, tree, Opair, C, L)
     Oleaf = full_transform(tree, W, C, i_cols)
 
     # multipoles O^{ij} of every box, [nbox, nlm, |I|, nocc]

@@ -66,6 +66,7 @@ void free_tree_device(occk_tree* t) {
     dfree(d.pairs); dfree(d.prim_exp); dfree(d.prim_coef);
     dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.opdesc);
     dfree(d.l2l_op); dfree(d.lscale); dfree(d.box_scale);
+    dfree(d.box_key); dfree(d.box_level); dfree(d.hlev); dfree(d.m2l_tgt);
 }
 
 inline long long ifloor_clamp(double v, long long n) {
@@ -113,7 +114,8 @@ extern "C" void occk_destroy(occk_ctx* c) {
         for (int k = 0; k <= OCCK_NSTAGE; ++k)
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         for (occk::DevBuf* b : {&c->ct, &c->w, &c->obox, &c->mbox, &c->kb, &c->part, &c->edev,
-                                &c->scratch}) {
+                                &c->scratch, &c->mlp_prm, &c->mlp_norm, &c->mlp_m, &c->mlp_v, &c->mlp_h,
+                                &c->mlp_grad, &c->mlp_ws, &c->feat, &c->pred, &c->ranks, &c->nrm, &c->gram}) {
             if (b->p) cudaFree(b->p);
             b->p = nullptr;
         }
@@ -517,6 +519,10 @@ extern "C" occk_status occk_build_tree(occk_ctx* ctx, const occk_basis* bs,
         if (e == cudaSuccess) e = upload(&d.prim_coef, t->prim_coef);
         if (e == cudaSuccess) e = upload(&d.opdesc, t->ops);
         if (e == cudaSuccess) e = upload(&d.m2l_lmax_full, lmfull);
+        if (e == cudaSuccess) e = upload(&d.box_key, t->box_key);
+        if (e == cudaSuccess) e = upload(&d.box_level, level);
+        if (e == cudaSuccess) e = upload(&d.hlev, t->h);
+        if (e == cudaSuccess) e = upload(&d.m2l_tgt, t->m2l_tgt);
         if (e != cudaSuccess) {
             free_tree_device(t);
             delete t;
@@ -670,7 +676,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     if (nocc <= 0 || !C_dev || !K_dev) return fail(ctx, OCCK_ERR_ARG, "nocc <= 0 or null C/K");
     if (ldc < t->nao || ldk < t->nao) return fail(ctx, OCCK_ERR_SHAPE, "ldc/ldk < nao");
     if (prec < OCCK_FP64 || prec > OCCK_FP16X3) return fail(ctx, OCCK_ERR_ARG, "unknown precision");
-    if (lmax_policy != 0 && lmax_policy != 1) return fail(ctx, OCCK_ERR_ARG, "lmax_policy must be 0 or 1");
+    if (lmax_policy < 0 || lmax_policy > 2) return fail(ctx, OCCK_ERR_ARG, "lmax_policy must be 0, 1 or 2");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
@@ -722,6 +728,31 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.kb = (double*)ctx->kb.p; a.part = (double*)ctx->part.p;
     a.leaf_rowoff_host = t->leaf_rowoff.data();
     a.max_rows = max_rows;
+    a.learned = 0;
+    ctx->ranks_valid = 0;
+    const int nm2l = (int)t->m2l_tgt.size();
+    if (lmax_policy == 2 && ctx->mlp_ready && L >= 2 && nm2l > 0) {
+        if ((e = ensure(ctx->feat, sizeof(float) * (size_t)nm2l * OCCK_MLP_NIN)) != cudaSuccess ||
+            (e = ensure(ctx->pred, sizeof(float) * (size_t)nm2l * OCCK_MLP_NOUT)) != cudaSuccess ||
+            (e = ensure(ctx->ranks, sizeof(int) * (size_t)nm2l)) != cudaSuccess ||
+            (e = ensure(ctx->nrm, sizeof(double) * (size_t)nbox * (L + 1))) != cudaSuccess)
+            return cuda_fail(ctx, e, "selector workspace");
+        a.learned = 1;
+        a.mlp_prm = (const float*)ctx->mlp_prm.p;
+        a.mlp_h = ctx->mlp_h.p;
+        a.mlp_norm = (const float*)ctx->mlp_norm.p;
+        a.feat = (float*)ctx->feat.p;
+        a.pred = (float*)ctx->pred.p;
+        a.ranks = (int*)ctx->ranks.p;
+        a.nrm = (double*)ctx->nrm.p;
+        a.tau = ctx->tau;
+        a.nm2l = nm2l;
+        a.m2l_tgt = d.m2l_tgt;
+        a.box_key = d.box_key;
+        a.box_level = d.box_level;
+        a.hlev = d.hlev;
+        ctx->ranks_valid = 1;
+    }
     a.lscale = d.lscale;
     a.box_scale = d.box_scale;
     a.err_word = (int*)ctx->scratch.p;
@@ -845,4 +876,232 @@ extern "C" occk_status occk_debug_tc_gemm(occk_ctx* ctx, int prec, int M, int N,
     if (e == cudaSuccess) e = occk::tc_gemm(prec, M, N, K, A, B, D, (int*)ctx->scratch.p, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_debug_tc_gemm");
     return occk_device_status(ctx, stream);
+}
+
+// ===========================================================================
+// Learned rank selector
+// ===========================================================================
+
+namespace {
+
+occk_status mlp_alloc(occk_ctx* ctx) {
+    const size_t np = (size_t)OCCK_MLP_NPARAM;
+    cudaError_t e;
+    if ((e = ensure(ctx->mlp_prm, 4 * np)) != cudaSuccess || (e = ensure(ctx->mlp_m, 4 * np)) != cudaSuccess ||
+        (e = ensure(ctx->mlp_v, 4 * np)) != cudaSuccess || (e = ensure(ctx->mlp_h, 2 * np)) != cudaSuccess ||
+        (e = ensure(ctx->mlp_grad, 4 * np)) != cudaSuccess ||
+        (e = ensure(ctx->mlp_norm, 4 * (size_t)OCCK_MLP_NNORM)) != cudaSuccess)
+        return cuda_fail(ctx, e, "MLP storage");
+    return OCCK_OK;
+}
+
+struct MlpWs {
+    float *Xn, *Z1, *Z2, *Y, *dY, *dZ1, *dZ2;
+    double* part;
+};
+
+occk_status mlp_workspace(occk_ctx* ctx, int n, MlpWs* w) {
+    const size_t N = (size_t)n;
+    const size_t nfl = N * (OCCK_MLP_NIN + 4 * OCCK_MLP_HIDDEN + 2 * OCCK_MLP_NOUT);
+    cudaError_t e = ensure(ctx->mlp_ws, nfl * 4 + 8 * 256 + 256);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "MLP workspace");
+    float* f = (float*)ctx->mlp_ws.p;
+    w->Xn = f; f += N * OCCK_MLP_NIN;
+    w->Z1 = f; f += N * OCCK_MLP_HIDDEN;
+    w->Z2 = f; f += N * OCCK_MLP_HIDDEN;
+    w->dZ1 = f; f += N * OCCK_MLP_HIDDEN;
+    w->dZ2 = f; f += N * OCCK_MLP_HIDDEN;
+    w->Y = f; f += N * OCCK_MLP_NOUT;
+    w->dY = f; f += N * OCCK_MLP_NOUT;
+    uintptr_t u = ((uintptr_t)f + 255) & ~(uintptr_t)255;
+    w->part = (double*)u;
+    return OCCK_OK;
+}
+
+double host_loss(const double* part, int n) {
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    return s;
+}
+
+}  // namespace
+
+extern "C" occk_status occk_mlp_init(occk_ctx* ctx, uint64_t seed) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device");
+    if (occk::mlp_nparams() != OCCK_MLP_NPARAM) return fail(ctx, OCCK_ERR_STATE, "MLP size mismatch");
+    cudaSetDevice(ctx->device);
+    occk_status st = mlp_alloc(ctx);
+    if (st) return st;
+    std::vector<float> p(OCCK_MLP_NPARAM, 0.f), nrm(OCCK_MLP_NNORM, 0.f);
+    uint64_t x = seed ? seed : 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {   // splitmix64
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto fill = [&](int off, int fan_in, int count) {
+        const double lim = std::sqrt(6.0 / fan_in);
+        for (int k = 0; k < count; ++k) {
+            double u = (double)(next() >> 11) / 9007199254740992.0;
+            p[off + k] = (float)((2.0 * u - 1.0) * lim);
+        }
+    };
+    const int NIN = OCCK_MLP_NIN, H = OCCK_MLP_HIDDEN, NO = OCCK_MLP_NOUT;
+    fill(0, NIN, NIN * H);
+    fill(NIN * H + H, H, H * H);
+    fill(NIN * H + H + H * H + H, H, H * NO);
+    for (int i = 0; i < NIN; ++i) nrm[NIN + i] = 1.f;
+    for (int k = 0; k < NO; ++k) nrm[2 * NIN + NO + k] = 1.f;
+    cudaError_t e = cudaMemcpy(ctx->mlp_prm.p, p.data(), 4 * p.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->mlp_norm.p, nrm.data(), 4 * nrm.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_m.p, 0, 4 * (size_t)OCCK_MLP_NPARAM);
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_v.p, 0, 4 * (size_t)OCCK_MLP_NPARAM);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_mlp_init");
+    ctx->mlp_t = 0;
+    ctx->mlp_ready = 0;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_mlp_set(occk_ctx* ctx, const float* params, const float* norm) {
+    if (!ctx || !params || !norm) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device");
+    cudaSetDevice(ctx->device);
+    occk_status st = mlp_alloc(ctx);
+    if (st) return st;
+    for (int k = 0; k < OCCK_MLP_NIN + OCCK_MLP_NOUT; ++k) {
+        const float sd = k < OCCK_MLP_NIN ? norm[OCCK_MLP_NIN + k] : norm[2 * OCCK_MLP_NIN + OCCK_MLP_NOUT + k - OCCK_MLP_NIN];
+        if (!(sd > 0.f)) return fail(ctx, OCCK_ERR_ARG, "normalisation standard deviations must be > 0");
+    }
+    cudaError_t e = cudaMemcpy(ctx->mlp_prm.p, params, 4 * (size_t)OCCK_MLP_NPARAM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->mlp_norm.p, norm, 4 * (size_t)OCCK_MLP_NNORM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_m.p, 0, 4 * (size_t)OCCK_MLP_NPARAM);
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_v.p, 0, 4 * (size_t)OCCK_MLP_NPARAM);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_mlp_set");
+    ctx->mlp_t = 0;
+    ctx->mlp_ready = 1;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_mlp_get(occk_ctx* ctx, float* params, float* norm) {
+    if (!ctx || !params || !norm) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (!ctx->mlp_prm.p) return fail(ctx, OCCK_ERR_STATE, "no MLP on this context");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpy(params, ctx->mlp_prm.p, 4 * (size_t)OCCK_MLP_NPARAM, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(norm, ctx->mlp_norm.p, 4 * (size_t)OCCK_MLP_NNORM, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_mlp_get");
+}
+
+extern "C" occk_status occk_mlp_grad(occk_ctx* ctx, const float* X, const float* T, int n, float* grad,
+                                     float* loss_host, void* stream) {
+    if (!ctx || !X || !T || !grad || n <= 0) return fail(ctx, OCCK_ERR_ARG, "bad argument");
+    if (!ctx->mlp_prm.p) return fail(ctx, OCCK_ERR_STATE, "call occk_mlp_init or occk_mlp_set first");
+    cudaSetDevice(ctx->device);
+    MlpWs w;
+    occk_status st = mlp_workspace(ctx, n, &w);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float* prm = (const float*)ctx->mlp_prm.p;
+    cudaError_t e = occk::mlp_forward_train(prm, (const float*)ctx->mlp_norm.p, X, n, w.Xn, w.Z1, w.Z2, w.Y, s);
+    if (e == cudaSuccess)
+        e = occk::mlp_backward(prm, w.Xn, w.Z1, w.Z2, w.Y, T, n, w.dY, w.dZ1, w.dZ2, grad, w.part, 256, s);
+    double part[256];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part, w.part, sizeof(part), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_mlp_grad");
+    if (loss_host) *loss_host = (float)(host_loss(part, 256) / ((double)n * OCCK_MLP_NOUT));
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_mlp_train(occk_ctx* ctx, const float* X, const float* T, int n, int steps, float lr,
+                                      float* loss_host, void* stream) {
+    if (!ctx || !X || !T || n <= 0 || steps < 0) return fail(ctx, OCCK_ERR_ARG, "bad argument");
+    if (!ctx->mlp_prm.p) return fail(ctx, OCCK_ERR_STATE, "call occk_mlp_init or occk_mlp_set first");
+    cudaSetDevice(ctx->device);
+    MlpWs w;
+    occk_status st = mlp_workspace(ctx, n, &w);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* prm = (float*)ctx->mlp_prm.p;
+    float* g = (float*)ctx->mlp_grad.p;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < steps && e == cudaSuccess; ++it) {
+        e = occk::mlp_forward_train(prm, (const float*)ctx->mlp_norm.p, X, n, w.Xn, w.Z1, w.Z2, w.Y, s);
+        if (e == cudaSuccess)
+            e = occk::mlp_backward(prm, w.Xn, w.Z1, w.Z2, w.Y, T, n, w.dY, w.dZ1, w.dZ2, g, w.part, 256, s);
+        if (e == cudaSuccess)
+            e = occk::mlp_adam(prm, g, (float*)ctx->mlp_m.p, (float*)ctx->mlp_v.p, ++ctx->mlp_t, lr, s);
+    }
+    double part[256];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part, w.part, sizeof(part), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_mlp_train");
+    if (loss_host) *loss_host = (float)(host_loss(part, 256) / ((double)n * OCCK_MLP_NOUT));
+    ctx->mlp_ready = 1;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_mlp_predict(occk_ctx* ctx, const float* X, int n, float* Y, void* stream) {
+    if (!ctx || !X || !Y || n < 0) return fail(ctx, OCCK_ERR_ARG, "bad argument");
+    if (!ctx->mlp_prm.p) return fail(ctx, OCCK_ERR_STATE, "no MLP on this context");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = occk::mlp_predict_fp16((const float*)ctx->mlp_prm.p, (__half*)ctx->mlp_h.p,
+                                           (const float*)ctx->mlp_norm.p, X, n, Y, (cudaStream_t)stream);
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_mlp_predict");
+}
+
+static occk_status last_run_check(occk_ctx* ctx, const occk_tree* t) {
+    if (ctx->last_tree != t || ctx->last_lmax != t->lmax || !ctx->obox.p)
+        return fail(ctx, OCCK_ERR_STATE, "needs a previous occk_farfield_K on this tree and rank");
+    if (ctx->last_prec != OCCK_FP64 && ctx->last_prec != OCCK_FP32 && occk::tc_mode(ctx->last_prec) < 0)
+        return fail(ctx, OCCK_ERR_STATE, "unknown precision of the last run");
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_edge_features(occk_ctx* ctx, const occk_tree* t, float* F, void* stream) {
+    if (!ctx || !t || !F) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    occk_status st = last_run_check(ctx, t);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    const int nbox = (int)t->parent.size(), L = t->lmax;
+    cudaError_t e = ensure(ctx->nrm, sizeof(double) * (size_t)nbox * (L + 1));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "norm workspace");
+    const long long P = (long long)ctx->last_nocc * ctx->last_nocc;
+    e = occk::edge_features(ctx->last_prec == OCCK_FP64, ctx->obox.p, ctx->last_first_box, nbox,
+                            occk::ncomp(L), L, P, (int)t->m2l_tgt.size(), t->dev.m2l_tgt, t->dev.m2l_src,
+                            t->dev.box_key, t->dev.box_level, t->dev.hlev, t->depth, (double*)ctx->nrm.p, F,
+                            (cudaStream_t)stream);
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_edge_features");
+}
+
+extern "C" occk_status occk_edge_energies(occk_ctx* ctx, const occk_tree* t, double* E, void* stream) {
+    if (!ctx || !t || !E) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    occk_status st = last_run_check(ctx, t);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    const int L = t->lmax, nc = occk::ncomp(L), ne = (int)t->m2l_tgt.size();
+    cudaError_t e = ensure(ctx->gram, sizeof(double) * (size_t)std::max(ne, 1) * nc * nc);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Gram workspace");
+    const long long P = (long long)ctx->last_nocc * ctx->last_nocc;
+    e = occk::edge_energies(ctx->last_prec == OCCK_FP64, ctx->obox.p, ctx->last_first_box, nc, L, P, ne,
+                            t->dev.m2l_tgt, t->dev.m2l_src, t->dev.ops, t->dev.m2l_op, (double*)ctx->gram.p, E,
+                            (cudaStream_t)stream);
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_edge_energies");
+}
+
+extern "C" occk_status occk_set_learned_tau(occk_ctx* ctx, double tau) {
+    if (!ctx || !(tau > 0)) return fail(ctx, OCCK_ERR_ARG, "tau must be > 0");
+    ctx->tau = tau;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_get_edge_ranks(occk_ctx* ctx, const occk_tree* t, int* ranks, int n) {
+    if (!ctx || !t || !ranks) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    if (n != (int)t->m2l_tgt.size()) return fail(ctx, OCCK_ERR_SHAPE, "n != nm2l");
+    if (!ctx->ranks_valid || ctx->last_tree != t) return fail(ctx, OCCK_ERR_STATE, "no learned run on this tree");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpy(ranks, ctx->ranks.p, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_get_edge_ranks");
 }

@@ -360,6 +360,32 @@ __global__ void k_fma_probe(T* out, int iters, T seed) {
     if (s == T(-1.2345)) out[threadIdx.x] = s;
 }
 
+// Output components per block of k_translate: the instantiated width that
+// wastes the fewest lanes of the last chunk (rows past nc still cost FMAs).
+int translate_chunk(int nc) {
+    const int cand[] = {25, 21, 16, 9, 4};
+    int best = 25, waste = 1 << 30;
+    for (int c : cand) {
+        int w = ((nc + c - 1) / c) * c - nc;
+        if (w < waste) {
+            waste = w;
+            best = c;
+        }
+    }
+    return best;
+}
+
+template <typename T, typename... Args>
+void launch_translate(int lmc, dim3 g, cudaStream_t s, Args... args) {
+    switch (lmc) {
+        case 4: k_translate<T, 4><<<g, 128, 0, s>>>(args...); break;
+        case 9: k_translate<T, 9><<<g, 128, 0, s>>>(args...); break;
+        case 16: k_translate<T, 16><<<g, 128, 0, s>>>(args...); break;
+        case 21: k_translate<T, 21><<<g, 128, 0, s>>>(args...); break;
+        default: k_translate<T, 25><<<g, 128, 0, s>>>(args...); break;
+    }
+}
+
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
@@ -412,7 +438,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    constexpr int LMC = 16;
+    const int LMC = translate_chunk(nc);
     const int nchunk = (nc + LMC - 1) / LMC;
     const unsigned pblocks = (unsigned)((P + 127) / 128);
     // (b) M2M: parents at level lev-1 gather their children at level lev
@@ -420,29 +446,41 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     for (int lev = D; lev >= 3; --lev) {
         int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
         dim3 g(pblocks, nt, nchunk);
-        k_translate<T, LMC><<<g, 128, 0, s>>>(0, (int)P, nc, a.L, a.first_box, t0, a.child_ptr,
+        launch_translate<T>(LMC, g, s, 0, (int)P, nc, a.L, a.first_box, t0, a.child_ptr,
                                              a.child_list, a.m2m_op, nullptr, a.parent, ops, Ob, Ob, 0);
+    }
+    // learned ranks: features from the multipoles of every box, FP16 MLP,
+    // budgeted choice; M2L then reads the per-edge ranks
+    const int* lmax_e = a.m2l_lmax;
+    if (a.learned) {
+        cudaError_t e2 = edge_features(sizeof(T) == 8, Ob, a.first_box, a.nbox, nc, a.L, P, a.nm2l, a.m2l_tgt,
+                                       a.m2l_src, a.box_key, a.box_level, a.hlev, D, a.nrm, a.feat, s);
+        if (e2 == cudaSuccess)
+            e2 = mlp_predict_fp16(a.mlp_prm, (__half*)a.mlp_h, a.mlp_norm, a.feat, a.nm2l, a.pred, s);
+        if (e2 == cudaSuccess) e2 = select_ranks(a.pred, a.nm2l, a.L, a.tau, a.ranks, s);
+        if (e2 != cudaSuccess) return e2;
+        lmax_e = a.ranks;
     }
     // (c) M2L: every box of levels 2..D, all levels in one launch
     mark(3);
     if (tcm && nc <= 128) {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         cudaError_t e2 = tc_run_m2l(a.prec, (int)P, nc, a.L, a.first_box, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op,
-                                    a.m2l_lmax, (const float*)ops, (const float*)Ob, (float*)Mb, a.box_scale,
+                                    lmax_e, (const float*)ops, (const float*)Ob, (float*)Mb, a.box_scale,
                                     a.err_word, s);
         if (e2 != cudaSuccess) return e2;
     } else {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         dim3 g(pblocks, nt, nchunk);
-        k_translate<T, LMC><<<g, 128, 0, s>>>(1, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
-                                             a.m2l_op, a.m2l_lmax, a.parent, ops, Ob, Mb, 0);
+        launch_translate<T>(LMC, g, s, 1, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
+                                             a.m2l_op, lmax_e, a.parent, ops, Ob, Mb, 0);
     }
     // (d) L2L: children at level lev accumulate their parent's expansion
     mark(4);
     for (int lev = 3; lev <= D; ++lev) {
         int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
         dim3 g(pblocks, nt, nchunk);
-        k_translate<T, LMC><<<g, 128, 0, s>>>(2, (int)P, nc, a.L, a.first_box, t0, nullptr, nullptr,
+        launch_translate<T>(LMC, g, s, 2, (int)P, nc, a.L, a.first_box, t0, nullptr, nullptr,
                                              a.l2l_op, nullptr, a.parent, ops, Mb, Mb, 1);
     }
     // (e) L2P

@@ -46,7 +46,6 @@ struct PrecT {
     static constexpr int KSTEP = (P == PM_TF32) ? 8 : 16;
     static constexpr int EPC = 16 / esz;             // elements per 16-byte chunk
     static constexpr uint32_t fmt = (P == PM_BF16 || P == PM_BF16X3) ? 1u : (P == PM_TF32 ? 2u : 0u);
-    static constexpr int nprod = split ? 3 : 1;
 };
 
 // rank l of real-form component index c = l*l + ...

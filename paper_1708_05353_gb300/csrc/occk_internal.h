@@ -1,6 +1,7 @@
 // Internal declarations shared by the host ABI layer and the CUDA kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -102,6 +103,10 @@ struct occk_tree {
         occk::OpDesc* opdesc = nullptr;
         float* lscale = nullptr;       // [nc] 1/s_leaf^l
         float* box_scale = nullptr;    // [nbox]
+        int* box_key = nullptr;        // [nbox*3]
+        int* box_level = nullptr;      // [nbox]
+        double* hlev = nullptr;        // [depth+1]
+        int* m2l_tgt = nullptr;        // [nm2l]
     } dev;
     int nops_alloc_lmax = -1;
 };
@@ -115,6 +120,11 @@ struct occk_ctx {
     // last run (for debug fetch)
     int last_prec = -1, last_nocc = 0, last_lmax = -1, last_first_box = 0;
     const occk_tree* last_tree = nullptr;
+    // learned rank selector
+    int mlp_ready = 0, mlp_t = 0;
+    double tau = 1e-6;
+    occk::DevBuf mlp_prm, mlp_norm, mlp_m, mlp_v, mlp_h, mlp_grad, mlp_ws, feat, pred, ranks, nrm, gram;
+    int ranks_valid = 0;
     // stage timers
     int timing = 0;
     cudaEvent_t ev[OCCK_NSTAGE + 1] = {};
@@ -157,11 +167,34 @@ struct FmmArgs {
     const float* lscale;             // [nc] 1/s_leaf^l
     const float* box_scale;          // [nbox] side of each box's level
     int* err_word;                   // device error word (bounded waits)
+    // learned selector (lmax_policy 2); learned == 0 when unused
+    int learned;
+    const float* mlp_prm; void* mlp_h; const float* mlp_norm;
+    float* feat; float* pred; int* ranks; double* nrm; double tau; int nm2l;
+    const int* m2l_tgt; const int* box_key; const int* box_level; const double* hlev;
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
 size_t workspace_elems_w(const FmmArgs& a);
 
 cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s);
+
+// ----- learned selector (kernels_mlp.cu) ------------------------------------
+int mlp_nparams();
+cudaError_t mlp_forward_train(const float* prm, const float* norm, const float* X, int n, float* Xn, float* Z1,
+                              float* Z2, float* Y, cudaStream_t s);
+cudaError_t mlp_backward(const float* prm, const float* Xn, const float* Z1, const float* Z2, const float* Y,
+                         const float* T, int n, float* dY, float* dZ1, float* dZ2, float* grad, double* part,
+                         int npart, cudaStream_t s);
+cudaError_t mlp_adam(float* prm, const float* g, float* m, float* v, int t, float lr, cudaStream_t s);
+cudaError_t mlp_predict_fp16(const float* prm, __half* prm_h, const float* norm, const float* X, int n,
+                             float* Y, cudaStream_t s);
+cudaError_t edge_features(bool fp64, const void* O, int first_box, int nbox, int nc, int L, long long P,
+                          int nedge, const int* tgt, const int* src, const int* box_key, const int* box_level,
+                          const double* hlev, int depth, double* nrm, float* F, cudaStream_t s);
+cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L, long long P, int nedge,
+                          const int* tgt, const int* src, const double* ops, const int* opidx, double* G,
+                          double* out, cudaStream_t s);
+cudaError_t select_ranks(const float* pred, int nedge, int Lmax, double tau, int* ranks, cudaStream_t s);
 
 // ----- tensor-core steps (kernels_tc.cu) ------------------------------------
 int tc_mode(int prec);

@@ -77,6 +77,17 @@ _SIGS = {
     "occk_probe_fma_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_device_status": (ctypes.c_int, [_vp, _vp]),
+    "occk_mlp_init": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "occk_mlp_set": (ctypes.c_int, [_vp, _vp, _vp]),
+    "occk_mlp_get": (ctypes.c_int, [_vp, _vp, _vp]),
+    "occk_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                      ctypes.POINTER(ctypes.c_float), _vp]),
+    "occk_mlp_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_float), _vp]),
+    "occk_mlp_predict": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+    "occk_edge_features": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "occk_edge_energies": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "occk_set_learned_tau": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "occk_get_edge_ranks": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "occk_debug_tc_gemm": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                           _vp, _vp]),
     "occk_exchange_energy_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
@@ -84,6 +95,9 @@ _SIGS = {
     "occk_get_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
 }
 NSTAGE = 7
+MLP_NIN, MLP_HIDDEN, MLP_NOUT = 16, 64, 8
+MLP_NPARAM = MLP_NIN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_NOUT + MLP_NOUT
+MLP_NNORM = 2 * MLP_NIN + 2 * MLP_NOUT
 STAGES = ["a_half", "a_full", "b_m2m", "c_m2l", "d_l2l", "e_l2p", "reduce"]
 
 
@@ -264,6 +278,80 @@ def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K
                                ctypes.byref(eh) if want_energy_host else None, _stream_ptr(stream))
     ctx.check(rc, "occk_farfield_K")
     return K, (eh.value if want_energy_host else Ex)
+
+
+# ---- learned rank selector --------------------------------------------------
+
+def mlp_init(ctx: Context, seed: int = 1):
+    ctx.check(lib().occk_mlp_init(ctx._h, seed), "occk_mlp_init")
+
+
+def mlp_set(ctx: Context, params, norm):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    n = np.ascontiguousarray(norm, dtype=np.float32)
+    assert p.size == MLP_NPARAM and n.size == MLP_NNORM
+    ctx.check(lib().occk_mlp_set(ctx._h, p.ctypes.data_as(_vp), n.ctypes.data_as(_vp)), "occk_mlp_set")
+
+
+def mlp_get(ctx: Context):
+    p = np.zeros(MLP_NPARAM, dtype=np.float32)
+    n = np.zeros(MLP_NNORM, dtype=np.float32)
+    ctx.check(lib().occk_mlp_get(ctx._h, p.ctypes.data_as(_vp), n.ctypes.data_as(_vp)), "occk_mlp_get")
+    return p, n
+
+
+def mlp_train(ctx: Context, X, T, steps: int, lr: float, stream=None) -> float:
+    loss = ctypes.c_float()
+    ctx.check(lib().occk_mlp_train(ctx._h, _vp(X.data_ptr()), _vp(T.data_ptr()), X.shape[0], steps, lr,
+                                   ctypes.byref(loss), _stream_ptr(stream)), "occk_mlp_train")
+    return loss.value
+
+
+def mlp_grad(ctx: Context, X, T, stream=None):
+    import torch
+    g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+    loss = ctypes.c_float()
+    ctx.check(lib().occk_mlp_grad(ctx._h, _vp(X.data_ptr()), _vp(T.data_ptr()), X.shape[0], _vp(g.data_ptr()),
+                                  ctypes.byref(loss), _stream_ptr(stream)), "occk_mlp_grad")
+    return loss.value, g
+
+
+def mlp_predict(ctx: Context, X, stream=None):
+    import torch
+    Y = torch.empty((X.shape[0], MLP_NOUT), dtype=torch.float32, device=X.device)
+    ctx.check(lib().occk_mlp_predict(ctx._h, _vp(X.data_ptr()), X.shape[0], _vp(Y.data_ptr()),
+                                     _stream_ptr(stream)), "occk_mlp_predict")
+    return Y
+
+
+def edge_features(ctx: Context, tree: Tree, stream=None):
+    import torch
+    n = tree.info()["nm2l"]
+    F = torch.empty((max(n, 1), MLP_NIN), dtype=torch.float32, device=f"cuda:{ctx.device}")
+    ctx.check(lib().occk_edge_features(ctx._h, tree._h, _vp(F.data_ptr()), _stream_ptr(stream)),
+              "occk_edge_features")
+    return F[:n]
+
+
+def edge_energies(ctx: Context, tree: Tree, stream=None):
+    import torch
+    inf = tree.info()
+    E = torch.empty((max(inf["nm2l"], 1), inf["lmax"] + 1), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    ctx.check(lib().occk_edge_energies(ctx._h, tree._h, _vp(E.data_ptr()), _stream_ptr(stream)),
+              "occk_edge_energies")
+    return E[:inf["nm2l"]]
+
+
+def set_learned_tau(ctx: Context, tau: float):
+    ctx.check(lib().occk_set_learned_tau(ctx._h, tau), "occk_set_learned_tau")
+
+
+def edge_ranks(ctx: Context, tree: Tree):
+    n = tree.info()["nm2l"]
+    r = np.zeros(max(n, 1), dtype=np.int32)
+    ctx.check(lib().occk_get_edge_ranks(ctx._h, tree._h, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n),
+              "occk_get_edge_ranks")
+    return r[:n]
 
 
 def debug_tc_gemm(ctx: Context, prec: str, A, B, stream=None):
