@@ -279,6 +279,35 @@ occk_status occk_set_learned_tau(occk_ctx* ctx, double tau);
 /* Ranks chosen by the last lmax_policy 2 call (host int [nm2l]). */
 occk_status occk_get_edge_ranks(occk_ctx* ctx, const occk_tree* tree, int* ranks, int n);
 
+/* ---- Batches of uneven systems (an addition to the paper's method) ---------
+ * A batch runs the far-field exchange of many systems (same lmax, each tree
+ * with its multipoles) as one sequence of persistent kernels -- one per step,
+ * and one per tree level for M2M and L2L -- over static work lists of all
+ * systems, captured once into a CUDA graph.  The batch owns one device arena
+ * with every system's workspace and its input/output buffers.
+ * prec: OCCK_FP64 or OCCK_FP32. */
+typedef struct occk_batch occk_batch;
+occk_status occk_batch_create(occk_ctx* ctx, int nsys, occk_tree* const* trees, const int* nocc, int prec,
+                              occk_batch** out);
+void occk_batch_destroy(occk_batch* batch);
+/* Device buffers of system `sys`, owned by the batch: C (input) and K
+ * (output), column-major [nao x nocc] with leading dimension *ld = nao, and
+ * the energies E [nsys] (output, one per system).  Any pointer may be NULL. */
+occk_status occk_batch_buffers(occk_batch* batch, int sys, double** C_dev, double** K_dev, int* ld,
+                               double** E_dev);
+/* Run the batch on `stream` (ordered with it through events).  use_graph != 0
+ * captures the launch sequence into a CUDA graph on first use (and after a
+ * tuning change) and replays it. */
+occk_status occk_batch_run(occk_batch* batch, int use_graph, void* stream);
+/* Autotune the batch's tile shapes: components per translation block (4, 9,
+ * 16, 21, 25), persistent blocks per SM (2..32) and, in FP32, the SIMT GEMM
+ * tile (64 or 128), by coordinate search timing whole batch runs with CUDA
+ * events; the winner is cached in the text file `cache_path` (nullable) under
+ * a key of GPU name, lmax, precision, number of systems, total pair count and
+ * depth, and reused when the key is present.  cfg_out (nullable) receives
+ * {chunk, blocks per SM, tile}.  Synchronises `stream`. */
+occk_status occk_batch_tune(occk_batch* batch, const char* cache_path, int* cfg_out, void* stream);
+
 /* Reads the device error word of the last occk_farfield_K on this context
  * (synchronises `stream`).  Returns OCCK_ERR_TIMEOUT if a bounded wait inside
  * a tensor-core kernel gave up (its results are then invalid), else OK. */

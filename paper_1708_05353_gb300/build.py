@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libocck.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_ops.cu", "kernels_fmm.cu", "kernels_tc.cu", "kernels_mlp.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_ops.cu", "kernels_fmm.cu", "kernels_tc.cu", "kernels_mlp.cu", "kernels_batch.cu", "noalloc.cu"]
 CPP_SOURCES = ["host.cpp"]
 
 
@@ -48,7 +48,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
     nvcc = _nvcc()
     if nvcc is None:
         raise RuntimeError("nvcc not found")
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "occk.h"))
     jobs = []
     objs = []

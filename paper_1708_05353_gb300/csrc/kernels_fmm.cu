@@ -12,336 +12,58 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "fmm_bodies.cuh"
 #include "occk_internal.h"
 
 namespace occk {
 
 namespace {
 
-constexpr int kNcMax = 169;   // (12+1)^2
+using body::k_final_energy;
+using body::k_zero_K;
 
-// ---------------------------------------------------------------------------
-// C (column-major, ldc) -> Ct (row-major), 32x32 tiles through shared memory
-// ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_transpose_C(const double* __restrict__ C, int ldc, int nao, int nocc,
-                              T* __restrict__ Ct) {
-    __shared__ double tile[32][33];
-    int r0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        int r = r0 + threadIdx.x, i = i0 + k;
-        tile[k][threadIdx.x] = (r < nao && i < nocc) ? C[(size_t)i * ldc + r] : 0.0;
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        int r = r0 + k, i = i0 + threadIdx.x;
-        if (r < nao && i < nocc) Ct[(size_t)r * nocc + i] = (T)tile[threadIdx.x][k];
-    }
+__global__ void k_transpose_C(const double* __restrict__ C, int ldc, int nao, int nocc, T* __restrict__ Ct) {
+    body::transpose_body<T>(blockIdx.x, blockIdx.y, 0, C, ldc, nao, nocc, Ct);
 }
 
-// ---------------------------------------------------------------------------
-// Step (a), first half (Eq. motrans, first line):
-//   W[lm][row][j] = sum_{entries (row, s, v)} O^{rs}_lm C_sj
-// grid (nrow, lm chunks); threads stride over j.
-// ---------------------------------------------------------------------------
 template <typename T, int LMC>
 __global__ void k_half(const int* __restrict__ row_ptr, const int* __restrict__ ent_col,
                        const int* __restrict__ ent_val, const T* __restrict__ vals, int nc,
                        const T* __restrict__ Ct, int nocc, int nrow, T* __restrict__ W) {
-    const int row = blockIdx.x;
-    const int c0 = blockIdx.y * LMC;
-    const int e0 = row_ptr[row], e1 = row_ptr[row + 1];
-    const int ncl = min(LMC, nc - c0);
-    for (int j = threadIdx.x; j < nocc; j += blockDim.x) {
-        T acc[LMC];
-#pragma unroll
-        for (int q = 0; q < LMC; ++q) acc[q] = T(0);
-        for (int e = e0; e < e1; ++e) {
-            const T cs = Ct[(size_t)ent_col[e] * nocc + j];
-            const T* v = vals + (size_t)ent_val[e] * nc + c0;
-#pragma unroll
-            for (int q = 0; q < LMC; ++q)
-                if (q < ncl) acc[q] += v[q] * cs;
-        }
-#pragma unroll
-        for (int q = 0; q < LMC; ++q)
-            if (q < ncl) W[((size_t)(c0 + q) * nrow + row) * nocc + j] = acc[q];
-    }
+    body::half_body<T, LMC>(blockIdx.x, blockIdx.y, 0, row_ptr, ent_col, ent_val, vals, nc, Ct, nocc, nrow, W);
 }
 
-// ---------------------------------------------------------------------------
-// Register-tiled GEMM core shared by steps (a) and (e):
-//   acc[tm][tn] += sum_k As[k][ty*TM+tm] * Bs[k][tx*TN+tn]
-// ---------------------------------------------------------------------------
-template <typename T, int BM, int BN, int BK, int TM, int TN>
-struct Tile {
-    static constexpr int NT = (BM / TM) * (BN / TN);
-};
-
-// Step (a), second half (Eq. motrans, second line), per leaf B and component lm:
-//   O[B][lm][i][j] = sum_{r in S_B} C_ri W[lm][rowoff_B + r][j]
-// Only tiles with ti <= tj are computed; O^{ij} = O^{ji} fills the rest.
 template <typename T, int BM, int BK, int TM>
 __global__ void __launch_bounds__((BM / TM) * (BM / TM))
-k_full(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos,
-       const T* __restrict__ Ct, const T* __restrict__ W, int nocc, int nrow, int nc,
-       int ntile, T* __restrict__ Obox, int leaf_store0) {
-    constexpr int NTH = (BM / TM) * (BM / TM);
-    __shared__ T As[BK][BM];
-    __shared__ T Bs[BK][BM];
-    __shared__ int aos[BK];
-    const int B = blockIdx.y / nc;
-    const int lm = blockIdx.y - B * nc;
-    // triangular tile index -> (ti, tj), ti <= tj
-    int t = blockIdx.x, ti = 0;
-    while (t >= ntile - ti) {
-        t -= ntile - ti;
-        ++ti;
-    }
-    const int tj = ti + t;
-    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
-    const int i0 = ti * BM, j0 = tj * BM;
-    const int tx = threadIdx.x % (BM / TM), ty = threadIdx.x / (BM / TM);
-    const T* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
-    T acc[TM][TM];
-#pragma unroll
-    for (int a = 0; a < TM; ++a)
-#pragma unroll
-        for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
-    for (int k0 = 0; k0 < nr; k0 += BK) {
-        if (threadIdx.x < BK) aos[threadIdx.x] = (k0 + threadIdx.x < nr) ? leaf_aos[rb0 + k0 + threadIdx.x] : -1;
-        __syncthreads();
-        for (int e = threadIdx.x; e < BK * BM; e += NTH) {
-            int kk = e / BM, c = e - kk * BM;
-            int ao = aos[kk];
-            int ii = i0 + c, jj = j0 + c;
-            As[kk][c] = (ao >= 0 && ii < nocc) ? Ct[(size_t)ao * nocc + ii] : T(0);
-            Bs[kk][c] = (ao >= 0 && jj < nocc) ? Wl[(size_t)(k0 + kk) * nocc + jj] : T(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            T a[TM], b[TM];
-#pragma unroll
-            for (int q = 0; q < TM; ++q) {
-                a[q] = As[kk][ty * TM + q];
-                b[q] = Bs[kk][tx * TM + q];
-            }
-#pragma unroll
-            for (int x = 0; x < TM; ++x)
-#pragma unroll
-                for (int y = 0; y < TM; ++y) acc[x][y] += a[x] * b[y];
-        }
-        __syncthreads();
-    }
-    const size_t P = (size_t)nocc * nocc;
-    T* O = Obox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
-#pragma unroll
-    for (int x = 0; x < TM; ++x) {
-        int i = i0 + ty * TM + x;
-        if (i >= nocc) continue;
-#pragma unroll
-        for (int y = 0; y < TM; ++y) {
-            int j = j0 + tx * TM + y;
-            if (j >= nocc) continue;
-            O[(size_t)i * nocc + j] = acc[x][y];
-            if (ti != tj) O[(size_t)j * nocc + i] = acc[x][y];
-        }
-    }
+k_full(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const T* __restrict__ Ct,
+       const T* __restrict__ W, int nocc, int nrow, int nc, int ntile, T* __restrict__ Obox, int leaf_store0) {
+    body::full_body<T, BM, BK, TM>(blockIdx.x, blockIdx.y, 0, leaf_rowoff, leaf_aos, Ct, W, nocc, nrow, nc, ntile,
+                                   Obox, leaf_store0);
 }
 
-// ---------------------------------------------------------------------------
-// Steps (b), (c), (d): out[tgt][lm][p] (+)= sum_src sum_l'm' T_src[lm][l'm'] in[src][l'm'][p]
-// mode 0: M2M, sources = children of tgt, operator m2m_op[child], lower in l
-// mode 1: M2L, sources = interaction list of tgt, operator m2l_op[e], rank lmax_e
-// mode 2: L2L, source = parent of tgt, operator l2l_op[tgt], upper in l
-// grid (pair blocks, targets, lm chunks).
-// ---------------------------------------------------------------------------
 template <typename T, int LMC>
 __global__ void __launch_bounds__(128)
 k_translate(int mode, int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr,
             const int* __restrict__ list, const int* __restrict__ opidx, const int* __restrict__ lmax_e,
             const int* __restrict__ parent, const T* __restrict__ ops, const T* __restrict__ in,
             T* __restrict__ out, int accumulate) {
-    __shared__ T sop[LMC][kNcMax];
-    const int tgt = tgt0 + blockIdx.y;
-    const int c0 = blockIdx.z * LMC;
-    const int ncl = min(LMC, nc - c0);
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = p < P;
-    T acc[LMC];
-    T* o = out + ((size_t)(tgt - first_box) * nc + c0) * P + p;
-#pragma unroll
-    for (int q = 0; q < LMC; ++q) acc[q] = (accumulate && live && q < ncl) ? o[(size_t)q * P] : T(0);
-    int e0, e1;
-    if (mode == 2) {
-        e0 = 0;
-        e1 = 1;
-    } else {
-        e0 = ptr[tgt];
-        e1 = ptr[tgt + 1];
-    }
-    // output rank range of this chunk
-    int lhi = 0;
-    while ((lhi + 1) * (lhi + 1) <= c0 + ncl - 1) ++lhi;
-    int llo = 0;
-    while ((llo + 1) * (llo + 1) <= c0) ++llo;
-    for (int e = e0; e < e1; ++e) {
-        int src, op, Le = L;
-        if (mode == 0) {
-            src = list[e];
-            op = opidx[src];
-        } else if (mode == 1) {
-            src = list[e];
-            op = opidx[e];
-            if (lmax_e) Le = lmax_e[e];
-        } else {
-            src = parent[tgt];
-            op = opidx[tgt];
-        }
-        const int ncr = (Le + 1) * (Le + 1);
-        if (c0 >= ncr) continue;   // uniform across the block
-        int cb0 = 0, cb1 = ncr;
-        if (mode == 0) cb1 = min(ncr, (lhi + 1) * (lhi + 1));
-        if (mode == 2) cb0 = llo * llo;
-        const T* Tm = ops + (size_t)op * nc * nc;
-        __syncthreads();
-        for (int x = threadIdx.x; x < LMC * (cb1 - cb0); x += blockDim.x) {
-            int q = x / (cb1 - cb0), c = cb0 + (x - q * (cb1 - cb0));
-            sop[q][c] = (q < ncl && c0 + q < ncr) ? Tm[(size_t)(c0 + q) * nc + c] : T(0);
-        }
-        __syncthreads();
-        if (live) {
-            const T* x = in + (size_t)(src - first_box) * nc * P + p;
-            for (int c = cb0; c < cb1; ++c) {
-                const T v = x[(size_t)c * P];
-#pragma unroll
-                for (int q = 0; q < LMC; ++q) acc[q] += sop[q][c] * v;
-            }
-        }
-    }
-    if (live) {
-#pragma unroll
-        for (int q = 0; q < LMC; ++q)
-            if (q < ncl) o[(size_t)q * P] = acc[q];
-    }
+    body::translate_body<T, LMC>(blockIdx.x, blockIdx.y, blockIdx.z, mode, P, nc, L, first_box, tgt0, ptr, list,
+                                 opidx, lmax_e, parent, ops, in, out, accumulate);
 }
 
-// ---------------------------------------------------------------------------
-// Step (e), Eq. kri, per leaf B:
-//   KB[rowoff_B + r][i] = 2 sum_lm w_lm sum_j W[lm][rowoff_B + r][j] Mcal[B][lm][i][j]
-// with w = 1 for m = 0, 2 for Re(m>0), -2 for Im(m>0): the real form of
-// sum_{m=-l..l} O_lm Mcal_lm for real densities.
-// ---------------------------------------------------------------------------
 template <typename T, int BM, int BK, int TM>
 __global__ void __launch_bounds__((BM / TM) * (BM / TM))
-k_l2p(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const T* __restrict__ Mbox,
-      int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
-    constexpr int NTH = (BM / TM) * (BM / TM);
-    __shared__ T As[BK][BM + 1];
-    __shared__ T Bs[BK][BM + 1];
-    const int B = blockIdx.z;
-    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
-    const int r0 = blockIdx.x * BM, i0 = blockIdx.y * BM;
-    if (r0 >= nr) return;
-    const int tx = threadIdx.x % (BM / TM), ty = threadIdx.x / (BM / TM);
-    const size_t P = (size_t)nocc * nocc;
-    T acc[TM][TM];
-#pragma unroll
-    for (int a = 0; a < TM; ++a)
-#pragma unroll
-        for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
-    for (int lm = 0; lm < nc; ++lm) {
-        int l = 0;
-        while ((l + 1) * (l + 1) <= lm) ++l;
-        const T w = (lm == l * l) ? T(2) : (((lm - l * l) & 1) ? T(4) : T(-4));
-        const T* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
-        const T* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
-        for (int k0 = 0; k0 < nocc; k0 += BK) {
-            for (int e = threadIdx.x; e < BK * BM; e += NTH) {
-                int row = e / BK, kk = e - row * BK;
-                int r = r0 + row, i = i0 + row, j = k0 + kk;
-                As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : T(0);
-                Bs[kk][row] = (i < nocc && j < nocc) ? w * Ml[(size_t)i * nocc + j] : T(0);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
-                T a[TM], b[TM];
-#pragma unroll
-                for (int q = 0; q < TM; ++q) {
-                    a[q] = As[kk][ty * TM + q];
-                    b[q] = Bs[kk][tx * TM + q];
-                }
-#pragma unroll
-                for (int x = 0; x < TM; ++x)
-#pragma unroll
-                    for (int y = 0; y < TM; ++y) acc[x][y] += a[x] * b[y];
-            }
-            __syncthreads();
-        }
-    }
-#pragma unroll
-    for (int x = 0; x < TM; ++x) {
-        int r = r0 + ty * TM + x;
-        if (r >= nr) continue;
-#pragma unroll
-        for (int y = 0; y < TM; ++y) {
-            int i = i0 + tx * TM + y;
-            if (i < nocc) KB[(size_t)(rb0 + r) * nocc + i] = (double)acc[x][y];
-        }
-    }
+k_l2p(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const T* __restrict__ Mbox, int nocc, int nrow,
+      int nc, int leaf_store0, double* __restrict__ KB) {
+    body::l2p_body<T, BM, BK, TM>(blockIdx.x, blockIdx.y, blockIdx.z, leaf_rowoff, W, Mbox, nocc, nrow, nc,
+                                  leaf_store0, KB);
 }
 
-// ---------------------------------------------------------------------------
-// K[r + i*ldk] = sum over the leaf rows of AO r of KB[row][i], in FP64, and the
-// per-block partial of E = -1/2 sum_ri C_ri K_ri.
-// ---------------------------------------------------------------------------
 __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
-                           const double* __restrict__ KB, int nao, int nocc,
-                           const double* __restrict__ C, int ldc, double* __restrict__ K, int ldk,
-                           double* __restrict__ part) {
-    __shared__ double red[256];
-    double e = 0.0;
-    const long long n = (long long)nao * nocc;
-    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(x / nao), r = (int)(x - (long long)i * nao);
-        double s = 0.0;
-        for (int q = ao_row_ptr[r]; q < ao_row_ptr[r + 1]; ++q) s += KB[(size_t)ao_rows[q] * nocc + i];
-        K[(size_t)i * ldk + r] = s;
-        e += C[(size_t)i * ldc + r] * s;
-    }
-    red[threadIdx.x] = e;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
-
-__global__ void k_final_energy(const double* __restrict__ part, int n, double* __restrict__ E) {
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int x = threadIdx.x; x < n; x += blockDim.x) s += part[x];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *E = -0.5 * red[0];
-}
-
-__global__ void k_zero_K(double* K, int ldk, int nao, int nocc, double* E) {
-    long long n = (long long)nao * nocc;
-    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(x / nao), r = (int)(x - (long long)i * nao);
-        K[(size_t)i * ldk + r] = 0.0;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *E = 0.0;
+                           const double* __restrict__ KB, int nao, int nocc, const double* __restrict__ C, int ldc,
+                           double* __restrict__ K, int ldk, double* __restrict__ part) {
+    body::reduce_body(blockIdx.x, 0, gridDim.x, ao_row_ptr, ao_rows, KB, nao, nocc, C, ldc, K, ldk, part);
 }
 
 // ---------------------------------------------------------------------------

@@ -77,6 +77,13 @@ _SIGS = {
     "occk_probe_fma_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_device_status": (ctypes.c_int, [_vp, _vp]),
+    "occk_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.c_int, ctypes.POINTER(_vp)]),
+    "occk_batch_destroy": (None, [_vp]),
+    "occk_batch_buffers": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp)]),
+    "occk_batch_run": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "occk_batch_tune": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), _vp]),
     "occk_mlp_init": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "occk_mlp_set": (ctypes.c_int, [_vp, _vp, _vp]),
     "occk_mlp_get": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -278,6 +285,66 @@ def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K
                                ctypes.byref(eh) if want_energy_host else None, _stream_ptr(stream))
     ctx.check(rc, "occk_farfield_K")
     return K, (eh.value if want_energy_host else Ex)
+
+
+# ---- batches ---------------------------------------------------------------------
+
+class Batch:
+    """occk_batch over trees (each with pair multipoles at the same lmax)."""
+
+    def __init__(self, ctx: Context, trees, noccs, prec="fp32"):
+        self.ctx = ctx
+        self.trees = list(trees)
+        arr = (_vp * len(trees))(*[t._h for t in trees])
+        no = (ctypes.c_int * len(trees))(*noccs)
+        self._h = _vp()
+        ctx.check(lib().occk_batch_create(ctx._h, len(trees), arr, no, PRECISIONS[prec], ctypes.byref(self._h)),
+                  "occk_batch_create")
+        self.noccs = list(noccs)
+
+    def buffers(self, sys):
+        """(C, K, E) as torch views of the batch-owned device buffers."""
+        import torch
+        c, k, e = _vp(), _vp(), _vp()
+        ld = ctypes.c_int()
+        self.ctx.check(lib().occk_batch_buffers(self._h, sys, ctypes.byref(c), ctypes.byref(k), ctypes.byref(ld),
+                                                ctypes.byref(e)), "occk_batch_buffers")
+        return c.value, k.value, e.value, ld.value
+
+    def run(self, use_graph=True, stream=None):
+        self.ctx.check(lib().occk_batch_run(self._h, 1 if use_graph else 0, _stream_ptr(stream)), "occk_batch_run")
+
+    def tune(self, cache_path=None, stream=None):
+        cfg = (ctypes.c_int * 3)()
+        self.ctx.check(lib().occk_batch_tune(self._h, cache_path.encode() if cache_path else None, cfg,
+                                             _stream_ptr(stream)), "occk_batch_tune")
+        return dict(chunk=cfg[0], blocks_per_sm=cfg[1], tile=cfg[2])
+
+    def close(self):
+        if self._h:
+            lib().occk_batch_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def device_view(ptr, shape, dtype, device, strides=None):
+    """A torch tensor aliasing library-owned device memory (no copy)."""
+    import torch
+    n = int(np.prod(shape))
+    itemsize = torch.tensor([], dtype=dtype).element_size()
+
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": {8: "<f8", 4: "<f4"}[itemsize],
+                                    "data": (ptr, False), "version": 2}
+    flat = torch.as_tensor(_Holder(), device=device)
+    if strides is None:
+        return flat.view(shape)
+    return flat.as_strided(shape, strides)
 
 
 # ---- learned rank selector --------------------------------------------------
