@@ -43,7 +43,18 @@ def parse():
     p.add_argument("--prec", default="fp64")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-cols", type=int, default=2)
+    p.add_argument("--workload", default="chain", choices=["chain", "water", "batch"])
+    p.add_argument("--batch-fp64", action="store_true", help="run the batch workload in FP64 (default FP32)")
+    p.add_argument("--variants", default="fp32,tf32,bf16,fp16,bf16x3,fp16x3",
+                   help="extra precisions timed beside the main one (comma list, or 'none')")
     return p.parse_args()
+
+
+def make_system(args):
+    from paper_1708_05353_gb300 import inputs
+    if args.workload == "water":
+        return inputs.water(100, lmax=args.lmax)
+    return inputs.alkane(args.ncarbon, lmax=args.lmax)
 
 
 # ---------------------------------------------------------------------------
@@ -139,10 +150,9 @@ def cpu_baseline(system, L, ncols):
     W = fmm.half_transform(system.basis, tr, Op, system.C, L)
     t1 = time.perf_counter()
     cols = list(range(ncols))
-    fmm.farfield(system, L=L, tree=tr, i_subset=cols)
+    fmm.farfield(system, L=L, tree=tr, i_subset=cols, Opair=Op, W=W)
     t2 = time.perf_counter()
-    # farfield() repeats step a0 and the half transform; subtract them once
-    t_cols = max((t2 - t1) - (t1 - t0), 1e-3)
+    t_cols = t2 - t1
     est = (t1 - t0) + t_cols * system.nocc / ncols
     del W, Op
     return {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
@@ -155,8 +165,7 @@ def cpu_baseline(system, L, ncols):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    from paper_1708_05353_gb300 import inputs
-    system = inputs.alkane(args.ncarbon, lmax=args.lmax)
+    system = make_system(args)
     vals = []
     for k in range(args.warmup + args.steps):
         cb = cpu_baseline(system, args.lmax, args.cpu_cols)
@@ -172,6 +181,82 @@ def run_reference(args, rank, world):
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_batch(args, rank, world, local):
+    """The uneven batch: graphene-like flake, chains of 50/100/200 carbons and
+    16 water clusters of 10-60 molecules, lmax 4, FP32 contractions, in one
+    persistent, graph-captured launch sequence with autotuned tiles; timed
+    against the same systems run one call after another."""
+    import torch
+    from paper_1708_05353_gb300 import inputs, occk
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = 4
+    systems = inputs.batch_workload(lmax=L)
+    ctx = occk.Context(local)
+    trees = []
+    for s_ in systems:
+        t = occk.Tree(ctx, s_.basis, depth=s_.depth, target_atoms_per_leaf=s_.target_atoms_per_leaf)
+        t.pair_multipoles(L)
+        trees.append(t)
+    prec = "fp64" if args.prec == "fp64" and args.batch_fp64 else "fp32"
+    b = occk.Batch(ctx, trees, [s_.nocc for s_ in systems], prec=prec)
+    for k, s_ in enumerate(systems):
+        c, _, _, ld = b.buffers(k)
+        occk.device_view(c, (s_.nocc, ld), torch.float64, dev).copy_(torch.tensor(s_.C.T, dtype=torch.float64))
+    cfg = b.tune(os.path.join(ROOT, "profiles", "batch_tune_cache.txt"))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(fn, n):
+        ev = []
+        for k in range(n):
+            flush.fill_(float(k))
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            ev.append((a, e))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(e) for a, e in ev) / n
+
+    for _ in range(max(args.warmup, 3)):
+        b.run(use_graph=True)
+    clocks = Clocks(local)
+    ms_graph = timed(lambda: b.run(use_graph=True), args.steps)
+    clk = clocks.stop()
+    ms_nograph = timed(lambda: b.run(use_graph=False), args.steps)
+    Cs = [occk.fortran(torch.tensor(s_.C, dtype=torch.float64, device=dev)) for s_ in systems]
+    Ks = [occk.empty_fortran(s_.basis.nao, s_.nocc, torch.float64, dev) for s_ in systems]
+    Es = torch.empty(len(systems), dtype=torch.float64, device=dev)
+
+    def seq():
+        for k in range(len(systems)):
+            occk.farfield_K(ctx, trees[k], Cs[k], prec=prec, K=Ks[k], Ex=Es[k])
+    for _ in range(2):
+        seq()
+    ms_seq = timed(seq, args.steps)
+    # errors of the batch against per-system FP64 runs
+    import numpy as np
+    Eb = occk.device_view(b.buffers(0)[2], (len(systems),), torch.float64, dev).cpu().numpy()
+    errs = []
+    for k in range(len(systems)):
+        occk.farfield_K(ctx, trees[k], Cs[k], prec="fp64", K=Ks[k], Ex=Es[k])
+    torch.cuda.synchronize()
+    E64 = Es.cpu().numpy()
+    errs = np.abs(Eb - E64)
+    line = {"metric": METRIC, "value": ms_graph * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "batch: flake C150H30, chains C50/C100/C200, 16 water clusters 10-60",
+                       "nsys": len(systems), "lmax": L, "tuned": cfg,
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "batch_graph_ms": ms_graph, "batch_no_graph_ms": ms_nograph, "sequential_calls_ms": ms_seq,
+            "speedup_vs_sequential": ms_seq / ms_graph, "max_abs_dE_vs_fp64_Eh": float(errs.max()),
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line, default=float), flush=True)
 
 
 def main():
@@ -193,7 +278,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    system = inputs.alkane(args.ncarbon, lmax=args.lmax)
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
+        return
+    system = make_system(args)
     L = args.lmax
     ctx = occk.Context(local)
     tree = occk.Tree(ctx, system.basis, depth=system.depth,
@@ -316,6 +404,39 @@ def main():
         "clocks": clk,
         "energy": float(Ex.item()),
     }
+    # ---- other precisions on the same workload: time and error against the
+    # FP64 GPU result (which the parity tests tie to the FP64 oracle)
+    if args.variants != "none":
+        E64 = None
+        K64 = None
+        if args.prec == "fp64":
+            E64 = float(Ex.item())
+            K64 = K.clone()
+        else:
+            occk.farfield_K(ctx, tree, Cf, prec="fp64", K=K, Ex=Ex)
+            E64 = float(Ex.item())
+            K64 = K.clone()
+        kmax = float(K64.abs().max().item())
+        var = {}
+        for vp in [v for v in args.variants.split(",") if v and v != args.prec]:
+            for _ in range(2):
+                occk.farfield_K(ctx, tree, Cf, prec=vp, K=K, Ex=Ex)
+            ev = []
+            for k in range(max(3, args.steps // 2)):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                occk.farfield_K(ctx, tree, Cf, prec=vp, K=K, Ex=Ex)
+                b.record(stream)
+                ev.append((a, b))
+            torch.cuda.synchronize()
+            vms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+            var[vp] = {"ms": round(vms, 4), "speedup_vs_fp64": round(ms_max / vms, 3) if args.prec == "fp64" else None,
+                       "tflops": round(total_flops / (vms * 1e-3) / 1e12, 3),
+                       "abs_dE_Eh": abs(float(Ex.item()) - E64),
+                       "rel_dK": float((K - K64).abs().max().item()) / kmax}
+        result["variants"] = var
+        result["variants_reference"] = "errors against the FP64 GPU path of the same run (E = %.10f Eh)" % E64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(system, L, args.cpu_cols)
     if rank == 0:

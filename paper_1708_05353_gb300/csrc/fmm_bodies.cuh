@@ -281,6 +281,70 @@ __device__ __forceinline__ void l2p_body(int bx, int by, int bz, const int* __re
     }
 }
 
+// FP64 step (e) with a 32-row x 128-column block tile (thread tile 2 x 8):
+// same sum as l2p_body, less padding on leaves with a few dozen AOs.
+__device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int* __restrict__ leaf_rowoff,
+                                              const double* __restrict__ W, const double* __restrict__ Mbox,
+                                              int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+    constexpr int BR = 32, BI = 128, BK = 8, TR = 2, TI = 8;
+    __shared__ double As[BK][BR + 1];
+    __shared__ double Bs[BK][BI + 1];
+    const int B = bz;
+    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+    const int r0 = bx * BR, i0 = by * BI;
+    if (r0 >= nr) return;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const size_t P = (size_t)nocc * nocc;
+    double acc[TR][TI];
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TI; ++b) acc[a][b] = 0.0;
+    for (int lm = 0; lm < nc; ++lm) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= lm) ++l;
+        const double w = (lm == l * l) ? 2.0 : (((lm - l * l) & 1) ? 4.0 : -4.0);
+        const double* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
+        const double* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
+        for (int k0 = 0; k0 < nocc; k0 += BK) {
+            {   // A: 32 rows x 8 columns, one element per thread
+                const int row = threadIdx.x / BK, kk = threadIdx.x % BK;
+                const int r = r0 + row, j = k0 + kk;
+                As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.0;
+            }
+            for (int e = threadIdx.x; e < BK * BI; e += 256) {   // B: 128 rows x 8 columns
+                const int row = e / BK, kk = e % BK;
+                const int i = i0 + row, j = k0 + kk;
+                Bs[kk][row] = (i < nocc && j < nocc) ? w * Ml[(size_t)i * nocc + j] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                double a[TR], b[TI];
+#pragma unroll
+                for (int q = 0; q < TR; ++q) a[q] = As[kk][ty * TR + q];
+#pragma unroll
+                for (int q = 0; q < TI; ++q) b[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+                for (int x = 0; x < TR; ++x)
+#pragma unroll
+                    for (int y = 0; y < TI; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < TR; ++x) {
+        const int r = r0 + ty * TR + x;
+        if (r >= nr) continue;
+#pragma unroll
+        for (int y = 0; y < TI; ++y) {
+            const int i = i0 + tx + 16 * y;
+            if (i < nocc) KB[(size_t)(rb0 + r) * nocc + i] = acc[x][y];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K[r + i*ldk] = sum over the leaf rows of AO r of KB[row][i], in FP64, and the
 // per-block partial of E = -1/2 sum_ri C_ri K_ri.

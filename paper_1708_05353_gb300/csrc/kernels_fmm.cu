@@ -60,6 +60,12 @@ k_l2p(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const T* __r
                                   leaf_store0, KB);
 }
 
+__global__ void __launch_bounds__(256)
+k_l2p_r32(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const double* __restrict__ Mbox,
+          int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+    body::l2p_rect_body(blockIdx.x, blockIdx.y, blockIdx.z, leaf_rowoff, W, Mbox, nocc, nrow, nc, leaf_store0, KB);
+}
+
 __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
                            const double* __restrict__ KB, int nao, int nocc, const double* __restrict__ C, int ldc,
                            double* __restrict__ K, int ldk, double* __restrict__ part) {
@@ -70,15 +76,18 @@ __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __rest
 // FMA throughput probe: 8 independent dependent chains per thread.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_fma_probe(T* out, int iters, T seed) {
-    T a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5,
-      a6 = a0 + 6, a7 = a0 + 7;
+__global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed) {
+    T a[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) a[q] = seed + T(threadIdx.x + q);
     const T m = T(0.999999), c = T(1e-7);
     for (int k = 0; k < iters; ++k) {
-        a0 = a0 * m + c; a1 = a1 * m + c; a2 = a2 * m + c; a3 = a3 * m + c;
-        a4 = a4 * m + c; a5 = a5 * m + c; a6 = a6 * m + c; a7 = a7 * m + c;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = a[q] * m + c;
     }
-    T s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s += a[q];
     if (s == T(-1.2345)) out[threadIdx.x] = s;
 }
 
@@ -185,7 +194,10 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (c) M2L: every box of levels 2..D, all levels in one launch
     mark(3);
-    if (tcm && nc <= 128) {
+    // tensor cores for M2L only where it is compute-bound (nc >= 49): below
+    // that the translation moves more bytes than it has FLOPs to hide them and
+    // runs in FP32 on the SIMT cores
+    if (tcm && nc >= 49 && nc <= 128) {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         cudaError_t e2 = tc_run_m2l(a.prec, (int)P, nc, a.L, a.first_box, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op,
                                     lmax_e, (const float*)ops, (const float*)Ob, (float*)Mb, a.box_scale,
@@ -212,10 +224,11 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
                                     a.nleaf, leaf_store0, a.max_rows, a.lscale, a.kb, a.err_word, s);
         if (e2 != cudaSuccess) return e2;
     } else if constexpr (sizeof(T) == 8) {
-        constexpr int BM = 64, BK = 8, TM = 4;
-        dim3 g((a.max_rows + BM - 1) / BM, (nocc + BM - 1) / BM, a.nleaf);
-        k_l2p<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, W, Mb, nocc, a.nrow, nc,
-                                                                 leaf_store0, a.kb);
+        // 32 AO rows x 128 orbitals per block: leaves hold ~70-600 AOs, and a
+        // 64-row tile would spend a third of the DFMA on padding
+        dim3 g((a.max_rows + 31) / 32, (nocc + 127) / 128, a.nleaf);
+        k_l2p_r32<<<g, 256, 0, s>>>(a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow, nc,
+                                    leaf_store0, a.kb);
     } else {
         constexpr int BM = 128, BK = 8, TM = 8;
         dim3 g((a.max_rows + BM - 1) / BM, (nocc + BM - 1) / BM, a.nleaf);
@@ -239,7 +252,7 @@ cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s) {
 }
 
 cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s) {
-    const int iters = 1 << 14;
+    const int iters = 1 << 13;
     const int blocks = sm_count * 8, threads = 256;
     void* buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, 1024 * 8);
@@ -261,7 +274,7 @@ cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s) {
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep > 0) best = std::min(best, ms);
     }
-    const double nfma = (double)blocks * threads * 8.0 * (prec == OCCK_FP64 ? iters : iters * 8.0);
+    const double nfma = (double)blocks * threads * 16.0 * (prec == OCCK_FP64 ? iters : iters * 8.0);
     *flops = 2.0 * nfma / (best * 1e-3);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -46,7 +46,12 @@ struct PrecT {
     static constexpr int KSTEP = (P == PM_TF32) ? 8 : 16;
     static constexpr int EPC = 16 / esz;             // elements per 16-byte chunk
     static constexpr uint32_t fmt = (P == PM_BF16 || P == PM_BF16X3) ? 1u : (P == PM_TF32 ? 2u : 0u);
+    // FP16 lo parts are stored scaled by 2^11 (they would otherwise fall into
+    // FP16 subnormals) and accumulate in a second TMEM accumulator that the
+    // epilogue adds back with weight 2^-11
+    static constexpr bool dual = (P == PM_FP16X3);
 };
+constexpr float kLoScale = 2048.f;
 
 // rank l of real-form component index c = l*l + ...
 __device__ __forceinline__ int lrank(int c) {
@@ -77,9 +82,29 @@ __device__ __forceinline__ void put_chunk(uint8_t* hi, uint8_t* lo, int row, int
         using S = typename std::conditional<(P == PM_BF16 || P == PM_BF16X3), SplitBF16, SplitFP16>::type;
         typename S::T h[8], l[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) S::split(v[q], h[q], l[q]);
+        for (int q = 0; q < 8; ++q) {
+            if constexpr (PrecT<P>::dual) {
+                h[q] = __float2half_rn(v[q]);
+                l[q] = __float2half_rn((v[q] - __half2float(h[q])) * kLoScale);
+            } else {
+                S::split(v[q], h[q], l[q]);
+            }
+        }
         *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<uint4*>(h);
         if constexpr (PrecT<P>::split) *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<uint4*>(l);
+    }
+}
+
+// Accumulator columns [col, col+16) of this warp's 32 lanes; for the dual
+// form add the scaled second accumulator N columns further on.
+template <int P>
+__device__ __forceinline__ void acc_ld16(uint32_t tmem, int warp, int col, int N, float* v) {
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+    if constexpr (PrecT<P>::dual) {
+        float w[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(col + N), w);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] += w[q] * (1.f / kLoScale);
     }
 }
 
@@ -100,7 +125,7 @@ struct EngineState {
 
 // Issue the MMAs of one stage (called by one thread).
 template <int P>
-__device__ __forceinline__ void issue_stage(uint8_t* stage, uint32_t tmem, uint32_t idesc, bool first) {
+__device__ __forceinline__ void issue_stage(uint8_t* stage, uint32_t tmem, uint32_t idesc, bool first, int N) {
     constexpr int T = Smem<P>::tile;
     const uint32_t a_hi = smem_u32(stage), b_hi = smem_u32(stage + T);
     const uint32_t a_lo = smem_u32(stage + 2 * T), b_lo = smem_u32(stage + 3 * T);
@@ -116,8 +141,9 @@ __device__ __forceinline__ void issue_stage(uint8_t* stage, uint32_t tmem, uint3
             mma_f16(tmem, dah, dbh, idesc, acc0);
             if constexpr (PrecT<P>::split) {
                 const uint64_t dal = smem_desc(a_lo + adv, kLBO, kSBO), dbl = smem_desc(b_lo + adv, kLBO, kSBO);
-                mma_f16(tmem, dah, dbl, idesc, 1u);
-                mma_f16(tmem, dal, dbh, idesc, 1u);
+                const uint32_t t2 = PrecT<P>::dual ? tmem + (uint32_t)N : tmem;
+                mma_f16(t2, dah, dbl, idesc, PrecT<P>::dual ? acc0 : 1u);
+                mma_f16(t2, dal, dbh, idesc, 1u);
             }
         }
     }
@@ -137,6 +163,7 @@ __device__ __forceinline__ void engine(typename Mode::Ctx& c, int N, uint32_t nc
     constexpr int BK = PrecT<P>::BK, EPC = PrecT<P>::EPC;
     static_assert(8 % EPC == 0, "chunk");
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if constexpr (PrecT<P>::dual) ncols *= 2;
     if (warp == 0) {
         tmem_alloc(&st.tmem, ncols);
         tmem_relinquish();
@@ -178,7 +205,7 @@ __device__ __forceinline__ void engine(typename Mode::Ctx& c, int N, uint32_t nc
         __syncthreads();
         if (t == 0) {
             fence_after_sync();
-            issue_stage<P>(stage, tmem, idesc, kc == 0);
+            issue_stage<P>(stage, tmem, idesc, kc == 0, N);
             mma_commit(&st.bar[s]);
         }
     }
@@ -239,7 +266,7 @@ struct ModeA2 {
         const int i = c.ti * 128 + warp * 32 + lane;
         for (int cc = 0; cc < 8; ++cc) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, v);
+            acc_ld16<P>(tmem, warp, cc * 16, 128, v);
             if (i < A.nocc) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -316,7 +343,7 @@ struct ModeL2P {
         const int r = c.r0 + warp * 32 + lane;
         for (int cc = 0; cc < 8; ++cc) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, v);
+            acc_ld16<P>(tmem, warp, cc * 16, 128, v);
             if (r < c.nr) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -399,7 +426,7 @@ struct ModeM2L {
         float* Mt = A.M + (size_t)(c.tgt - A.first_box) * A.nc * A.P;
         for (int cc = 0; cc * 16 < c.N; ++cc) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, v);
+            acc_ld16<P>(tmem, warp, cc * 16, c.N, v);
             if (p < A.P) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -460,7 +487,7 @@ struct ModeGemm {
         const int m = c.m0 + warp * 32 + lane;
         for (int cc = 0; cc < 8; ++cc) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, v);
+            acc_ld16<P>(tmem, warp, cc * 16, 128, v);
             if (m < G.M) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
