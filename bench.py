@@ -58,12 +58,13 @@ def make_system(args):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic FLOPs per stage (real form; the symmetric half of O^{ij} in a)
+# algorithmic FLOPs per stage (real form; only the symmetric half of the
+# occupied pairs in (a) O^{ij} and in the tree passes b-d)
 # ---------------------------------------------------------------------------
 def stage_flops(tree_info, rowoff, nocc, L, depth, level_off, nent, nm2m, nl2l, nm2l):
     nc = (L + 1) ** 2
     tl = sum((2 * l + 1) * (l + 1) ** 2 for l in range(L + 1))
-    P = nocc * nocc
+    P = nocc * (nocc + 1) // 2          # the tree passes need only pairs i <= j
     S = [rowoff[k + 1] - rowoff[k] for k in range(len(rowoff) - 1)]
     return {
         "a_half": 2.0 * nent * nocc * nc,

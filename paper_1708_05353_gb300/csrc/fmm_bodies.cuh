@@ -9,6 +9,13 @@
 namespace occk {
 namespace body {
 
+// Occupied pairs are stored once: p = (i, j) with i <= j, row-major upper
+// triangle (O^{ij} = O^{ji} and Mcal^{ij} = Mcal^{ji}).
+__host__ __device__ __forceinline__ size_t tri_index(int i, int j, int n) {
+    return (size_t)i * (size_t)(2 * n - i + 1) / 2 + (size_t)(j - i);
+}
+__host__ __device__ __forceinline__ size_t npairs(int n) { return (size_t)n * (size_t)(n + 1) / 2; }
+
 constexpr int kNcMax = 169;   // (12+1)^2
 
 // ---------------------------------------------------------------------------
@@ -124,7 +131,7 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
         }
         __syncthreads();
     }
-    const size_t P = (size_t)nocc * nocc;
+    const size_t P = npairs(nocc);
     T* O = Obox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
 #pragma unroll
     for (int x = 0; x < TM; ++x) {
@@ -133,9 +140,8 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
 #pragma unroll
         for (int y = 0; y < TM; ++y) {
             int j = j0 + tx * TM + y;
-            if (j >= nocc) continue;
-            O[(size_t)i * nocc + j] = acc[x][y];
-            if (ti != tj) O[(size_t)j * nocc + i] = acc[x][y];
+            if (j >= nocc || j < i) continue;
+            O[tri_index(i, j, nocc)] = acc[x][y];
         }
     }
 }
@@ -233,7 +239,7 @@ __device__ __forceinline__ void l2p_body(int bx, int by, int bz, const int* __re
     const int r0 = bx * BM, i0 = by * BM;
     if (r0 >= nr) return;
     const int tx = threadIdx.x % (BM / TM), ty = threadIdx.x / (BM / TM);
-    const size_t P = (size_t)nocc * nocc;
+    const size_t P = npairs(nocc);
     T acc[TM][TM];
 #pragma unroll
     for (int a = 0; a < TM; ++a)
@@ -246,11 +252,16 @@ __device__ __forceinline__ void l2p_body(int bx, int by, int bz, const int* __re
         const T* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
         const T* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
         for (int k0 = 0; k0 < nocc; k0 += BK) {
+            const bool below = k0 + BK <= i0;   // every j < every i: packed rows j, contiguous in i
             for (int e = threadIdx.x; e < BK * BM; e += NTH) {
                 int row = e / BK, kk = e - row * BK;
-                int r = r0 + row, i = i0 + row, j = k0 + kk;
+                int r = r0 + row, j = k0 + kk;
                 As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : T(0);
-                Bs[kk][row] = (i < nocc && j < nocc) ? w * Ml[(size_t)i * nocc + j] : T(0);
+                int rb = below ? e % BM : row, kb = below ? e / BM : kk;
+                int i = i0 + rb, jb = k0 + kb;
+                Bs[kb][rb] = (i < nocc && jb < nocc)
+                                 ? w * Ml[i <= jb ? tri_index(i, jb, nocc) : tri_index(jb, i, nocc)]
+                                 : T(0);
             }
             __syncthreads();
 #pragma unroll
@@ -294,7 +305,7 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
     const int r0 = bx * BR, i0 = by * BI;
     if (r0 >= nr) return;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const size_t P = (size_t)nocc * nocc;
+    const size_t P = npairs(nocc);
     double acc[TR][TI];
 #pragma unroll
     for (int a = 0; a < TR; ++a)
@@ -312,10 +323,15 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
                 const int r = r0 + row, j = k0 + kk;
                 As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.0;
             }
-            for (int e = threadIdx.x; e < BK * BI; e += 256) {   // B: 128 rows x 8 columns
-                const int row = e / BK, kk = e % BK;
+            // B: 128 rows (i) x 8 columns (j) of the symmetric Mcal, read from
+            // the packed upper triangle; thread order follows the stored rows
+            const bool below = k0 + BK <= i0;
+            for (int e = threadIdx.x; e < BK * BI; e += 256) {
+                const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
                 const int i = i0 + row, j = k0 + kk;
-                Bs[kk][row] = (i < nocc && j < nocc) ? w * Ml[(size_t)i * nocc + j] : 0.0;
+                Bs[kk][row] = (i < nocc && j < nocc)
+                                  ? w * Ml[i <= j ? tri_index(i, j, nocc) : tri_index(j, i, nocc)]
+                                  : 0.0;
             }
             __syncthreads();
 #pragma unroll

@@ -686,7 +686,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     const int first = D >= 2 ? t->level_off[2] : nbox;
     const int nleaf = (int)t->leaf_rowoff.size() - 1;
     const int nrow = (int)t->leaf_aos.size();
-    const size_t P = (size_t)nocc * nocc;
+    const size_t P = (size_t)nocc * (nocc + 1) / 2;   // stored occupied pairs i <= j
     const size_t es = prec == OCCK_FP64 ? 8 : 4;
     int max_rows = 0;
     for (int B = 0; B < nleaf; ++B) max_rows = std::max(max_rows, t->leaf_rowoff[B + 1] - t->leaf_rowoff[B]);
@@ -802,21 +802,37 @@ extern "C" occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* t, int w
     if (ctx->last_tree != t) return fail(ctx, OCCK_ERR_STATE, "last run used another tree");
     const int nbox = (int)t->parent.size();
     const int nc = occk::ncomp(ctx->last_lmax);
-    const size_t P = (size_t)ctx->last_nocc * ctx->last_nocc;
+    const int no = ctx->last_nocc;
+    const size_t P = (size_t)no * no;
+    const size_t Ps = (size_t)no * (no + 1) / 2;
     const size_t n = (size_t)nbox * nc * P;
     if (bytes != n * 8) return fail(ctx, OCCK_ERR_SHAPE, "size mismatch");
     std::memset(out, 0, bytes);
-    const size_t nst = (size_t)(nbox - ctx->last_first_box) * nc * P;
+    const size_t nst = (size_t)(nbox - ctx->last_first_box) * nc * Ps;
     const void* src = what == OCCK_DBG_OBOX ? ctx->obox.p : ctx->mbox.p;
-    double* dst = (double*)out + (size_t)ctx->last_first_box * nc * P;
+    std::vector<double> tmp(nst);
     if (ctx->last_prec == OCCK_FP64) {
-        e = cudaMemcpy(dst, src, nst * 8, cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(tmp.data(), src, nst * 8, cudaMemcpyDeviceToHost);
     } else {
-        std::vector<float> tmp(nst);
-        e = cudaMemcpy(tmp.data(), src, nst * 4, cudaMemcpyDeviceToHost);
-        for (size_t i = 0; i < nst; ++i) dst[i] = tmp[i];
+        std::vector<float> tf(nst);
+        e = cudaMemcpy(tf.data(), src, nst * 4, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < nst; ++i) tmp[i] = tf[i];
     }
-    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "copy");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy");
+    // stored upper triangle -> full i,j square
+    double* dst = (double*)out;
+    for (int b = ctx->last_first_box; b < nbox; ++b)
+        for (int c = 0; c < nc; ++c) {
+            const double* sp = tmp.data() + ((size_t)(b - ctx->last_first_box) * nc + c) * Ps;
+            double* dp = dst + ((size_t)b * nc + c) * P;
+            size_t q = 0;
+            for (int i = 0; i < no; ++i)
+                for (int j = i; j < no; ++j, ++q) {
+                    dp[(size_t)i * no + j] = sp[q];
+                    dp[(size_t)j * no + i] = sp[q];
+                }
+        }
+    return OCCK_OK;
 }
 
 extern "C" occk_status occk_probe_fma_peak(occk_ctx* ctx, int prec, double* flops, void* stream) {
@@ -1068,9 +1084,9 @@ extern "C" occk_status occk_edge_features(occk_ctx* ctx, const occk_tree* t, flo
     const int nbox = (int)t->parent.size(), L = t->lmax;
     cudaError_t e = ensure(ctx->nrm, sizeof(double) * (size_t)nbox * (L + 1));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "norm workspace");
-    const long long P = (long long)ctx->last_nocc * ctx->last_nocc;
+    const long long P = (long long)ctx->last_nocc * (ctx->last_nocc + 1) / 2;
     e = occk::edge_features(ctx->last_prec == OCCK_FP64, ctx->obox.p, ctx->last_first_box, nbox,
-                            occk::ncomp(L), L, P, (int)t->m2l_tgt.size(), t->dev.m2l_tgt, t->dev.m2l_src,
+                            occk::ncomp(L), L, P, ctx->last_nocc, (int)t->m2l_tgt.size(), t->dev.m2l_tgt, t->dev.m2l_src,
                             t->dev.box_key, t->dev.box_level, t->dev.hlev, t->depth, (double*)ctx->nrm.p, F,
                             (cudaStream_t)stream);
     return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_edge_features");
@@ -1084,8 +1100,9 @@ extern "C" occk_status occk_edge_energies(occk_ctx* ctx, const occk_tree* t, dou
     const int L = t->lmax, nc = occk::ncomp(L), ne = (int)t->m2l_tgt.size();
     cudaError_t e = ensure(ctx->gram, sizeof(double) * (size_t)std::max(ne, 1) * nc * nc);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "Gram workspace");
-    const long long P = (long long)ctx->last_nocc * ctx->last_nocc;
-    e = occk::edge_energies(ctx->last_prec == OCCK_FP64, ctx->obox.p, ctx->last_first_box, nc, L, P, ne,
+    const long long P = (long long)ctx->last_nocc * (ctx->last_nocc + 1) / 2;
+    e = occk::edge_energies(ctx->last_prec == OCCK_FP64, ctx->obox.p, ctx->last_first_box, nc, L, P,
+                            ctx->last_nocc, ne,
                             t->dev.m2l_tgt, t->dev.m2l_src, t->dev.ops, t->dev.m2l_op, (double*)ctx->gram.p, E,
                             (cudaStream_t)stream);
     return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_edge_energies");

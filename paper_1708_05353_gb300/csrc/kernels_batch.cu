@@ -394,7 +394,7 @@ extern "C" occk_status occk_batch_create(occk_ctx* ctx, int nsys, occk_tree* con
         const occk_tree* t = trees[s];
         const int nbox = (int)t->parent.size();
         const int first = t->depth >= 2 ? t->level_off[2] : nbox;
-        const size_t P = (size_t)nocc[s] * nocc[s];
+        const size_t P = (size_t)nocc[s] * (nocc[s] + 1) / 2;   // stored pairs i <= j
         const size_t nrow = t->leaf_aos.size();
         o[s].C = take(8 * (size_t)t->nao * nocc[s]);
         o[s].K = take(8 * (size_t)t->nao * nocc[s]);
@@ -432,7 +432,7 @@ extern "C" occk_status occk_batch_create(occk_ctx* ctx, int nsys, occk_tree* con
         int mr = 0;
         for (int B = 0; B < d.nleaf; ++B) mr = std::max(mr, t->leaf_rowoff[B + 1] - t->leaf_rowoff[B]);
         d.max_rows = mr;
-        d.P = (long long)nocc[s] * nocc[s];
+        d.P = (long long)nocc[s] * (nocc[s] + 1) / 2;
         d.C = (const double*)(base + o[s].C);
         d.K = (double*)(base + o[s].K);
         auto& td = t->dev;

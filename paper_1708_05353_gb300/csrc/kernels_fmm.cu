@@ -1,11 +1,12 @@
 // Steps (a)-(e) of the far-field occupied exchange on SIMT cores, in FP64
 // (DFMA) or FP32 (FFMA); K and the energy are always reduced in FP64.
 //
-// Layouts in HBM (P = nocc^2 occupied pairs, pair index p = i*nocc + j):
+// Layouts in HBM (P = nocc(nocc+1)/2 stored occupied pairs i <= j, packed
+// row-major upper triangle; W and KB keep every orbital):
 //   Ct   [nao][nocc]            row-major copy of C
 //   W    [nc][nrow][nocc]       O^{rj,X}_lm for the AO set S_B of every leaf,
 //                               leaves stacked (row = leaf_rowoff[B] + local)
-//   Obox [box][nc][P]           O^{ij,X}_lm for boxes of levels 2..D
+//   Obox [box][nc][P]           O^{ij,X}_lm (i <= j) for boxes of levels 2..D
 //   Mbox [box][nc][P]           Mcal^{ij}_lm(X), same boxes
 //   KB   [nrow][nocc]           per-leaf partial K rows (FP64)
 // Every pair-indexed access is coalesced along p (or along j).
@@ -121,7 +122,7 @@ void launch_translate(int lmc, dim3 g, cudaStream_t s, Args... args) {
 template <typename T>
 cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     const int nocc = a.nocc, nc = a.nc, D = a.depth;
-    const long long P = (long long)nocc * nocc;
+    const long long P = (long long)body::npairs(nocc);   // stored pairs i <= j
     auto mark = [&](int k) {
         if (a.ev) cudaEventRecord(a.ev[k], s);
     };
@@ -184,7 +185,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     // budgeted choice; M2L then reads the per-edge ranks
     const int* lmax_e = a.m2l_lmax;
     if (a.learned) {
-        cudaError_t e2 = edge_features(sizeof(T) == 8, Ob, a.first_box, a.nbox, nc, a.L, P, a.nm2l, a.m2l_tgt,
+        cudaError_t e2 = edge_features(sizeof(T) == 8, Ob, a.first_box, a.nbox, nc, a.L, P, nocc, a.nm2l, a.m2l_tgt,
                                        a.m2l_src, a.box_key, a.box_level, a.hlev, D, a.nrm, a.feat, s);
         if (e2 == cudaSuccess)
             e2 = mlp_predict_fp16(a.mlp_prm, (__half*)a.mlp_h, a.mlp_norm, a.feat, a.nm2l, a.pred, s);

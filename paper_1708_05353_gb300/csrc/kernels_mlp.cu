@@ -10,7 +10,8 @@
 // over M2L edges because M2M and L2L are exact re-expansions, so
 //   e_edge(L') = -sum_p sum_{c,c' <= L'} w_c T_e[c][c'] O_t[c][p] O_s[c'][p]
 // with w the real-form weights (1, 2, -2) and p all occupied pairs; it is
-// evaluated through the pair-summed Gram matrix G_e = O_t O_s^T.
+// evaluated through the pair-summed Gram matrix G_e = O_t O_s^T over the
+// stored pairs i <= j, off-diagonal pairs counted twice.
 //
 // Rank choice: minimise sum_e (L_e+1)^4 (the M2L cost) subject to
 // sum_e err_e(L_e) <= tau, by bisection on the Lagrange multiplier; edges
@@ -211,19 +212,34 @@ __global__ void k_to_half(const float* __restrict__ a, __half* __restrict__ b, i
 // ---------------------------------------------------------------------------
 // Per-box multipole norms: nrm[box][l] = sqrt(sum_{c in rank l} sum_p O[box][c][p]^2)
 // ---------------------------------------------------------------------------
+// Pairs are stored once (i <= j); a stored off-diagonal pair stands for two
+// entries of the full i,j square, so sums over pairs weigh it by 2.
+__device__ __forceinline__ double pair_weight(long long p, int n) {
+    // p is diagonal iff p == i(2n - i + 1)/2 for some i; solve for i
+    const double b = 2.0 * n + 1.0;
+    int i = (int)floor((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
+    if (i < 0) i = 0;
+    if (i > n - 1) i = n - 1;
+    while (i > 0 && (long long)i * (2 * n - i + 1) / 2 > p) --i;
+    while (i < n - 1 && (long long)(i + 1) * (2 * n - i) / 2 <= p) ++i;
+    return ((long long)i * (2 * n - i + 1) / 2 == p) ? 1.0 : 2.0;
+}
+
 template <typename T>
-__global__ void k_box_norms(const T* __restrict__ O, int first_box, int nc, int L, long long P,
+__global__ void k_box_norms(const T* __restrict__ O, int first_box, int nc, int L, long long P, int nocc,
                             double* __restrict__ nrm) {
     __shared__ double red[256];
     const int box = first_box + blockIdx.x;
     const int l = blockIdx.y;
     double acc = 0.0;
     const T* base = O + (size_t)blockIdx.x * nc * P;
-    for (int c = l * l; c < (l + 1) * (l + 1); ++c)
-        for (long long p = threadIdx.x; p < P; p += blockDim.x) {
+    for (long long p = threadIdx.x; p < P; p += blockDim.x) {
+        const double w = pair_weight(p, nocc);
+        for (int c = l * l; c < (l + 1) * (l + 1); ++c) {
             const double v = (double)base[(size_t)c * P + p];
-            acc += v * v;
+            acc += w * v * v;
         }
+    }
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
@@ -277,7 +293,7 @@ __global__ void k_edge_features(int nedge, const int* __restrict__ tgt, const in
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_edge_gram(const int* __restrict__ tgt, const int* __restrict__ src, const T* __restrict__ O,
-                            int first_box, int nc, long long P, int ntile, int nslice,
+                            int first_box, int nc, long long P, int nocc, int ntile, int nslice,
                             double* __restrict__ G) {
     __shared__ double At[16][65], Bs[16][65];
     const int e = blockIdx.x;
@@ -296,7 +312,7 @@ __global__ void k_edge_gram(const int* __restrict__ tgt, const int* __restrict__
             const int r = x / 64, q = x % 64;
             const long long p = pb + q;
             const bool pv = p < p1;
-            At[r][q] = (pv && c0 + r < nc) ? (double)Ot[(size_t)(c0 + r) * P + p] : 0.0;
+            At[r][q] = (pv && c0 + r < nc) ? pair_weight(p, nocc) * (double)Ot[(size_t)(c0 + r) * P + p] : 0.0;
             Bs[r][q] = (pv && d0 + r < nc) ? (double)Os[(size_t)(d0 + r) * P + p] : 0.0;
         }
         __syncthreads();
@@ -431,20 +447,21 @@ cudaError_t mlp_predict_fp16(const float* prm, __half* prm_h, const float* norm,
 }
 
 cudaError_t edge_features(bool fp64, const void* O, int first_box, int nbox, int nc, int L, long long P,
-                          int nedge, const int* tgt, const int* src, const int* box_key, const int* box_level,
+                          int nocc, int nedge, const int* tgt, const int* src, const int* box_key, const int* box_level,
                           const double* hlev, int depth, double* nrm, float* F, cudaStream_t s) {
     const int nst = nbox - first_box;
     if (nst <= 0 || nedge == 0) return cudaSuccess;
     dim3 g(nst, L + 1);
     if (fp64)
-        k_box_norms<double><<<g, 256, 0, s>>>((const double*)O, first_box, nc, L, P, nrm);
+        k_box_norms<double><<<g, 256, 0, s>>>((const double*)O, first_box, nc, L, P, nocc, nrm);
     else
-        k_box_norms<float><<<g, 256, 0, s>>>((const float*)O, first_box, nc, L, P, nrm);
+        k_box_norms<float><<<g, 256, 0, s>>>((const float*)O, first_box, nc, L, P, nocc, nrm);
     k_edge_features<<<(nedge + 127) / 128, 128, 0, s>>>(nedge, tgt, src, box_key, box_level, hlev, depth, L, nrm, F);
     return cudaGetLastError();
 }
 
-cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L, long long P, int nedge,
+cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L, long long P, int nocc,
+                          int nedge,
                           const int* tgt, const int* src, const double* ops, const int* opidx, double* G,
                           double* out, cudaStream_t s) {
     if (nedge == 0) return cudaSuccess;
@@ -454,9 +471,9 @@ cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L
     const int nslice = (int)std::min<long long>(64, std::max<long long>(1, P / 4096));
     dim3 g(nedge, ntile * ntile, nslice);
     if (fp64)
-        k_edge_gram<double><<<g, 256, 0, s>>>(tgt, src, (const double*)O, first_box, nc, P, ntile, nslice, G);
+        k_edge_gram<double><<<g, 256, 0, s>>>(tgt, src, (const double*)O, first_box, nc, P, nocc, ntile, nslice, G);
     else
-        k_edge_gram<float><<<g, 256, 0, s>>>(tgt, src, (const float*)O, first_box, nc, P, ntile, nslice, G);
+        k_edge_gram<float><<<g, 256, 0, s>>>(tgt, src, (const float*)O, first_box, nc, P, nocc, ntile, nslice, G);
     k_edge_energy<<<nedge, 256, 0, s>>>(G, ops, opidx, nc, L, out);
     return cudaGetLastError();
 }

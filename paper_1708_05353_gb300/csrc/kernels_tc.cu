@@ -260,7 +260,7 @@ struct ModeA2 {
     }
     __device__ static void epilogue(const Ctx& c, int warp, int lane, uint32_t tmem, bool valid) {
         const A2Args& A = *c.a;
-        const size_t P2 = (size_t)A.nocc * A.nocc;
+        const size_t P2 = (size_t)A.nocc * (A.nocc + 1) / 2;   // stored pairs i <= j
         float* O = A.Obox + ((size_t)(A.leaf_store0 + c.B) * A.nc + c.lm) * P2;
         const float inv = 1.0f / A.lscale[c.lm];
         const int i = c.ti * 128 + warp * 32 + lane;
@@ -271,11 +271,8 @@ struct ModeA2 {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int j = c.tj * 128 + cc * 16 + q;
-                    if (j < A.nocc) {
-                        const float x = valid ? v[q] * inv : 0.f;
-                        O[(size_t)i * A.nocc + j] = x;
-                        if (c.ti != c.tj) O[(size_t)j * A.nocc + i] = x;
-                    }
+                    if (j < A.nocc && j >= i)
+                        O[(size_t)i * (2 * A.nocc - i + 1) / 2 + (j - i)] = valid ? v[q] * inv : 0.f;
                 }
             }
         }
@@ -327,14 +324,17 @@ struct ModeL2P {
         const float sa = A.lscale[lm], sb = w / A.lscale[lm];
         const int r = c.r0 + t, i = c.i0 + t;
         const float* Wr = A.W + ((size_t)lm * A.nrow + c.rb0 + r) * A.nocc;
-        const float* Mi = A.Mbox + (((size_t)(A.leaf_store0 + c.B) * A.nc + lm) * A.nocc + i) * A.nocc;
+        const size_t P2 = (size_t)A.nocc * (A.nocc + 1) / 2;
+        const float* Ml = A.Mbox + ((size_t)(A.leaf_store0 + c.B) * A.nc + lm) * P2;
         const bool rv = r < c.nr, iv = i < A.nocc;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int j = j0 + k;
             const bool jv = j < A.nocc;
             a[k] = (rv && jv) ? Wr[j] * sa : 0.f;
-            b[k] = (iv && jv) ? Mi[j] * sb : 0.f;
+            // Mcal^{ij} from the packed upper triangle
+            const int lo = i < j ? i : j, hi = i < j ? j : i;
+            b[k] = (iv && jv) ? Ml[(size_t)lo * (2 * A.nocc - lo + 1) / 2 + (hi - lo)] * sb : 0.f;
         }
         hasb = true;
     }

@@ -189,9 +189,10 @@ cudaError_t mlp_adam(float* prm, const float* g, float* m, float* v, int t, floa
 cudaError_t mlp_predict_fp16(const float* prm, __half* prm_h, const float* norm, const float* X, int n,
                              float* Y, cudaStream_t s);
 cudaError_t edge_features(bool fp64, const void* O, int first_box, int nbox, int nc, int L, long long P,
-                          int nedge, const int* tgt, const int* src, const int* box_key, const int* box_level,
+                          int nocc, int nedge, const int* tgt, const int* src, const int* box_key, const int* box_level,
                           const double* hlev, int depth, double* nrm, float* F, cudaStream_t s);
-cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L, long long P, int nedge,
+cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L, long long P, int nocc,
+                          int nedge,
                           const int* tgt, const int* src, const double* ops, const int* opidx, double* G,
                           double* out, cudaStream_t s);
 cudaError_t select_ranks(const float* pred, int nedge, int Lmax, double tau, int* ranks, cudaStream_t s);
