@@ -334,6 +334,8 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
                                   : 0.0;
             }
             __syncthreads();
+            // a warp covers rows r0 + 4w .. r0 + 4w + 3: skip warps past the leaf's rows
+            if (r0 + (threadIdx.x >> 5) * 2 * TR < nr) {
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
                 double a[TR], b[TI];
@@ -345,6 +347,7 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
                 for (int x = 0; x < TR; ++x)
 #pragma unroll
                     for (int y = 0; y < TI; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+            }
             }
             __syncthreads();
         }

@@ -95,19 +95,6 @@ __device__ __forceinline__ void put_chunk(uint8_t* hi, uint8_t* lo, int row, int
     }
 }
 
-// Accumulator columns [col, col+16) of this warp's 32 lanes; for the dual
-// form add the scaled second accumulator N columns further on.
-template <int P>
-__device__ __forceinline__ void acc_ld16(uint32_t tmem, int warp, int col, int N, float* v) {
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
-    if constexpr (PrecT<P>::dual) {
-        float w[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(col + N), w);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] += w[q] * (1.f / kLoScale);
-    }
-}
-
 // Shared-memory plan: per stage A_hi, A_lo, B_hi, B_lo tiles of 128 rows.
 template <int P>
 struct Smem {
@@ -156,16 +143,43 @@ __device__ __forceinline__ void issue_stage(uint8_t* stage, uint32_t tmem, uint3
 //                                              of A and B in stage kc
 //   Mode::epilogue(ctx, warp, lane, tmem, valid)
 // ---------------------------------------------------------------------------
-template <int P, class Mode>
-__device__ __forceinline__ void engine(typename Mode::Ctx& c, int N, uint32_t ncols, int* err_word) {
+// Add the accumulator buffer at `base` (this warp's 32 lanes, N columns) to
+// the thread's FP32 registers; the dual form adds its scaled second half.
+template <int P, int N>
+__device__ __forceinline__ void flush_acc(uint32_t base, int warp, float* acc) {
+#pragma unroll
+    for (int cc = 0; cc < N / 16; ++cc) {
+        float v[16];
+        tmem_ld16(base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16), v);
+        if constexpr (PrecT<P>::dual) {
+            float w[16];
+            tmem_ld16(base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(N + cc * 16), w);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] += w[q] * (1.f / kLoScale);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[cc * 16 + q] += v[q];
+    }
+}
+
+// The tensor core accumulates in FP32 with a bias toward zero that grows with
+// the number of products in one accumulation chain (about -2e-5 relative at
+// K = 4096).  So every stage (64 K elements of 16-bit, 32 of TF32) starts a
+// fresh accumulator in one of two TMEM buffers, and while the next stage's MMAs
+// run, the threads add the finished buffer into FP32 registers (round to
+// nearest): the chain never exceeds one stage.
+template <int P, int N, class Mode>
+__device__ __forceinline__ void engine(typename Mode::Ctx& c, int* err_word) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ EngineState st;
     constexpr int BK = PrecT<P>::BK, EPC = PrecT<P>::EPC;
     static_assert(8 % EPC == 0, "chunk");
+    static_assert(N % 16 == 0 && N <= 128, "N");
+    constexpr uint32_t kBuf = (uint32_t)N * (PrecT<P>::dual ? 2u : 1u);   // columns per buffer
+    constexpr uint32_t kCols = (2 * kBuf <= 32) ? 32u : (2 * kBuf <= 64 ? 64u : (2 * kBuf <= 128 ? 128u : (2 * kBuf <= 256 ? 256u : 512u)));
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    if constexpr (PrecT<P>::dual) ncols *= 2;
     if (warp == 0) {
-        tmem_alloc(&st.tmem, ncols);
+        tmem_alloc(&st.tmem, kCols);
         tmem_relinquish();
     }
     if (t == 0) {
@@ -180,6 +194,9 @@ __device__ __forceinline__ void engine(typename Mode::Ctx& c, int N, uint32_t nc
     const uint32_t tmem = st.tmem;
     const uint32_t idesc = instr_desc(128, N, PrecT<P>::fmt);
     const int nk = Mode::nchunks(c);
+    float acc[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc[q] = 0.f;
     bool ok = true;
     for (int kc = 0; kc < nk; ++kc) {
         const int s = kc & 1;
@@ -205,25 +222,34 @@ __device__ __forceinline__ void engine(typename Mode::Ctx& c, int N, uint32_t nc
         __syncthreads();
         if (t == 0) {
             fence_after_sync();
-            issue_stage<P>(stage, tmem, idesc, kc == 0, N);
+            issue_stage<P>(stage, tmem + (uint32_t)(kc & 1) * kBuf, idesc, true, N);
             mma_commit(&st.bar[s]);
+        }
+        if (kc >= 1) {   // flush the previous stage's buffer while this stage's MMAs run
+            const int pk = kc - 1;
+            if (!mbar_wait_bounded(&st.bar[pk & 1], (pk >> 1) & 1, kWaitLimit)) ok = false;
+            fence_after_sync();
+            if (ok) flush_acc<P, N>(tmem + (uint32_t)(pk & 1) * kBuf, warp, acc);
+            fence_before_sync();
         }
     }
     if (nk > 0) {
-        if (!mbar_wait_bounded(&st.bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kWaitLimit)) ok = false;
-        // the other stage's last commit precedes it, so it is complete too
+        const int pk = nk - 1;
+        if (!mbar_wait_bounded(&st.bar[pk & 1], (pk >> 1) & 1, kWaitLimit)) ok = false;
+        fence_after_sync();
+        if (ok) flush_acc<P, N>(tmem + (uint32_t)(pk & 1) * kBuf, warp, acc);
     }
     if (!ok) atomicExch(&st.err, 1);
-    fence_after_sync();
+    fence_before_sync();
     __syncthreads();
     if (st.err) {
         if (t == 0) atomicExch(err_word, 1);
     } else {
-        Mode::epilogue(c, warp, lane, tmem, nk > 0);
+        Mode::template epilogue<N>(c, warp, lane, acc, nk > 0);
     }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, ncols);
+    if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
 // ===========================================================================
@@ -258,15 +284,16 @@ struct ModeA2 {
         }
         hasb = true;
     }
-    __device__ static void epilogue(const Ctx& c, int warp, int lane, uint32_t tmem, bool valid) {
+    template <int N>
+    __device__ static void epilogue(const Ctx& c, int warp, int lane, const float* acc, bool valid) {
         const A2Args& A = *c.a;
         const size_t P2 = (size_t)A.nocc * (A.nocc + 1) / 2;   // stored pairs i <= j
         float* O = A.Obox + ((size_t)(A.leaf_store0 + c.B) * A.nc + c.lm) * P2;
         const float inv = 1.0f / A.lscale[c.lm];
         const int i = c.ti * 128 + warp * 32 + lane;
-        for (int cc = 0; cc < 8; ++cc) {
-            float v[16];
-            acc_ld16<P>(tmem, warp, cc * 16, 128, v);
+#pragma unroll
+        for (int cc = 0; cc < N / 16; ++cc) {
+            const float* v = acc + cc * 16;
             if (i < A.nocc) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -294,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_a2(A2Args args, int* err) {
     c.tj = ti + tt;
     c.rb0 = args.leaf_rowoff[c.B];
     c.nr = args.leaf_rowoff[c.B + 1] - c.rb0;
-    engine<P, ModeA2<P>>(c, 128, 128, err);
+    engine<P, 128, ModeA2<P>>(c, err);
 }
 
 // ===========================================================================
@@ -338,12 +365,13 @@ struct ModeL2P {
         }
         hasb = true;
     }
-    __device__ static void epilogue(const Ctx& c, int warp, int lane, uint32_t tmem, bool valid) {
+    template <int N>
+    __device__ static void epilogue(const Ctx& c, int warp, int lane, const float* acc, bool valid) {
         const L2PArgs& A = *c.a;
         const int r = c.r0 + warp * 32 + lane;
-        for (int cc = 0; cc < 8; ++cc) {
-            float v[16];
-            acc_ld16<P>(tmem, warp, cc * 16, 128, v);
+#pragma unroll
+        for (int cc = 0; cc < N / 16; ++cc) {
+            const float* v = acc + cc * 16;
             if (r < c.nr) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -366,7 +394,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_l2p(L2PArgs args, int* err) {
     c.i0 = blockIdx.y * 128;
     c.kpl = (args.nocc + PrecT<P>::BK - 1) / PrecT<P>::BK;
     if (c.r0 >= c.nr) return;   // uniform per block
-    engine<P, ModeL2P<P>>(c, 128, 128, err);
+    engine<P, 128, ModeL2P<P>>(c, err);
 }
 
 // ===========================================================================
@@ -420,13 +448,14 @@ struct ModeM2L {
             }
         }
     }
-    __device__ static void epilogue(const Ctx& c, int warp, int lane, uint32_t tmem, bool valid) {
+    template <int N>
+    __device__ static void epilogue(const Ctx& c, int warp, int lane, const float* acc, bool valid) {
         const M2LArgs& A = *c.a;
         const int p = c.p0 + warp * 32 + lane;
         float* Mt = A.M + (size_t)(c.tgt - A.first_box) * A.nc * A.P;
-        for (int cc = 0; cc * 16 < c.N; ++cc) {
-            float v[16];
-            acc_ld16<P>(tmem, warp, cc * 16, c.N, v);
+#pragma unroll
+        for (int cc = 0; cc < N / 16; ++cc) {
+            const float* v = acc + cc * 16;
             if (p < A.P) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -452,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_m2l(M2LArgs args, int* err) {
     c.spow[0] = 1.f;
     for (int k = 1; k < 16; ++k) c.spow[k] = c.spow[k - 1] * sd;
     for (int k = 0; k < 16; ++k) c.inv_spow[k] = 1.f / c.spow[k];
-    engine<P, ModeM2L<P>>(c, N, N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256)), err);
+    engine<P, N, ModeM2L<P>>(c, err);
 }
 
 // ===========================================================================
@@ -482,12 +511,13 @@ struct ModeGemm {
         }
         hasb = true;
     }
-    __device__ static void epilogue(const Ctx& c, int warp, int lane, uint32_t tmem, bool valid) {
+    template <int N>
+    __device__ static void epilogue(const Ctx& c, int warp, int lane, const float* acc, bool valid) {
         const GemmArgs& G = *c.a;
         const int m = c.m0 + warp * 32 + lane;
-        for (int cc = 0; cc < 8; ++cc) {
-            float v[16];
-            acc_ld16<P>(tmem, warp, cc * 16, 128, v);
+#pragma unroll
+        for (int cc = 0; cc < N / 16; ++cc) {
+            const float* v = acc + cc * 16;
             if (m < G.M) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -505,7 +535,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(GemmArgs args, int* err) {
     c.a = &args;
     c.m0 = blockIdx.x * 128;
     c.n0 = blockIdx.y * 128;
-    engine<P, ModeGemm<P>>(c, 128, 128, err);
+    engine<P, 128, ModeGemm<P>>(c, err);
 }
 
 template <int P>

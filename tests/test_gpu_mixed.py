@@ -67,3 +67,20 @@ def test_mixed_farfield_water(ctx, water_ref, prec):
     print(f"far field {prec}: max|dK|/max|K| = {err:.2e}, |dE| = {abs(E - Er):.2e} Eh (E = {Er:.8f})")
     assert err < K_BOUND.get(prec, 1e-4)
     assert abs(E - Er) <= K_BOUND.get(prec, 1e-4) * abs(Er)
+
+
+@pytest.mark.parametrize("prec,bound", [("fp16x3", 5e-7), ("bf16x3", 2e-6), ("tf32", 2e-5)])
+def test_tc_long_sum_unbiased(ctx, prec, bound):
+    """The tensor core's FP32 accumulation is biased toward zero over long
+    chains; the engine restarts the accumulator every stage and sums stages in
+    FP32 registers, so a K = 8192 sum of positive products stays unbiased to
+    the level of its operand rounding."""
+    from paper_1708_05353_gb300 import occk
+    g = torch.Generator(device="cpu").manual_seed(11)
+    A = (1.0 + 0.1 * torch.rand(128, 8192, generator=g)).float().cuda()
+    B = (1.0 + 0.1 * torch.rand(128, 8192, generator=g)).float().cuda()
+    D = occk.debug_tc_gemm(ctx, prec, A, B).double()
+    ref = A.double() @ B.double().T
+    bias = float(((D - ref) / ref).mean())
+    print(f"{prec}: mean relative error over K = 8192: {bias:.2e}")
+    assert abs(bias) < bound
