@@ -115,7 +115,8 @@ extern "C" void occk_destroy(occk_ctx* c) {
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         for (occk::DevBuf* b : {&c->ct, &c->w, &c->obox, &c->mbox, &c->kb, &c->part, &c->edev,
                                 &c->scratch, &c->mlp_prm, &c->mlp_norm, &c->mlp_m, &c->mlp_v, &c->mlp_h,
-                                &c->mlp_grad, &c->mlp_ws, &c->feat, &c->pred, &c->ranks, &c->nrm, &c->gram}) {
+                                &c->mlp_grad, &c->mlp_ws, &c->feat, &c->pred, &c->ranks, &c->nrm, &c->gram,
+                                &c->pplan, &c->panels}) {
             if (b->p) cudaFree(b->p);
             b->p = nullptr;
         }
@@ -752,6 +753,75 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.box_level = d.box_level;
         a.hlev = d.hlev;
         ctx->ranks_valid = 1;
+    }
+    // panel plan of the tensor-core steps (a) and (e): panel counts per leaf
+    if (occk::tc_mode(prec) >= 0) {
+        const int esz = occk::panel_elem_bytes(prec), pbytes = occk::panel_bytes(prec);
+        if (ctx->pp_tree != t || ctx->pp_nocc != nocc || ctx->pp_nc != nc || ctx->pp_esz != esz ||
+            ctx->pp_pbytes != pbytes) {
+            const int BK = 128 / esz;
+            const int jc = (nocc + BK - 1) / BK, it = (nocc + 127) / 128, KC = nc * jc;
+            std::vector<int> rtA(nleaf), kca(nleaf);
+            std::vector<long long> offA(nleaf), offAa(nleaf), offBa(nleaf);
+            long long cA = 0, cAa = 0, cBa = 0;
+            int max_rt = 0, max_kca = 0;
+            for (int B = 0; B < nleaf; ++B) {
+                const int nr = t->leaf_rowoff[B + 1] - t->leaf_rowoff[B];
+                rtA[B] = (nr + 127) / 128;
+                kca[B] = (nr + BK - 1) / BK;
+                offA[B] = cA;
+                cA += (long long)rtA[B] * KC;
+                offAa[B] = cAa;
+                cAa += (long long)it * kca[B];
+                offBa[B] = cBa;
+                cBa += (long long)nc * it * kca[B];
+                max_rt = std::max(max_rt, rtA[B]);
+                max_kca = std::max(max_kca, kca[B]);
+            }
+            const size_t bytes = 8 * (size_t)nleaf * 5 + 256;
+            if ((e = ensure(ctx->pplan, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "panel plan");
+            std::vector<char> hbuf(bytes);
+            char* hp = hbuf.data();
+            std::memcpy(hp, offA.data(), 8 * nleaf);
+            std::memcpy(hp + 8 * nleaf, offAa.data(), 8 * nleaf);
+            std::memcpy(hp + 16 * nleaf, offBa.data(), 8 * nleaf);
+            std::memcpy(hp + 24 * nleaf, rtA.data(), 4 * nleaf);
+            std::memcpy(hp + 28 * nleaf, kca.data(), 4 * nleaf);
+            if ((e = cudaMemcpy(ctx->pplan.p, hp, bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(ctx, e, "panel plan upload");
+            const size_t l2p = (size_t)(cA + (long long)nleaf * it * KC), a2 = (size_t)(cAa + cBa);
+            if ((e = ensure(ctx->panels, (size_t)pbytes * std::max(l2p, a2) + 1024)) != cudaSuccess)
+                return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "tensor-core panels")
+                                                      : cuda_fail(ctx, e, "panels");
+            ctx->pp_tree = t;
+            ctx->pp_nocc = nocc;
+            ctx->pp_nc = nc;
+            ctx->pp_esz = esz;
+            ctx->pp_pbytes = pbytes;
+            ctx->pp_KC = KC;
+            ctx->pp_jc = jc;
+            ctx->pp_it = it;
+            ctx->pp_max_rt = max_rt;
+            ctx->pp_max_kca = max_kca;
+            ctx->pp_l2pA = (size_t)cA;
+            ctx->pp_a2A = (size_t)cAa;
+        }
+        char* pb = (char*)ctx->pplan.p;
+        a.pp_offA = (const long long*)pb;
+        a.pp_offAa = (const long long*)(pb + 8 * (size_t)nleaf);
+        a.pp_offBa = (const long long*)(pb + 16 * (size_t)nleaf);
+        a.pp_rtA = (const int*)(pb + 24 * (size_t)nleaf);
+        a.pp_kca = (const int*)(pb + 28 * (size_t)nleaf);
+        a.pp_KC = ctx->pp_KC;
+        a.pp_jc = ctx->pp_jc;
+        a.pp_it = ctx->pp_it;
+        a.pp_max_rt = ctx->pp_max_rt;
+        a.pp_max_kca = ctx->pp_max_kca;
+        uint8_t* base = (uint8_t*)ctx->panels.p;
+        a.pan_l2pA = base;
+        a.pan_l2pB = base + (size_t)ctx->pp_pbytes * ctx->pp_l2pA;
+        a.pan_a2A = base;
+        a.pan_a2B = base + (size_t)ctx->pp_pbytes * ctx->pp_a2A;
     }
     a.lscale = d.lscale;
     a.box_scale = d.box_scale;

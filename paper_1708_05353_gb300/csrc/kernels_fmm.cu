@@ -151,9 +151,19 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     const int leaf_store0 = a.leaf0 - a.first_box;
     const bool tcm = sizeof(T) == 4 && tc_mode(a.prec) >= 0;
     mark(1);
+    PanelArgs pa{};
     if (tcm) {
-        cudaError_t e2 = tc_run_a2(a.prec, a.leaf_rowoff, a.leaf_aos, (const float*)Ct, (const float*)W, nocc,
-                                   a.nrow, nc, a.nleaf, leaf_store0, a.lscale, (float*)Ob, a.err_word, s);
+        pa.rtA = a.pp_rtA; pa.offA = a.pp_offA; pa.KC = a.pp_KC; pa.jc = a.pp_jc; pa.it = a.pp_it;
+        pa.kca = a.pp_kca; pa.offAa = a.pp_offAa; pa.offBa = a.pp_offBa;
+        pa.max_rt = a.pp_max_rt; pa.max_kca = a.pp_max_kca; pa.nleaf = a.nleaf;
+        pa.leaf_rowoff = a.leaf_rowoff; pa.leaf_aos = a.leaf_aos;
+        pa.Ct = (const float*)Ct; pa.W = (const float*)W; pa.Mbox = (const float*)Mb; pa.Obox = (float*)Ob;
+        pa.KB = a.kb; pa.lscale = a.lscale;
+        pa.nocc = nocc; pa.nrow = a.nrow; pa.nc = nc; pa.leaf_store0 = leaf_store0;
+        pa.err = a.err_word;
+        pa.panA = a.pan_a2A;
+        pa.panB = a.pan_a2B;
+        cudaError_t e2 = panel_a2(a.prec, pa, s);
         if (e2 != cudaSuccess) return e2;
     } else if constexpr (sizeof(T) == 8) {
         constexpr int BM = 64, BK = 8, TM = 4;
@@ -221,8 +231,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     // (e) L2P
     mark(5);
     if (tcm) {
-        cudaError_t e2 = tc_run_l2p(a.prec, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
-                                    a.nleaf, leaf_store0, a.max_rows, a.lscale, a.kb, a.err_word, s);
+        pa.panA = a.pan_l2pA;
+        pa.panB = a.pan_l2pB;
+        cudaError_t e2 = panel_l2p(a.prec, pa, s);
         if (e2 != cudaSuccess) return e2;
     } else if constexpr (sizeof(T) == 8) {
         // 32 AO rows x 128 orbitals per block: leaves hold ~70-600 AOs, and a

@@ -125,6 +125,12 @@ struct occk_ctx {
     double tau = 1e-6;
     occk::DevBuf mlp_prm, mlp_norm, mlp_m, mlp_v, mlp_h, mlp_grad, mlp_ws, feat, pred, ranks, nrm, gram;
     int ranks_valid = 0;
+    // panel plan cache (tensor-core steps a and e)
+    occk::DevBuf pplan, panels;
+    const occk_tree* pp_tree = nullptr;
+    int pp_nocc = -1, pp_nc = -1, pp_esz = -1, pp_pbytes = -1;
+    int pp_KC = 0, pp_jc = 0, pp_it = 0, pp_max_rt = 0, pp_max_kca = 0;
+    size_t pp_l2pA = 0, pp_l2pB = 0, pp_a2A = 0, pp_a2B = 0;   // panel counts
     // stage timers
     int timing = 0;
     cudaEvent_t ev[OCCK_NSTAGE + 1] = {};
@@ -167,6 +173,10 @@ struct FmmArgs {
     const float* lscale;             // [nc] 1/s_leaf^l
     const float* box_scale;          // [nbox] side of each box's level
     int* err_word;                   // device error word (bounded waits)
+    // panel plan of the tensor-core steps (a) and (e)
+    const int* pp_rtA; const long long* pp_offA; const int* pp_kca; const long long* pp_offAa;
+    const long long* pp_offBa; int pp_KC, pp_jc, pp_it, pp_max_rt, pp_max_kca;
+    uint8_t* pan_l2pA; uint8_t* pan_l2pB; uint8_t* pan_a2A; uint8_t* pan_a2B;
     // learned selector (lmax_policy 2); learned == 0 when unused
     int learned;
     const float* mlp_prm; void* mlp_h; const float* mlp_norm;
@@ -196,6 +206,23 @@ cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L
                           const int* tgt, const int* src, const double* ops, const int* opidx, double* G,
                           double* out, cudaStream_t s);
 cudaError_t select_ranks(const float* pred, int nedge, int Lmax, double tau, int* ranks, cudaStream_t s);
+
+// ----- panel tensor-core GEMMs (kernels_tc2.cu) -----------------------------
+struct PanelArgs {
+    const int* rtA; const long long* offA; int KC, jc, it;       // step (e) plan
+    const int* kca; const long long* offAa; const long long* offBa;  // step (a) plan
+    int max_rt, max_kca, nleaf;
+    const int* leaf_rowoff; const int* leaf_aos;
+    const float* Ct; const float* W; const float* Mbox; float* Obox; double* KB;
+    const float* lscale;
+    int nocc, nrow, nc, leaf_store0;
+    uint8_t* panA; uint8_t* panB;
+    int* err;
+};
+int panel_elem_bytes(int prec);
+int panel_bytes(int prec);
+cudaError_t panel_l2p(int prec, const PanelArgs& a, cudaStream_t s);
+cudaError_t panel_a2(int prec, const PanelArgs& a, cudaStream_t s);
 
 // ----- tensor-core steps (kernels_tc.cu) ------------------------------------
 int tc_mode(int prec);
