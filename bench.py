@@ -40,12 +40,13 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--ncarbon", type=int, default=150)
     p.add_argument("--lmax", type=int, default=2)
-    p.add_argument("--prec", default="fp64")
+    p.add_argument("--prec", default="fp32",
+                   help="main precision; the C150H302 workload is specified for plain FP64/FP32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-cols", type=int, default=2)
     p.add_argument("--workload", default="chain", choices=["chain", "water", "batch"])
     p.add_argument("--batch-fp64", action="store_true", help="run the batch workload in FP64 (default FP32)")
-    p.add_argument("--variants", default="fp32,tf32,bf16,fp16,bf16x3,fp16x3",
+    p.add_argument("--variants", default="fp64,fp32,tf32,bf16,fp16,bf16x3,fp16x3",
                    help="extra precisions timed beside the main one (comma list, or 'none')")
     return p.parse_args()
 
@@ -430,19 +431,26 @@ def main():
             for _ in range(2):
                 occk.farfield_K(ctx, tree, Cf, prec=vp, K=K, Ex=Ex)
             ev = []
-            for k in range(max(3, args.steps // 2)):
+            vst = {k: 0.0 for k in occk.STAGES}
+            ctx.set_timing(True)
+            nv = max(3, args.steps // 2)
+            for k in range(nv):
                 flush.fill_(float(k))
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 occk.farfield_K(ctx, tree, Cf, prec=vp, K=K, Ex=Ex)
                 b.record(stream)
                 ev.append((a, b))
+                for n_, v_ in ctx.timings().items():
+                    vst[n_] += v_ / nv
+            ctx.set_timing(False)
             torch.cuda.synchronize()
             vms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
             var[vp] = {"ms": round(vms, 4), "speedup_vs_fp64": round(ms_max / vms, 3) if args.prec == "fp64" else None,
                        "tflops": round(total_flops / (vms * 1e-3) / 1e12, 3),
                        "abs_dE_Eh": abs(float(Ex.item()) - E64),
-                       "rel_dK": float((K - K64).abs().max().item()) / kmax}
+                       "rel_dK": float((K - K64).abs().max().item()) / kmax,
+                       "stage_ms": {k: round(v, 4) for k, v in vst.items()}}
         result["variants"] = var
         result["variants_reference"] = "errors against the FP64 GPU path of the same run (E = %.10f Eh)" % E64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -84,8 +84,8 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
        const T* __restrict__ Ct, const T* __restrict__ W, int nocc, int nrow, int nc,
        int ntile, T* __restrict__ Obox, int leaf_store0) {
     constexpr int NTH = (BM / TM) * (BM / TM);
-    __shared__ T As[BK][BM];
-    __shared__ T Bs[BK][BM];
+    __shared__ __align__(16) T As[BK][BM];
+    __shared__ __align__(16) T Bs[BK][BM];
     __shared__ int aos[BK];
     const int B = by / nc;
     const int lm = by - B * nc;
@@ -119,10 +119,20 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             T a[TM], b[TM];
+            if constexpr (sizeof(T) == 4 && TM % 4 == 0) {   // float4 shared loads
 #pragma unroll
-            for (int q = 0; q < TM; ++q) {
-                a[q] = As[kk][ty * TM + q];
-                b[q] = Bs[kk][tx * TM + q];
+                for (int q = 0; q < TM; q += 4) {
+                    const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * TM + q]);
+                    const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * TM + q]);
+                    a[q] = av.x; a[q + 1] = av.y; a[q + 2] = av.z; a[q + 3] = av.w;
+                    b[q] = bv.x; b[q + 1] = bv.y; b[q + 2] = bv.z; b[q + 3] = bv.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < TM; ++q) {
+                    a[q] = As[kk][ty * TM + q];
+                    b[q] = Bs[kk][tx * TM + q];
+                }
             }
 #pragma unroll
             for (int x = 0; x < TM; ++x)
@@ -153,21 +163,33 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
 // mode 2: L2L, source = parent of tgt, operator l2l_op[tgt], upper in l
 // grid (pair blocks, targets, lm chunks).
 // ---------------------------------------------------------------------------
+// Pairs per thread of the translations: FP32 reuses each operator entry read
+// from shared memory for 4 pairs (one broadcast load per 4 FMAs); FP64 is
+// bound by the DFMA rate and keeps one.
+template <typename T>
+__host__ __device__ constexpr int translate_ppt() { return sizeof(T) == 4 ? 4 : 1; }
+
 template <typename T, int LMC>
 __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode, int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr,
             const int* __restrict__ list, const int* __restrict__ opidx, const int* __restrict__ lmax_e,
             const int* __restrict__ parent, const T* __restrict__ ops, const T* __restrict__ in,
             T* __restrict__ out, int accumulate) {
-    __shared__ T sop[LMC][kNcMax];
+    constexpr int PPT = translate_ppt<T>();
+    __shared__ T sop[kNcMax][LMC];      // [input component][output component of the chunk]
     const int tgt = tgt0 + by;
     const int c0 = bz * LMC;
     const int ncl = min(LMC, nc - c0);
-    const int p = bx * blockDim.x + threadIdx.x;
-    const bool live = p < P;
-    T acc[LMC];
-    T* o = out + ((size_t)(tgt - first_box) * nc + c0) * P + p;
+    const int pb = bx * blockDim.x * PPT + threadIdx.x;      // pairs pb + k * blockDim.x
+    bool live[PPT];
 #pragma unroll
-    for (int q = 0; q < LMC; ++q) acc[q] = (accumulate && live && q < ncl) ? o[(size_t)q * P] : T(0);
+    for (int k = 0; k < PPT; ++k) live[k] = pb + k * (int)blockDim.x < P;
+    T acc[PPT][LMC];
+    T* o = out + ((size_t)(tgt - first_box) * nc + c0) * P + pb;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+#pragma unroll
+        for (int q = 0; q < LMC; ++q)
+            acc[k][q] = (accumulate && live[k] && q < ncl) ? o[(size_t)q * P + k * blockDim.x] : T(0);
     int e0, e1;
     if (mode == 2) {
         e0 = 0;
@@ -203,22 +225,28 @@ __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode,
         __syncthreads();
         for (int x = threadIdx.x; x < LMC * (cb1 - cb0); x += blockDim.x) {
             int q = x / (cb1 - cb0), c = cb0 + (x - q * (cb1 - cb0));
-            sop[q][c] = (q < ncl && c0 + q < ncr) ? Tm[(size_t)(c0 + q) * nc + c] : T(0);
+            sop[c][q] = (q < ncl && c0 + q < ncr) ? Tm[(size_t)(c0 + q) * nc + c] : T(0);
         }
         __syncthreads();
-        if (live) {
-            const T* x = in + (size_t)(src - first_box) * nc * P + p;
-            for (int c = cb0; c < cb1; ++c) {
-                const T v = x[(size_t)c * P];
+        const T* x = in + (size_t)(src - first_box) * nc * P + pb;
+        for (int c = cb0; c < cb1; ++c) {
+            T v[PPT];
 #pragma unroll
-                for (int q = 0; q < LMC; ++q) acc[q] += sop[q][c] * v;
+            for (int k = 0; k < PPT; ++k) v[k] = live[k] ? x[(size_t)c * P + k * blockDim.x] : T(0);
+#pragma unroll
+            for (int q = 0; q < LMC; ++q) {
+                const T w = sop[c][q];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) acc[k][q] += w * v[k];
             }
         }
     }
-    if (live) {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!live[k]) continue;
 #pragma unroll
         for (int q = 0; q < LMC; ++q)
-            if (q < ncl) o[(size_t)q * P] = acc[q];
+            if (q < ncl) o[(size_t)q * P + k * blockDim.x] = acc[k][q];
     }
 }
 
@@ -368,6 +396,86 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
 // K[r + i*ldk] = sum over the leaf rows of AO r of KB[row][i], in FP64, and the
 // per-block partial of E = -1/2 sum_ri C_ri K_ri.
 // ---------------------------------------------------------------------------
+// FP32 step (e): 96 AO rows x 128 orbitals per block (256 threads, thread
+// tile 6 rows x 8 contiguous orbitals, K step 16).  A leaf of up to 96 AOs is
+// one row tile, so each element of the packed Mcal is read once per leaf;
+// shared-memory operands are read as float2/float4 (5 loads per 48 FMAs).
+__device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, const int* __restrict__ leaf_rowoff,
+                                                const float* __restrict__ W, const float* __restrict__ Mbox,
+                                                int nocc, int nrow, int nc, int leaf_store0,
+                                                double* __restrict__ KB) {
+    constexpr int BR = 96, BI = 128, BK = 16, TR = 6, TI = 8;
+    __shared__ __align__(16) float As[BK][BR + 4];
+    __shared__ __align__(16) float Bs[BK][BI + 4];
+    const int B = bz;
+    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+    const int r0 = bx * BR, i0 = by * BI;
+    if (r0 >= nr) return;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const size_t P = npairs(nocc);
+    float acc[TR][TI];
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TI; ++b) acc[a][b] = 0.f;
+    // rows of this warp: r0 + 12 w .. r0 + 12 w + 11
+    const bool warp_live = r0 + (threadIdx.x >> 5) * 2 * TR < nr;
+    for (int lm = 0; lm < nc; ++lm) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= lm) ++l;
+        const float w = (lm == l * l) ? 2.f : (((lm - l * l) & 1) ? 4.f : -4.f);
+        const float* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
+        const float* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
+        for (int k0 = 0; k0 < nocc; k0 += BK) {
+#pragma unroll
+            for (int m = 0; m < (BR * BK) / 256; ++m) {
+                const int e = threadIdx.x + 256 * m;
+                const int row = e / BK, kk = e % BK;
+                const int r = r0 + row, j = k0 + kk;
+                As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.f;
+            }
+            const bool below = k0 + BK <= i0;
+#pragma unroll
+            for (int m = 0; m < (BI * BK) / 256; ++m) {
+                const int e = threadIdx.x + 256 * m;
+                const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
+                const int i = i0 + row, j = k0 + kk;
+                Bs[kk][row] = (i < nocc && j < nocc)
+                                  ? w * Ml[i <= j ? tri_index(i, j, nocc) : tri_index(j, i, nocc)]
+                                  : 0.f;
+            }
+            __syncthreads();
+            if (warp_live) {
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    const float2 a0 = *reinterpret_cast<const float2*>(&As[kk][ty * TR]);
+                    const float2 a1 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 2]);
+                    const float2 a2 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 4]);
+                    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * TI]);
+                    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * TI + 4]);
+                    const float av[6] = {a0.x, a0.y, a1.x, a1.y, a2.x, a2.y};
+                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int x = 0; x < TR; ++x)
+#pragma unroll
+                        for (int y = 0; y < TI; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < TR; ++x) {
+        const int r = r0 + ty * TR + x;
+        if (r >= nr) continue;
+#pragma unroll
+        for (int y = 0; y < TI; ++y) {
+            const int i = i0 + tx * TI + y;
+            if (i < nocc) KB[(size_t)(rb0 + r) * nocc + i] = (double)acc[x][y];
+        }
+    }
+}
+
 static __device__ __forceinline__ void reduce_body(int bx, int by, int bz, const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
                            const double* __restrict__ KB, int nao, int nocc,
                            const double* __restrict__ C, int ldc, double* __restrict__ K, int ldk,

@@ -957,9 +957,13 @@ extern "C" occk_status occk_debug_tc_gemm(occk_ctx* ctx, int prec, int M, int N,
     cudaSetDevice(ctx->device);
     cudaError_t e = ensure(ctx->scratch, 256);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch");
+    e = ensure(ctx->panels, occk::tc_gemm_panel_bytes(prec, M, N, K) + 1024);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "panels");
+    ctx->pp_tree = nullptr;   // the panel buffer no longer holds a far-field plan's panels
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(ctx->scratch.p, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = occk::tc_gemm(prec, M, N, K, A, B, D, (int*)ctx->scratch.p, s);
+    if (e == cudaSuccess)
+        e = occk::tc_gemm(prec, M, N, K, A, B, D, (uint8_t*)ctx->panels.p, (int*)ctx->scratch.p, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_debug_tc_gemm");
     return occk_device_status(ctx, stream);
 }

@@ -217,6 +217,7 @@ void free_items(occk_batch* b) {
 // Translation items for chunk width lmc.
 cudaError_t build_translate_items(occk_batch* b, int lmc) {
     free_items(b);
+    const int ppt = b->prec == OCCK_FP64 ? occk::body::translate_ppt<double>() : occk::body::translate_ppt<float>();
     cudaError_t e = cudaSuccess;
     const int steps = std::max(b->maxD - 2, 0);
     for (int k = 0; k < steps && e == cudaSuccess; ++k) {
@@ -226,18 +227,19 @@ cudaError_t build_translate_items(occk_batch* b, int lmc) {
             const SysDesc& sd = b->h_sys[s];
             if (sd.depth < 3) continue;
             const int nch = (sd.nc + lmc - 1) / lmc;
-            const int pb = (int)((sd.P + 127) / 128);
+            const int pb = (int)((sd.P + 128 * ppt - 1) / (128 * ppt));
+            // pair block outermost: consecutive items share source pairs (L2 reuse)
             const int child = sd.depth - k;          // M2M: children at this level
             if (child >= 3) {
-                for (int tg = t->level_off[child - 1]; tg < t->level_off[child]; ++tg)
-                    for (int c = 0; c < nch; ++c)
-                        for (int p = 0; p < pb; ++p) m2m.push_back(TItem{s, 0, tg, p, c, 0});
+                for (int p = 0; p < pb; ++p)
+                    for (int tg = t->level_off[child - 1]; tg < t->level_off[child]; ++tg)
+                        for (int c = 0; c < nch; ++c) m2m.push_back(TItem{s, 0, tg, p, c, 0});
             }
             const int lev = 3 + k;                   // L2L: children at this level
             if (lev <= sd.depth) {
-                for (int tg = t->level_off[lev]; tg < t->level_off[lev + 1]; ++tg)
-                    for (int c = 0; c < nch; ++c)
-                        for (int p = 0; p < pb; ++p) l2l.push_back(TItem{s, 2, tg, p, c, 1});
+                for (int p = 0; p < pb; ++p)
+                    for (int tg = t->level_off[lev]; tg < t->level_off[lev + 1]; ++tg)
+                        for (int c = 0; c < nch; ++c) l2l.push_back(TItem{s, 2, tg, p, c, 1});
             }
         }
         TItem *dm = nullptr, *dl = nullptr;
@@ -254,10 +256,10 @@ cudaError_t build_translate_items(occk_batch* b, int lmc) {
         const SysDesc& sd = b->h_sys[s];
         if (sd.depth < 2) continue;
         const int nch = (sd.nc + lmc - 1) / lmc;
-        const int pb = (int)((sd.P + 127) / 128);
-        for (int tg = t->level_off[2]; tg < sd.nbox; ++tg)
-            for (int c = 0; c < nch; ++c)
-                for (int p = 0; p < pb; ++p) m2l.push_back(TItem{s, 1, tg, p, c, 0});
+        const int pb = (int)((sd.P + 128 * ppt - 1) / (128 * ppt));
+        for (int p = 0; p < pb; ++p)
+            for (int tg = t->level_off[2]; tg < sd.nbox; ++tg)
+                for (int c = 0; c < nch; ++c) m2l.push_back(TItem{s, 1, tg, p, c, 0});
     }
     if (e == cudaSuccess) e = occk::up(&b->it_m2l, m2l);
     b->n_m2l = (int)m2l.size();

@@ -49,7 +49,10 @@ k_translate(int mode, int P, int nc, int L, int first_box, int tgt0, const int* 
             const int* __restrict__ list, const int* __restrict__ opidx, const int* __restrict__ lmax_e,
             const int* __restrict__ parent, const T* __restrict__ ops, const T* __restrict__ in,
             T* __restrict__ out, int accumulate) {
-    body::translate_body<T, LMC>(blockIdx.x, blockIdx.y, blockIdx.z, mode, P, nc, L, first_box, tgt0, ptr, list,
+    // blockIdx.x = target, blockIdx.y = pair block: consecutive blocks work on
+    // the same pairs of different targets, so the source slices they share
+    // stay in L2 (a pair block of every box of a level is well under 1 MB)
+    body::translate_body<T, LMC>(blockIdx.y, blockIdx.x, blockIdx.z, mode, P, nc, L, first_box, tgt0, ptr, list,
                                  opidx, lmax_e, parent, ops, in, out, accumulate);
 }
 
@@ -65,6 +68,12 @@ __global__ void __launch_bounds__(256)
 k_l2p_r32(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const double* __restrict__ Mbox,
           int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
     body::l2p_rect_body(blockIdx.x, blockIdx.y, blockIdx.z, leaf_rowoff, W, Mbox, nocc, nrow, nc, leaf_store0, KB);
+}
+
+__global__ void __launch_bounds__(256)
+k_l2p_r96f(const int* __restrict__ leaf_rowoff, const float* __restrict__ W, const float* __restrict__ Mbox,
+           int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+    body::l2p_rect_body_f(blockIdx.x, blockIdx.y, blockIdx.z, leaf_rowoff, W, Mbox, nocc, nrow, nc, leaf_store0, KB);
 }
 
 __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
@@ -182,12 +191,12 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     const int LMC = translate_chunk(nc);
     const int nchunk = (nc + LMC - 1) / LMC;
-    const unsigned pblocks = (unsigned)((P + 127) / 128);
+    const unsigned pblocks = (unsigned)((P + 128 * body::translate_ppt<T>() - 1) / (128 * body::translate_ppt<T>()));
     // (b) M2M: parents at level lev-1 gather their children at level lev
     mark(2);
     for (int lev = D; lev >= 3; --lev) {
         int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
-        dim3 g(pblocks, nt, nchunk);
+        dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 0, (int)P, nc, a.L, a.first_box, t0, a.child_ptr,
                                              a.child_list, a.m2m_op, nullptr, a.parent, ops, Ob, Ob, 0);
     }
@@ -205,18 +214,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (c) M2L: every box of levels 2..D, all levels in one launch
     mark(3);
-    // tensor cores for M2L only where it is compute-bound (nc >= 49): below
-    // that the translation moves more bytes than it has FLOPs to hide them and
-    // runs in FP32 on the SIMT cores
-    if (tcm && nc >= 49 && nc <= 128) {
+    {
         int t0 = a.level_off[2], nt = a.nbox - t0;
-        cudaError_t e2 = tc_run_m2l(a.prec, (int)P, nc, a.L, a.first_box, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op,
-                                    lmax_e, (const float*)ops, (const float*)Ob, (float*)Mb, a.box_scale,
-                                    a.err_word, s);
-        if (e2 != cudaSuccess) return e2;
-    } else {
-        int t0 = a.level_off[2], nt = a.nbox - t0;
-        dim3 g(pblocks, nt, nchunk);
+        dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 1, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
                                              a.m2l_op, lmax_e, a.parent, ops, Ob, Mb, 0);
     }
@@ -224,7 +224,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     mark(4);
     for (int lev = 3; lev <= D; ++lev) {
         int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
-        dim3 g(pblocks, nt, nchunk);
+        dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 2, (int)P, nc, a.L, a.first_box, t0, nullptr, nullptr,
                                              a.l2l_op, nullptr, a.parent, ops, Mb, Mb, 1);
     }
@@ -242,10 +242,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         k_l2p_r32<<<g, 256, 0, s>>>(a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow, nc,
                                     leaf_store0, a.kb);
     } else {
-        constexpr int BM = 128, BK = 8, TM = 8;
-        dim3 g((a.max_rows + BM - 1) / BM, (nocc + BM - 1) / BM, a.nleaf);
-        k_l2p<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, W, Mb, nocc, a.nrow, nc,
-                                                                 leaf_store0, a.kb);
+        dim3 g((a.max_rows + 95) / 96, (nocc + 127) / 128, a.nleaf);
+        k_l2p_r96f<<<g, 256, 0, s>>>(a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
+                                     leaf_store0, a.kb);
     }
     mark(6);
     constexpr int kRedBlocks = 1024;

@@ -26,6 +26,8 @@
 namespace occk {
 
 int tc_mode(int prec);
+int panel_elem_bytes(int prec);
+int panel_bytes(int prec);
 
 namespace {
 
@@ -412,6 +414,46 @@ k_pgemm_a2(int nocc, int nc, int ntile, int leaf_store0, Plan pl, const uint8_t*
     }
 }
 
+// Plain GEMM D[M][N] = A[M][K] B[N][K]^T on FP32 row-major inputs, for
+// checking the engine: generic panel builder and a plain epilogue.
+template <int P>
+__global__ void k_panel_rows(const float* __restrict__ X, int rows, int K, int KC, uint8_t* __restrict__ panels) {
+    const int kc = blockIdx.x, rt = blockIdx.y;
+    constexpr int BK = Q<P>::BK;
+    const int r = rt * 128 + threadIdx.x;
+    uint8_t* panel = panels + (size_t)((long long)rt * KC + kc) * Q<P>::pbytes;
+    for (int k8 = 0; k8 < BK; k8 += 8) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = kc * BK + k8 + q;
+            v[q] = (r < rows && k < K) ? X[(size_t)r * K + k] : 0.f;
+        }
+        panel_put8<P>(panel, threadIdx.x, k8, v);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(192, 1)
+k_pgemm_plain(int M, int N, int KC, const uint8_t* __restrict__ Apan, const uint8_t* __restrict__ Bpan,
+              float* __restrict__ D, int* err) {
+    const int mt = blockIdx.x, nt = blockIdx.y;
+    float acc[128];
+#pragma unroll
+    for (int q = 0; q < 128; ++q) acc[q] = 0.f;
+    const bool ok = pgemm_tile<P>(Apan + (size_t)mt * KC * Q<P>::pbytes, Bpan + (size_t)nt * KC * Q<P>::pbytes, KC,
+                                  acc, err);
+    const int warp = threadIdx.x >> 5;
+    if (!ok || warp < 2) return;
+    const int m = mt * 128 + (warp & 3) * 32 + (threadIdx.x & 31);
+    if (m >= M) return;
+#pragma unroll
+    for (int q = 0; q < 128; ++q) {
+        const int n = nt * 128 + q;
+        if (n < N) D[(size_t)m * N + n] = acc[q];
+    }
+}
+
 template <int P>
 cudaError_t attrs() {
     static bool done = false;
@@ -419,6 +461,8 @@ cudaError_t attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_pgemm_l2p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q<P>::smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pgemm_a2<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q<P>::smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pgemm_plain<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q<P>::smem);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -450,7 +494,51 @@ cudaError_t a2_typed(const PanelArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t plain_typed(int M, int N, int K, const float* A, const float* B, float* D, uint8_t* panels, int* err,
+                        cudaStream_t s) {
+    cudaError_t e = attrs<P>();
+    if (e != cudaSuccess) return e;
+    const int KC = (K + Q<P>::BK - 1) / Q<P>::BK, mt = (M + 127) / 128, nt = (N + 127) / 128;
+    uint8_t* pa = panels;
+    uint8_t* pb = panels + (size_t)mt * KC * Q<P>::pbytes;
+    k_panel_rows<P><<<dim3(KC, mt), 128, 0, s>>>(A, M, K, KC, pa);
+    k_panel_rows<P><<<dim3(KC, nt), 128, 0, s>>>(B, N, K, KC, pb);
+    k_pgemm_plain<P><<<dim3(mt, nt), 192, Q<P>::smem, s>>>(M, N, KC, pa, pb, D, err);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int tc_mode(int prec) {
+    switch (prec) {
+        case OCCK_BF16: return Q_BF16;
+        case OCCK_FP16: return Q_FP16;
+        case OCCK_TF32: return Q_TF32;
+        case OCCK_BF16X3: return Q_BF16X3;
+        case OCCK_FP16X3: return Q_FP16X3;
+        default: return -1;
+    }
+}
+
+size_t tc_gemm_panel_bytes(int prec, int M, int N, int K) {
+    const int esz = panel_elem_bytes(prec), pb = panel_bytes(prec);
+    if (!esz) return 0;
+    const size_t KC = (size_t)(K + 128 / esz - 1) / (128 / esz);
+    return KC * ((size_t)(M + 127) / 128 + (size_t)(N + 127) / 128) * (size_t)pb;
+}
+
+cudaError_t tc_gemm(int prec, int M, int N, int K, const float* A, const float* B, float* D, uint8_t* panels,
+                    int* err, cudaStream_t s) {
+    switch (tc_mode(prec)) {
+        case Q_BF16: return plain_typed<Q_BF16>(M, N, K, A, B, D, panels, err, s);
+        case Q_FP16: return plain_typed<Q_FP16>(M, N, K, A, B, D, panels, err, s);
+        case Q_TF32: return plain_typed<Q_TF32>(M, N, K, A, B, D, panels, err, s);
+        case Q_BF16X3: return plain_typed<Q_BF16X3>(M, N, K, A, B, D, panels, err, s);
+        case Q_FP16X3: return plain_typed<Q_FP16X3>(M, N, K, A, B, D, panels, err, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 int panel_elem_bytes(int prec) {
     switch (tc_mode(prec)) {

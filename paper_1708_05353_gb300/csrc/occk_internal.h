@@ -224,18 +224,10 @@ int panel_bytes(int prec);
 cudaError_t panel_l2p(int prec, const PanelArgs& a, cudaStream_t s);
 cudaError_t panel_a2(int prec, const PanelArgs& a, cudaStream_t s);
 
-// ----- tensor-core steps (kernels_tc.cu) ------------------------------------
+// ----- plain tensor-core GEMM for checking the engine (kernels_tc2.cu) --------
 int tc_mode(int prec);
-cudaError_t tc_gemm(int prec, int M, int N, int K, const float* A, const float* B, float* D, int* err,
-                    cudaStream_t s);
-cudaError_t tc_run_a2(int prec, const int* leaf_rowoff, const int* leaf_aos, const float* Ct, const float* W,
-                      int nocc, int nrow, int nc, int nleaf, int leaf_store0, const float* lscale, float* Obox,
-                      int* err, cudaStream_t s);
-cudaError_t tc_run_l2p(int prec, const int* leaf_rowoff, const float* W, const float* Mbox, int nocc, int nrow,
-                       int nc, int nleaf, int leaf_store0, int max_rows, const float* lscale, double* KB,
-                       int* err, cudaStream_t s);
-cudaError_t tc_run_m2l(int prec, int P, int nc, int L, int first_box, int tgt0, int ntgt, const int* ptr,
-                       const int* src, const int* op, const int* lmax_e, const float* ops, const float* O,
-                       float* M, const float* box_scale, int* err, cudaStream_t s);
+size_t tc_gemm_panel_bytes(int prec, int M, int N, int K);
+cudaError_t tc_gemm(int prec, int M, int N, int K, const float* A, const float* B, float* D, uint8_t* panels,
+                    int* err, cudaStream_t s);
 
 }  // namespace occk
