@@ -118,10 +118,21 @@ def m2l_cost(ranks):
     return float(np.sum((np.asarray(ranks, dtype=np.float64) + 1.0) ** 4))
 
 
+def _timed(fn):
+    torch = _torch()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
 def compare(ctx, system, tau, Lref=LREF, prec="fp64", depth=None, fixed=(2, 3, 4, 5, 6, 7, 8, 9, 10)):
     """Learned ranks vs fixed ranks on one system.  Errors are measured against
     the rank-Lref energy; the M2L cost is sum over edges of (L_e+1)^4."""
-    tree, K, Eref = run_far_field(ctx, system, Lref, prec=prec, depth=depth)
+    (tree, K, Eref), t_ref = _timed(lambda: run_far_field(ctx, system, Lref, prec=prec, depth=depth))
+    # a second run of the same tree for the far-field time without set-up
+    _, t_ref = _timed(lambda: run_far_field(ctx, system, Lref, prec=prec, tree=tree))
     nedge = tree.info()["nm2l"]
     Ee = occk.edge_energies(ctx, tree).cpu().numpy()
     rows = {}
@@ -129,7 +140,7 @@ def compare(ctx, system, tau, Lref=LREF, prec="fp64", depth=None, fixed=(2, 3, 4
         E_L = float(np.sum(Ee[:, L])) if nedge else 0.0
         rows[L] = dict(err=abs(E_L - Eref), cost=m2l_cost([L] * nedge))
     occk.set_learned_tau(ctx, tau)
-    _, K2, E_learn = run_far_field(ctx, system, Lref, prec=prec, policy=2, tree=tree)
+    (_, K2, E_learn), t_learn = _timed(lambda: run_far_field(ctx, system, Lref, prec=prec, policy=2, tree=tree))
     ranks = occk.edge_ranks(ctx, tree)
     learned = dict(err=abs(E_learn - Eref), cost=m2l_cost(ranks), ranks_hist=np.bincount(ranks, minlength=Lref + 1).tolist())
     # cheapest fixed rank at least as accurate as the learned choice
@@ -142,7 +153,9 @@ def compare(ctx, system, tau, Lref=LREF, prec="fp64", depth=None, fixed=(2, 3, 4
         r_opt = lagrangian_choice(true_log, Lref, tau)
         E_opt = float(np.sum(Ee[np.arange(nedge), r_opt]))
         optimal = dict(err=abs(E_opt - Eref), cost=m2l_cost(r_opt))
+    learned["time_s"] = t_learn
     return dict(E_ref=Eref, tau=tau, fixed=rows, learned=learned, optimal=optimal, matched_fixed_rank=matched,
+                time_fixed_lref_s=t_ref, speedup_time_vs_lref=t_ref / max(t_learn, 1e-9),
                 gain_vs_matched=rows[matched]["cost"] / max(learned["cost"], 1.0),
                 gain_vs_lref=rows[Lref]["cost"] / max(learned["cost"], 1.0), nedge=nedge)
 
@@ -195,7 +208,11 @@ def main():
     else:
         load(ctx, args.out)
         s = inputs.protein_like(lmax=LREF)
-        print(json.dumps(compare(ctx, s, args.tau), default=float), flush=True)
+        res = compare(ctx, s, args.tau)
+        res["system"] = s.name
+        res["nao"] = s.basis.nao
+        res["nocc"] = s.nocc
+        print(json.dumps(res, default=float), flush=True)
 
 
 if __name__ == "__main__":
