@@ -313,6 +313,15 @@ occk_status occk_batch_tune(occk_batch* batch, const char* cache_path, int* cfg_
  * a tensor-core kernel gave up (its results are then invalid), else OK. */
 occk_status occk_device_status(occk_ctx* ctx, void* stream);
 
+/* Engine of the translations (b) M2M, (c) M2L and (d) L2L in the mixed forms
+ * (OCCK_TF32 .. OCCK_FP16X3).  mask = -1 (default): chosen by expansion rank;
+ * otherwise bit 0 / 1 / 2 puts M2M / M2L / L2L on the tensor core (tcgen05,
+ * scaled operands, see Eqs. fmm1-3), the others on SIMT FP32; mask = 0 keeps
+ * all three on SIMT with unscaled storage.  Ignored when per-edge ranks are in
+ * use (lmax_policy 1 or 2): M2L then stays on SIMT.  OCCK_ERR_ARG for a mask
+ * outside -1..7.  No paper counterpart: an implementation choice. */
+occk_status occk_set_translate_engine(occk_ctx* ctx, int mask);
+
 /* D = A B^T on the tensor-core engine used by the mixed forms, for checking
  * it: A [M x K], B [N x K], D [M x N], all FP32 row-major device buffers; prec
  * one of OCCK_TF32, _BF16, _FP16, _BF16X3, _FP16X3.  Synchronises `stream`. */

@@ -4,6 +4,7 @@
 // the integer tree (pair screening, pair centres, box indices) is a plain IEEE
 // double expression evaluated in a fixed order, so the tree is reproducible.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -621,11 +622,17 @@ extern "C" occk_status occk_pair_multipoles(occk_ctx* ctx, occk_tree* t, int lma
                                               : cuda_fail(ctx, e, "occk_pair_multipoles alloc");
     }
     {
-        // per-level scale factors for the low-precision forms
+        // per-component scale factors of the low-precision forms at the leaf
+        // level, sqrt((l+m)!(l-m)!) / h^l: they bring every component of the
+        // leaf multipoles to O(1), so no FP16 operand of steps (a) and (e)
+        // overflows or flushes to zero at high l
         std::vector<float> ls(nc), bsc(t->parent.size());
         const double sl = t->h[t->depth];
         for (int l = 0; l <= lmax; ++l)
-            for (int c = l * l; c < (l + 1) * (l + 1); ++c) ls[c] = (float)std::pow(sl, -l);
+            for (int c = l * l; c < (l + 1) * (l + 1); ++c) {
+                const int m = c == l * l ? 0 : (c - l * l + 1) / 2;
+                ls[c] = (float)(std::sqrt(std::tgamma(l + m + 1.0) * std::tgamma(l - m + 1.0)) / std::pow(sl, l));
+            }
         for (size_t b = 0; b < bsc.size(); ++b) {
             int lev = 0;
             while (lev + 1 < (int)t->level_off.size() && t->level_off[lev + 1] <= (int)b) ++lev;
@@ -642,6 +649,8 @@ extern "C" occk_status occk_pair_multipoles(occk_ctx* ctx, occk_tree* t, int lma
     if (e == cudaSuccess && nops > 0) e = occk::launch_gen_ops(d.opdesc, nops, lmax, d.ops, d.ops_f, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_pair_multipoles launch");
     t->lmax = lmax;
+    static std::atomic<long long> gen_counter{0};
+    t->gen = ++gen_counter;
     return OCCK_OK;
 }
 
@@ -823,6 +832,94 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.pan_a2A = base;
         a.pan_a2B = base + (size_t)ctx->pp_pbytes * ctx->pp_a2A;
     }
+    // operator panels of the tensor-core translations (b)-(d), once per
+    // operator set and precision
+    a.tr_pan = nullptr;
+    a.tr_on = 0;
+    a.tr_nlev = D + 1;
+    a.inv_h_leaf = (float)(1.0 / t->h[D]);
+    a.sm_count = ctx->sm_count;
+    a.box_level = d.box_level;
+    if (occk::tc_mode(prec) >= 0 && occk::tr_np(nc) > 0 && D >= 2 && !t->ops.empty()) {
+        if (ctx->tp_gen != t->gen || ctx->tp_prec != prec) {
+            ctx->tp_ok = 0;
+            const int nops = (int)t->ops.size(), nlev = D + 1;
+            std::vector<int> lev(nbox), opinfo(4 * (size_t)nops, 0), seen(nops, 0);
+            for (int l = 0; l <= D; ++l)
+                for (int b = t->level_off[l]; b < t->level_off[l + 1]; ++b) lev[b] = l;
+            bool consistent = true;
+            auto setop = [&](int o, int kin, int lin, int kout, int lout) {
+                if (o < 0 || o >= nops) return;
+                int* r = &opinfo[4 * (size_t)o];
+                if (!seen[o]) {
+                    seen[o] = 1;
+                    r[0] = kin; r[1] = lin; r[2] = kout; r[3] = lout;
+                } else if (r[0] != kin || r[1] != lin || r[2] != kout || r[3] != lout) {
+                    consistent = false;
+                }
+            };
+            for (int b = 0; b < nbox; ++b) {
+                if (lev[b] < 1) continue;
+                setop(t->m2m_op[b], 0, lev[b], 0, lev[b] - 1);
+                setop(t->l2l_op[b], 1, lev[b] - 1, 1, lev[b]);
+            }
+            for (size_t q = 0; q < t->m2l_tgt.size(); ++q) {
+                const int l = lev[t->m2l_tgt[q]];
+                setop(t->m2l_op[q], 0, l, 1, l);
+            }
+            // component scales: multipoles sqrt((l+m)!(l-m)!) / h^l, local
+            // expansions h^(l+1) / sqrt((l+m)!(l-m)!)
+            std::vector<double> scd(2 * (size_t)nlev * nc);
+            for (int l = 0; l <= L; ++l) {
+                for (int c = l * l; c < (l + 1) * (l + 1); ++c) {
+                    const int m = c == l * l ? 0 : (c - l * l + 1) / 2;
+                    const double g = std::sqrt(std::tgamma(l + m + 1.0) * std::tgamma(l - m + 1.0));
+                    for (int k = 0; k < nlev; ++k) {
+                        const double h = t->h[k];
+                        scd[(size_t)k * nc + c] = g / std::pow(h, l);
+                        scd[((size_t)nlev + k) * nc + c] = std::pow(h, l + 1) / g;
+                    }
+                }
+            }
+            const size_t nsc = scd.size();
+            const size_t bytes_tab = 8 * nsc + 4 * opinfo.size() + 64;
+            if ((e = ensure(ctx->tscale, bytes_tab)) != cudaSuccess ||
+                (e = ensure(ctx->tpan, (size_t)nops * occk::tr_panel_bytes(prec, nc))) != cudaSuccess ||
+                (e = ensure(ctx->tops, sizeof(float) * (size_t)nops * nc * nc)) != cudaSuccess)
+                return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "translation panels")
+                                                      : cuda_fail(ctx, e, "translation panels");
+            char* tb = (char*)ctx->tscale.p;
+            if ((e = cudaMemcpy(tb, scd.data(), 8 * nsc, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(tb + 8 * nsc, opinfo.data(), 4 * opinfo.size(), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                return cuda_fail(ctx, e, "translation scales upload");
+            ctx->tp_scd = scd;
+            e = occk::tr_build_panels(prec, d.ops, nops, nc, (const int*)(tb + 8 * nsc), (const double*)tb, nlev,
+                                      (uint8_t*)ctx->tpan.p, (float*)ctx->tops.p, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "translation panels launch");
+            ctx->tp_ok = consistent ? 1 : 0;
+            ctx->tp_gen = t->gen;
+            ctx->tp_prec = prec;
+        }
+        if (ctx->tp_ok) a.tr_pan = (const uint8_t*)ctx->tpan.p;
+    }
+    // the tensor-core translations keep a target's edge table in shared
+    // memory (at most 256 edges; an interaction list has at most 189); they
+    // run when every M2L edge has the full rank (per-edge ranks keep all
+    // three translations on SIMT, with unscaled storage)
+    int max_m2l_edges = 0;
+    for (int b = 0; b + 1 < (int)t->m2l_ptr.size(); ++b)
+        max_m2l_edges = std::max(max_m2l_edges, t->m2l_ptr[b + 1] - t->m2l_ptr[b]);
+    a.tr_on = (a.tr_pan && a.m2l_lmax == nullptr && !a.learned && max_m2l_edges <= 256) ? 1 : 0;
+    // which translations go to the tensor core: measured on GB300 (C150H302
+    // and (H2O)100, FP16X3), the tensor-core form wins for M2M and M2L from
+    // rank 5 on (M2L 2x at rank 6, 3.8x at rank 8); L2L has one source per
+    // target, too little work per item, and stays on SIMT with the scaled
+    // operators; below rank 5 all three SIMT forms are faster and the storage
+    // stays unscaled
+    a.tr_mask = ctx->tr_engine >= 0 ? ctx->tr_engine : (L >= 5 ? 3 : 0);
+    if (!a.tr_mask) a.tr_on = 0;
+    a.ops_scaled = (const float*)ctx->tops.p;
     a.lscale = d.lscale;
     a.box_scale = d.box_scale;
     a.err_word = (int*)ctx->scratch.p;
@@ -838,6 +935,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     ctx->ev_recorded = ctx->timing ? 1 : 0;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_farfield_K launch");
     ctx->last_prec = prec;
+    ctx->last_scaled = a.tr_on;
     ctx->last_nocc = nocc;
     ctx->last_lmax = L;
     ctx->last_first_box = first;
@@ -889,11 +987,20 @@ extern "C" occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* t, int w
         for (size_t i = 0; i < nst; ++i) tmp[i] = tf[i];
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy");
-    // stored upper triangle -> full i,j square
+    // stored upper triangle -> full i,j square (scaled storage: back to O, Mcal)
     double* dst = (double*)out;
+    const int nlev = t->depth + 1;
+    const bool unscale = ctx->last_scaled && ctx->tp_scd.size() == 2 * (size_t)nlev * nc;
     for (int b = ctx->last_first_box; b < nbox; ++b)
         for (int c = 0; c < nc; ++c) {
-            const double* sp = tmp.data() + ((size_t)(b - ctx->last_first_box) * nc + c) * Ps;
+            double* sp = tmp.data() + ((size_t)(b - ctx->last_first_box) * nc + c) * Ps;
+            if (unscale) {
+                int lev = 0;
+                while (lev + 1 < nlev && t->level_off[lev + 1] <= b) ++lev;
+                const int kind = what == OCCK_DBG_OBOX ? 0 : 1;
+                const double f = 1.0 / ctx->tp_scd[((size_t)kind * nlev + lev) * nc + c];
+                for (size_t q = 0; q < Ps; ++q) sp[q] *= f;
+            }
             double* dp = dst + ((size_t)b * nc + c) * P;
             size_t q = 0;
             for (int i = 0; i < no; ++i)
@@ -945,6 +1052,13 @@ extern "C" occk_status occk_device_status(occk_ctx* ctx, void* stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_device_status");
     if (werr) return fail(ctx, OCCK_ERR_TIMEOUT, "a tensor-core wait gave up in the last call");
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_translate_engine(occk_ctx* ctx, int mask) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (mask < -1 || mask > 7) return fail(ctx, OCCK_ERR_ARG, "mask must be -1..7");
+    ctx->tr_engine = mask;
     return OCCK_OK;
 }
 

@@ -169,6 +169,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         pa.Ct = (const float*)Ct; pa.W = (const float*)W; pa.Mbox = (const float*)Mb; pa.Obox = (float*)Ob;
         pa.KB = a.kb; pa.lscale = a.lscale;
         pa.nocc = nocc; pa.nrow = a.nrow; pa.nc = nc; pa.leaf_store0 = leaf_store0;
+        pa.scaled = a.tr_on; pa.inv_h_leaf = a.inv_h_leaf;
         pa.err = a.err_word;
         pa.panA = a.pan_a2A;
         pa.panB = a.pan_a2B;
@@ -193,12 +194,28 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     const int nchunk = (nc + LMC - 1) / LMC;
     const unsigned pblocks = (unsigned)((P + 128 * body::translate_ppt<T>() - 1) / (128 * body::translate_ppt<T>()));
     // (b) M2M: parents at level lev-1 gather their children at level lev
+    // tensor-core translations for the mixed forms (multipoles kept in FP32
+    // between steps, operands scaled per component, see kernels_tc_translate.cu)
+    const bool trc = tcm && a.tr_on;
+    const T* tops = trc ? (const T*)a.ops_scaled : ops;   // SIMT operators matching the storage
+    TrArgs th{};
+    if (trc) {
+        th.P = (int)P; th.nc = nc; th.first_box = a.first_box; th.nlev = a.tr_nlev; th.sm_count = a.sm_count;
+        th.parent = a.parent; th.box_level = a.box_level;
+        th.pan = a.tr_pan; th.err = a.err_word;
+    }
     mark(2);
     for (int lev = D; lev >= 3; --lev) {
         int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
+        if (trc && (a.tr_mask & 1)) {
+            cudaError_t e2 = tr_translate(a.prec, th, 0, t0, nt, a.child_ptr, a.child_list, a.m2m_op,
+                                          (const float*)Ob, (float*)Ob, 0, s);
+            if (e2 != cudaSuccess) return e2;
+            continue;
+        }
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 0, (int)P, nc, a.L, a.first_box, t0, a.child_ptr,
-                                             a.child_list, a.m2m_op, nullptr, a.parent, ops, Ob, Ob, 0);
+                                             a.child_list, a.m2m_op, nullptr, a.parent, tops, Ob, Ob, 0);
     }
     // learned ranks: features from the multipoles of every box, FP16 MLP,
     // budgeted choice; M2L then reads the per-edge ranks
@@ -214,19 +231,30 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (c) M2L: every box of levels 2..D, all levels in one launch
     mark(3);
-    {
+    if (trc && (a.tr_mask & 2)) {
+        int t0 = a.level_off[2], nt = a.nbox - t0;
+        cudaError_t e2 = tr_translate(a.prec, th, 1, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op, (const float*)Ob,
+                                      (float*)Mb, 0, s);
+        if (e2 != cudaSuccess) return e2;
+    } else {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 1, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
-                                             a.m2l_op, lmax_e, a.parent, ops, Ob, Mb, 0);
+                                             a.m2l_op, lmax_e, a.parent, tops, Ob, Mb, 0);
     }
     // (d) L2L: children at level lev accumulate their parent's expansion
     mark(4);
     for (int lev = 3; lev <= D; ++lev) {
         int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
+        if (trc && (a.tr_mask & 4)) {
+            cudaError_t e2 = tr_translate(a.prec, th, 2, t0, nt, nullptr, nullptr, a.l2l_op, (const float*)Mb,
+                                          (float*)Mb, 1, s);
+            if (e2 != cudaSuccess) return e2;
+            continue;
+        }
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 2, (int)P, nc, a.L, a.first_box, t0, nullptr, nullptr,
-                                             a.l2l_op, nullptr, a.parent, ops, Mb, Mb, 1);
+                                             a.l2l_op, nullptr, a.parent, tops, Mb, Mb, 1);
     }
     // (e) L2P
     mark(5);

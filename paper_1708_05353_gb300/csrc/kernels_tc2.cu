@@ -16,8 +16,10 @@
 // Every mbarrier wait is bounded; on timeout the CTA records the error word,
 // raises an abort flag that the other roles poll, frees TMEM and returns.
 //
-//   (e) KB[rowoff + r][i] = sum_{lm, j} (W[lm][r][j] / s^l) (w_lm Mcal[lm][i][j] s^l)
-//   (a) O[B][lm][i <= j] = s^l sum_r C_ri (W[lm][r][j] / s^l)
+//   (e) KB[rowoff + r][i] = sum_{lm, j} (W[lm][r][j] s_lm) (w_lm Mcal[lm][i][j] / s_lm)
+//   (a) O[B][lm][i <= j] = (1 / s_lm) sum_r C_ri (W[lm][r][j] s_lm)
+// with s_lm = sqrt((l+m)!(l-m)!) / h^l at the leaf level, which brings every
+// component to O(1) for the 16-bit formats.
 #include <cstdio>
 
 #include "occk_internal.h"
@@ -36,20 +38,11 @@ using namespace tc;
 constexpr uint32_t kLBO = 128, kSBO = 1024;
 constexpr int kPart = 128 * 128;                 // bytes of one panel part
 constexpr uint32_t kWait = 1u << 22;
-constexpr float kLo = 2048.f;
-
-enum { Q_BF16 = 0, Q_FP16 = 1, Q_TF32 = 2, Q_BF16X3 = 3, Q_FP16X3 = 4 };
-
 template <int P>
-struct Q {
-    static constexpr bool split = (P == Q_BF16X3 || P == Q_FP16X3);
-    static constexpr bool dual = (P == Q_FP16X3);
-    static constexpr int esz = (P == Q_TF32) ? 4 : 2;
-    static constexpr int BK = 128 / esz;
-    static constexpr int KSTEP = (P == Q_TF32) ? 8 : 16;
-    static constexpr uint32_t fmt = (P == Q_BF16 || P == Q_BF16X3) ? 1u : (P == Q_TF32 ? 2u : 0u);
-    static constexpr int pbytes = kPart * (split ? 2 : 1);
-    static constexpr int stages = split ? 3 : 4;
+struct Q : Fmt<P> {
+    static constexpr int BK = 128 / Fmt<P>::esz;
+    static constexpr int pbytes = kPart * (Fmt<P>::split ? 2 : 1);
+    static constexpr int stages = Fmt<P>::split ? 3 : 4;
     static constexpr int smem = stages * 2 * pbytes;
 };
 
@@ -64,49 +57,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
 
 // Write 8 consecutive K values of one panel row (row r, elements k8..k8+7 of
 // the panel) in the canonical layout, hi then lo part.
 template <int P>
 __device__ __forceinline__ void panel_put8(uint8_t* panel, int r, int k8, const float* v) {
     const uint32_t rowoff = (uint32_t)(r >> 3) * kSBO + (uint32_t)(r & 7) * 16u;
-    if constexpr (P == Q_TF32) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint4 q;
-            q.x = tf32_bits(v[4 * h + 0]);
-            q.y = tf32_bits(v[4 * h + 1]);
-            q.z = tf32_bits(v[4 * h + 2]);
-            q.w = tf32_bits(v[4 * h + 3]);
-            *reinterpret_cast<uint4*>(panel + rowoff + (uint32_t)((k8 / 4) + h) * kLBO) = q;
-        }
-    } else {
-        const uint32_t off = rowoff + (uint32_t)(k8 / 8) * kLBO;
-        if constexpr (P == Q_BF16 || P == Q_BF16X3) {
-            __nv_bfloat16 h[8], l[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                h[q] = __float2bfloat16_rn(v[q]);
-                l[q] = __float2bfloat16_rn(v[q] - __bfloat162float(h[q]));
-            }
-            *reinterpret_cast<uint4*>(panel + off) = *reinterpret_cast<uint4*>(h);
-            if constexpr (Q<P>::split) *reinterpret_cast<uint4*>(panel + kPart + off) = *reinterpret_cast<uint4*>(l);
-        } else {
-            __half h[8], l[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                h[q] = __float2half_rn(v[q]);
-                l[q] = __float2half_rn((v[q] - __half2float(h[q])) * kLo);
-            }
-            *reinterpret_cast<uint4*>(panel + off) = *reinterpret_cast<uint4*>(h);
-            if constexpr (Q<P>::split) *reinterpret_cast<uint4*>(panel + kPart + off) = *reinterpret_cast<uint4*>(l);
-        }
-    }
+    put8<P>(panel + rowoff + (uint32_t)((k8 * Q<P>::esz) / 16) * kLBO, kPart, kLBO, v);
 }
 
 __device__ __forceinline__ size_t tri_ix(int i, int j, int n) {
@@ -132,6 +89,8 @@ struct Plan {
     const int* kca;      // [nleaf] K chunks (rows of S_B / BK)
     const long long* offAa;  // [nleaf] first C panel
     const long long* offBa;  // [nleaf] first W panel
+    int scaled;              // O and Mcal stored in scaled form
+    float inv_h;             // 1 / leaf side
 };
 
 template <int P>
@@ -165,7 +124,8 @@ __global__ void k_panel_l2p_B(const float* __restrict__ Mbox, int nocc, int nc, 
     const int lm = kc / pl.jc, j0 = (kc % pl.jc) * BK;
     const int l = rank_of(lm);
     const float w = (lm == l * l) ? 2.f : (((lm - l * l) & 1) ? 4.f : -4.f);
-    const float sc = w / lscale[lm];
+    // scaled storage holds Mcal~ = Mcal h^(l+1) / g, and Mcal / s_lm = Mcal~ / h
+    const float sc = w * (pl.scaled ? pl.inv_h : 1.f / lscale[lm]);
     const size_t P2 = (size_t)nocc * (nocc + 1) / 2;
     const float* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P2;
     const int i = it * 128 + threadIdx.x;
@@ -406,7 +366,7 @@ k_pgemm_a2(int nocc, int nc, int ntile, int leaf_store0, Plan pl, const uint8_t*
     if (i >= nocc) return;
     const size_t P2 = (size_t)nocc * (nocc + 1) / 2;
     float* O = Obox + ((size_t)(leaf_store0 + B) * nc + lm) * P2;
-    const float inv = 1.f / lscale[lm];
+    const float inv = pl.scaled ? 1.f : 1.f / lscale[lm];   // scaled storage keeps O~ = O s_lm
 #pragma unroll
     for (int q = 0; q < 128; ++q) {
         const int j = tj * 128 + q;
@@ -471,7 +431,7 @@ template <int P>
 cudaError_t l2p_typed(const PanelArgs& a, cudaStream_t s) {
     cudaError_t e = attrs<P>();
     if (e != cudaSuccess) return e;
-    Plan pl{a.rtA, a.offA, a.KC, a.jc, a.it, a.kca, a.offAa, a.offBa};
+    Plan pl{a.rtA, a.offA, a.KC, a.jc, a.it, a.kca, a.offAa, a.offBa, a.scaled, a.inv_h_leaf};
     dim3 gA(a.KC, a.max_rt, a.nleaf), gB(a.KC, a.it, a.nleaf);
     k_panel_l2p_A<P><<<gA, 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, pl, a.lscale, a.panA);
     k_panel_l2p_B<P><<<gB, 128, 0, s>>>(a.Mbox, a.nocc, a.nc, a.leaf_store0, pl, a.lscale, a.panB);
@@ -484,7 +444,7 @@ template <int P>
 cudaError_t a2_typed(const PanelArgs& a, cudaStream_t s) {
     cudaError_t e = attrs<P>();
     if (e != cudaSuccess) return e;
-    Plan pl{a.rtA, a.offA, a.KC, a.jc, a.it, a.kca, a.offAa, a.offBa};
+    Plan pl{a.rtA, a.offA, a.KC, a.jc, a.it, a.kca, a.offAa, a.offBa, a.scaled, a.inv_h_leaf};
     dim3 gA(a.max_kca, a.it, a.nleaf), gB(a.max_kca, a.it * a.nc, a.nleaf);
     k_panel_a2_A<P><<<gA, 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, a.Ct, a.nocc, pl, a.panA);
     k_panel_a2_B<P><<<gB, 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, a.nc, pl, a.lscale, a.panB);

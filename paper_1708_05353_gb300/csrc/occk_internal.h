@@ -101,7 +101,7 @@ struct occk_tree {
         double* ops = nullptr;         // [nops][nc][nc]
         float* ops_f = nullptr;
         occk::OpDesc* opdesc = nullptr;
-        float* lscale = nullptr;       // [nc] 1/s_leaf^l
+        float* lscale = nullptr;       // [nc] sqrt((l+m)!(l-m)!) / h_leaf^l
         float* box_scale = nullptr;    // [nbox]
         int* box_key = nullptr;        // [nbox*3]
         int* box_level = nullptr;      // [nbox]
@@ -109,6 +109,7 @@ struct occk_tree {
         int* m2l_tgt = nullptr;        // [nm2l]
     } dev;
     int nops_alloc_lmax = -1;
+    long long gen = 0;                      // changes whenever the operators are regenerated
 };
 
 struct occk_ctx {
@@ -131,6 +132,13 @@ struct occk_ctx {
     int pp_nocc = -1, pp_nc = -1, pp_esz = -1, pp_pbytes = -1;
     int pp_KC = 0, pp_jc = 0, pp_it = 0, pp_max_rt = 0, pp_max_kca = 0;
     size_t pp_l2pA = 0, pp_l2pB = 0, pp_a2A = 0, pp_a2B = 0;   // panel counts
+    // operator panels of the tensor-core translations
+    occk::DevBuf tpan, tscale, tops;
+    long long tp_gen = -1;
+    int tp_prec = -1, tp_ok = 0;
+    std::vector<double> tp_scd;             // [2][nlev][nc] scales of the last panel build (host)
+    int last_scaled = 0;                    // last run kept O and Mcal in scaled form
+    int tr_engine = -1;                     // occk_set_translate_engine mask
     // stage timers
     int timing = 0;
     cudaEvent_t ev[OCCK_NSTAGE + 1] = {};
@@ -170,13 +178,19 @@ struct FmmArgs {
     int max_rows;
     cudaEvent_t* ev;                 // OCCK_NSTAGE+1 events or nullptr
     // tensor-core forms
-    const float* lscale;             // [nc] 1/s_leaf^l
+    const float* lscale;             // [nc] sqrt((l+m)!(l-m)!) / h_leaf^l
     const float* box_scale;          // [nbox] side of each box's level
     int* err_word;                   // device error word (bounded waits)
     // panel plan of the tensor-core steps (a) and (e)
     const int* pp_rtA; const long long* pp_offA; const int* pp_kca; const long long* pp_offAa;
     const long long* pp_offBa; int pp_KC, pp_jc, pp_it, pp_max_rt, pp_max_kca;
     uint8_t* pan_l2pA; uint8_t* pan_l2pB; uint8_t* pan_a2A; uint8_t* pan_a2B;
+    // tensor-core translations (tr_on: steps b-d on tcgen05, multipoles and
+    // local expansions stored in scaled form; otherwise SIMT, unscaled)
+    // tr_mask: bit 0 M2M, bit 1 M2L, bit 2 L2L on the tensor core (the others
+    // run on SIMT with the scaled FP32 operators ops_scaled)
+    const uint8_t* tr_pan; const float* ops_scaled; int tr_nlev, tr_on, tr_mask, sm_count;
+    float inv_h_leaf;
     // learned selector (lmax_policy 2); learned == 0 when unused
     int learned;
     const float* mlp_prm; void* mlp_h; const float* mlp_norm;
@@ -216,6 +230,7 @@ struct PanelArgs {
     const float* Ct; const float* W; const float* Mbox; float* Obox; double* KB;
     const float* lscale;
     int nocc, nrow, nc, leaf_store0;
+    int scaled; float inv_h_leaf;          // scaled storage of O and Mcal (see kernels_tc_translate.cu)
     uint8_t* panA; uint8_t* panB;
     int* err;
 };
@@ -223,6 +238,20 @@ int panel_elem_bytes(int prec);
 int panel_bytes(int prec);
 cudaError_t panel_l2p(int prec, const PanelArgs& a, cudaStream_t s);
 cudaError_t panel_a2(int prec, const PanelArgs& a, cudaStream_t s);
+
+// ----- tensor-core translations, steps (b)-(d) (kernels_tc_translate.cu) --------
+struct TrArgs {
+    int P, nc, first_box, nlev, sm_count;
+    const int* parent; const int* box_level;
+    const uint8_t* pan;                    // operator panels
+    int* err;
+};
+int tr_np(int nc);                          // N of the GEMM (0: no tensor-core form for this nc)
+size_t tr_panel_bytes(int prec, int nc);    // bytes of one operator's panels
+cudaError_t tr_build_panels(int prec, const double* ops, int nops, int nc, const int* opinfo, const double* scd,
+                            int nlev, uint8_t* pan, float* ops_scaled, cudaStream_t s);
+cudaError_t tr_translate(int prec, const TrArgs& h, int mode, int tgt0, int ntgt, const int* ptr, const int* list,
+                         const int* opidx, const float* in, float* out, int accumulate, cudaStream_t s);
 
 // ----- plain tensor-core GEMM for checking the engine (kernels_tc2.cu) --------
 int tc_mode(int prec);

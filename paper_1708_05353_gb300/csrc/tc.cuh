@@ -125,6 +125,73 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N, uint32_t fmt) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// ---- operand formats of the mixed-precision forms ---------------------------------
+// BF16 / FP16 / TF32: one product per K step.  BF16X3 / FP16X3: each FP32
+// value x is split as hi = rn(x), lo = rn(x - hi) and the product is
+// hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-2p of the product, is dropped).
+// For FP16 the lo part is stored times 2^11 so that it stays a normal number;
+// the cross terms then go to a second accumulator that is scaled back by 2^-11.
+enum { Q_BF16 = 0, Q_FP16 = 1, Q_TF32 = 2, Q_BF16X3 = 3, Q_FP16X3 = 4 };
+constexpr float kLo = 2048.f;
+
+template <int P>
+struct Fmt {
+    static constexpr bool split = (P == Q_BF16X3 || P == Q_FP16X3);
+    static constexpr bool dual = (P == Q_FP16X3);
+    static constexpr int esz = (P == Q_TF32) ? 4 : 2;
+    static constexpr int KSTEP = (P == Q_TF32) ? 8 : 16;   // K of one tcgen05.mma
+    static constexpr uint32_t fmt = (P == Q_BF16 || P == Q_BF16X3) ? 1u : (P == Q_TF32 ? 2u : 0u);
+};
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Convert 8 consecutive K values of one operand row into the format of P and
+// store them at `dst` (16-bit formats: one 16-byte chunk, i.e. one core-matrix
+// row; TF32: two chunks, the second `lbo` bytes further along K).  For the
+// split formats the lo part goes to dst + part_bytes.
+template <int P>
+__device__ __forceinline__ void put8(uint8_t* dst, uint32_t part_bytes, uint32_t lbo, const float* v) {
+    if constexpr (P == Q_TF32) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint4 q;
+            q.x = tf32_bits(v[4 * h + 0]);
+            q.y = tf32_bits(v[4 * h + 1]);
+            q.z = tf32_bits(v[4 * h + 2]);
+            q.w = tf32_bits(v[4 * h + 3]);
+            *reinterpret_cast<uint4*>(dst + h * lbo) = q;
+        }
+    } else if constexpr (P == Q_BF16 || P == Q_BF16X3) {
+        __nv_bfloat162 h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            if constexpr (Fmt<P>::split) {
+                const float2 f = __bfloat1622float2(h[q]);
+                l[q] = __floats2bfloat162_rn(v[2 * q] - f.x, v[2 * q + 1] - f.y);
+            }
+        }
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(h);
+        if constexpr (Fmt<P>::split) *reinterpret_cast<uint4*>(dst + part_bytes) = *reinterpret_cast<uint4*>(l);
+    } else {
+        __half2 h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+            if constexpr (Fmt<P>::split) {
+                const float2 f = __half22float2(h[q]);
+                l[q] = __floats2half2_rn((v[2 * q] - f.x) * kLo, (v[2 * q + 1] - f.y) * kLo);
+            }
+        }
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(h);
+        if constexpr (Fmt<P>::split) *reinterpret_cast<uint4*>(dst + part_bytes) = *reinterpret_cast<uint4*>(l);
+    }
+}
+
 // ---- splitting FP32 into low-precision hi/lo parts --------------------------------
 struct SplitBF16 {
     using T = __nv_bfloat16;

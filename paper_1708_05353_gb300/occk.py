@@ -76,6 +76,7 @@ _SIGS = {
     "occk_debug_fetch": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "occk_probe_fma_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_set_translate_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_device_status": (ctypes.c_int, [_vp, _vp]),
     "occk_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                          ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -171,6 +172,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_translate_engine(self, mask: int = -1):
+        """Translations of the mixed forms on the tensor core: bit 0 M2M, bit 1
+        M2L, bit 2 L2L; -1 chooses by expansion rank."""
+        self.check(lib().occk_set_translate_engine(self._h, int(mask)), "occk_set_translate_engine")
 
     def set_timing(self, on: bool):
         self.check(lib().occk_set_timing(self._h, 1 if on else 0), "occk_set_timing")
