@@ -299,14 +299,22 @@ occk_status occk_batch_buffers(occk_batch* batch, int sys, double** C_dev, doubl
  * captures the launch sequence into a CUDA graph on first use (and after a
  * tuning change) and replays it. */
 occk_status occk_batch_run(occk_batch* batch, int use_graph, void* stream);
-/* Autotune the batch's tile shapes: components per translation block (4, 9,
- * 16, 21, 25), persistent blocks per SM (2..32) and, in FP32, the SIMT GEMM
- * tile (64 or 128), by coordinate search timing whole batch runs with CUDA
- * events; the winner is cached in the text file `cache_path` (nullable) under
- * a key of GPU name, lmax, precision, number of systems, total pair count and
- * depth, and reused when the key is present.  cfg_out (nullable) receives
- * {chunk, blocks per SM, tile}.  Synchronises `stream`. */
+/* Autotune the batch: for the level-synchronous persistent mode (mode 0) its
+ * tile shapes -- components per translation block (4, 9, 16, 21, 25),
+ * persistent blocks per SM (2..32) and, in FP32, the SIMT GEMM tile (64 or
+ * 128) -- by coordinate search, then the per-system mode (mode 1: every
+ * system's own single-system pipeline on one of up to 8 forked streams,
+ * largest first, joined at the end), timing whole batch runs with CUDA events;
+ * the winner is cached in the text file `cache_path` (nullable, one line
+ * "key chunk blocks_per_sm tile mode") under a key of GPU name, lmax,
+ * precision, number of systems, total pair count and depth, and reused when
+ * the key is present.  cfg_out (nullable, 4 ints) receives {chunk, blocks per
+ * SM, tile, mode}.  Synchronises `stream`. */
 occk_status occk_batch_tune(occk_batch* batch, const char* cache_path, int* cfg_out, void* stream);
+/* Set the batch configuration directly: cfg = {chunk (4, 9, 16, 21 or 25),
+ * blocks per SM (1..64), tile (64 or 128), mode (0 or 1)}, as occk_batch_tune
+ * reports it.  OCCK_ERR_ARG for a value outside those sets. */
+occk_status occk_batch_set_config(occk_batch* batch, const int* cfg);
 
 /* Reads the device error word of the last occk_farfield_K on this context
  * (synchronises `stream`).  Returns OCCK_ERR_TIMEOUT if a bounded wait inside

@@ -84,9 +84,12 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
        const T* __restrict__ Ct, const T* __restrict__ W, int nocc, int nrow, int nc,
        int ntile, T* __restrict__ Obox, int leaf_store0) {
     constexpr int NTH = (BM / TM) * (BM / TM);
-    __shared__ __align__(16) T As[BK][BM];
-    __shared__ __align__(16) T Bs[BK][BM];
-    __shared__ int aos[BK];
+    constexpr int NL = (BK * BM) / NTH;          // elements per operand one thread moves per step
+    // FP32 with 8 columns per thread: a thread owns columns tx*4..tx*4+3 and
+    // BM/2 + tx*4.., so a quarter warp's 16-byte loads cover 128 contiguous bytes
+    constexpr bool kSplitCols = sizeof(T) == 4 && TM == 8 && BM / 2 == (BM / TM) * 4;
+    __shared__ __align__(16) T As[2][BK][BM];
+    __shared__ __align__(16) T Bs[2][BK][BM];
     const int B = by / nc;
     const int lm = by - B * nc;
     // triangular tile index -> (ti, tj), ti <= tj
@@ -105,33 +108,54 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
     for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
-    for (int k0 = 0; k0 < nr; k0 += BK) {
-        if (threadIdx.x < BK) aos[threadIdx.x] = (k0 + threadIdx.x < nr) ? leaf_aos[rb0 + k0 + threadIdx.x] : -1;
-        __syncthreads();
-        for (int e = threadIdx.x; e < BK * BM; e += NTH) {
-            int kk = e / BM, c = e - kk * BM;
-            int ao = aos[kk];
-            int ii = i0 + c, jj = j0 + c;
-            As[kk][c] = (ao >= 0 && ii < nocc) ? Ct[(size_t)ao * nocc + ii] : T(0);
-            Bs[kk][c] = (ao >= 0 && jj < nocc) ? Wl[(size_t)(k0 + kk) * nocc + jj] : T(0);
+    // the next K step is loaded into registers while the current one is
+    // multiplied; one barrier per step
+    T ra[NL], rb[NL];
+    auto gload = [&](int k0) {
+#pragma unroll
+        for (int m = 0; m < NL; ++m) {
+            const int e = threadIdx.x + NTH * m;
+            const int kk = e / BM, c = e - kk * BM;
+            const int r = k0 + kk;
+            const int ao = r < nr ? leaf_aos[rb0 + r] : -1;
+            ra[m] = (ao >= 0 && i0 + c < nocc) ? Ct[(size_t)ao * nocc + i0 + c] : T(0);
+            rb[m] = (r < nr && j0 + c < nocc) ? Wl[(size_t)r * nocc + j0 + c] : T(0);
         }
-        __syncthreads();
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int m = 0; m < NL; ++m) {
+            const int e = threadIdx.x + NTH * m;
+            const int kk = e / BM, c = e - kk * BM;
+            As[buf][kk][c] = ra[m];
+            Bs[buf][kk][c] = rb[m];
+        }
+    };
+    const int nk = (nr + BK - 1) / BK;
+    if (nk > 0) {
+        gload(0);
+        sstore(0);
+    }
+    __syncthreads();
+    for (int ks = 0; ks < nk; ++ks) {
+        const int buf = ks & 1;
+        if (ks + 1 < nk) gload((ks + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             T a[TM], b[TM];
-            if constexpr (sizeof(T) == 4 && TM % 4 == 0) {   // float4 shared loads
+            if constexpr (kSplitCols) {   // float4 shared loads; B columns tx*4.. and BM/2 + tx*4..
 #pragma unroll
                 for (int q = 0; q < TM; q += 4) {
-                    const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * TM + q]);
-                    const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * TM + q]);
+                    const float4 av = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM + q]);
+                    const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][(q / 4) * (BM / 2) + tx * 4]);
                     a[q] = av.x; a[q + 1] = av.y; a[q + 2] = av.z; a[q + 3] = av.w;
                     b[q] = bv.x; b[q + 1] = bv.y; b[q + 2] = bv.z; b[q + 3] = bv.w;
                 }
             } else {
 #pragma unroll
                 for (int q = 0; q < TM; ++q) {
-                    a[q] = As[kk][ty * TM + q];
-                    b[q] = Bs[kk][tx * TM + q];
+                    a[q] = As[buf][kk][ty * TM + q];
+                    b[q] = Bs[buf][kk][tx * TM + q];
                 }
             }
 #pragma unroll
@@ -139,6 +163,7 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
 #pragma unroll
                 for (int y = 0; y < TM; ++y) acc[x][y] += a[x] * b[y];
         }
+        if (ks + 1 < nk) sstore(buf ^ 1);
         __syncthreads();
     }
     const size_t P = npairs(nocc);
@@ -149,7 +174,7 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
         if (i >= nocc) continue;
 #pragma unroll
         for (int y = 0; y < TM; ++y) {
-            int j = j0 + tx * TM + y;
+            int j = j0 + (kSplitCols ? (y / 4) * (BM / 2) + tx * 4 + (y % 4) : tx * TM + y);
             if (j >= nocc || j < i) continue;
             O[tri_index(i, j, nocc)] = acc[x][y];
         }
@@ -392,21 +417,19 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
     }
 }
 
-// ---------------------------------------------------------------------------
-// K[r + i*ldk] = sum over the leaf rows of AO r of KB[row][i], in FP64, and the
-// per-block partial of E = -1/2 sum_ri C_ri K_ri.
-// ---------------------------------------------------------------------------
 // FP32 step (e): 96 AO rows x 128 orbitals per block (256 threads, thread
-// tile 6 rows x 8 contiguous orbitals, K step 16).  A leaf of up to 96 AOs is
+// tile 6 rows x 8 orbitals, the orbitals in two groups of 4 at tx*4 and
+// 64 + tx*4 so that a quarter warp's 16-byte loads are conflict-free; K step 16).  A leaf of up to 96 AOs is
 // one row tile, so each element of the packed Mcal is read once per leaf;
 // shared-memory operands are read as float2/float4 (5 loads per 48 FMAs).
-__device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, const int* __restrict__ leaf_rowoff,
+__device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nsplit, const int* __restrict__ leaf_rowoff,
                                                 const float* __restrict__ W, const float* __restrict__ Mbox,
                                                 int nocc, int nrow, int nc, int leaf_store0,
                                                 double* __restrict__ KB) {
     constexpr int BR = 96, BI = 128, BK = 16, TR = 6, TI = 8;
     __shared__ __align__(16) float As[BK][BR + 4];
     __shared__ __align__(16) float Bs[BK][BI + 4];
+    (void)nsplit;   // one block covers the whole (lm, j) range of its tile
     const int B = bz;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
     const int r0 = bx * BR, i0 = by * BI;
@@ -451,8 +474,10 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, const in
                     const float2 a0 = *reinterpret_cast<const float2*>(&As[kk][ty * TR]);
                     const float2 a1 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 2]);
                     const float2 a2 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 4]);
-                    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * TI]);
-                    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * TI + 4]);
+                    // columns tx*4.. and 64 + tx*4..: each quarter warp reads
+                    // 128 contiguous bytes (no bank conflict)
+                    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+                    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
                     const float av[6] = {a0.x, a0.y, a1.x, a1.y, a2.x, a2.y};
                     const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -470,16 +495,21 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, const in
         if (r >= nr) continue;
 #pragma unroll
         for (int y = 0; y < TI; ++y) {
-            const int i = i0 + tx * TI + y;
+            const int i = i0 + (y >> 2) * 64 + tx * 4 + (y & 3);
             if (i < nocc) KB[(size_t)(rb0 + r) * nocc + i] = (double)acc[x][y];
         }
     }
 }
 
+// ---------------------------------------------------------------------------
+// K[r + i*ldk] = sum over the leaf rows of AO r of KB[row][i] (summed over the
+// nsplit copies of KB when step (e) split its K range), in FP64, and the
+// per-block partial of E = -1/2 sum_ri C_ri K_ri.
+// ---------------------------------------------------------------------------
 static __device__ __forceinline__ void reduce_body(int bx, int by, int bz, const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
                            const double* __restrict__ KB, int nao, int nocc,
                            const double* __restrict__ C, int ldc, double* __restrict__ K, int ldk,
-                           double* __restrict__ part) {
+                           double* __restrict__ part, int nsplit = 1, size_t split_stride = 0) {
     __shared__ double red[256];
     double e = 0.0;
     const long long n = (long long)nao * nocc;
@@ -487,7 +517,8 @@ static __device__ __forceinline__ void reduce_body(int bx, int by, int bz, const
          x += (long long)bz * blockDim.x) {
         int i = (int)(x / nao), r = (int)(x - (long long)i * nao);
         double s = 0.0;
-        for (int q = ao_row_ptr[r]; q < ao_row_ptr[r + 1]; ++q) s += KB[(size_t)ao_rows[q] * nocc + i];
+        for (int q = ao_row_ptr[r]; q < ao_row_ptr[r + 1]; ++q)
+            for (int sp = 0; sp < nsplit; ++sp) s += KB[sp * split_stride + (size_t)ao_rows[q] * nocc + i];
         K[(size_t)i * ldk + r] = s;
         e += C[(size_t)i * ldc + r] * s;
     }

@@ -674,6 +674,46 @@ extern "C" occk_status occk_set_edge_lmax(occk_ctx* ctx, occk_tree* t, const int
 // Far-field K (steps a-e)
 // ===========================================================================
 
+namespace occk {
+FmmArgs simt_args(const occk_ctx* ctx, const occk_tree* t, int nocc, int prec, const double* C, int ldc, double* K,
+                  int ldk, double* Ex, void* ct, void* w, void* obox, void* mbox, double* kb, double* part,
+                  int* err_word) {
+    FmmArgs a{};
+    const int L = t->lmax, D = t->depth;
+    const int nbox = (int)t->parent.size();
+    const int nleaf = (int)t->leaf_rowoff.size() - 1;
+    int max_rows = 0;
+    for (int B = 0; B < nleaf; ++B) max_rows = std::max(max_rows, t->leaf_rowoff[B + 1] - t->leaf_rowoff[B]);
+    auto& d = t->dev;
+    a.nao = t->nao; a.nocc = nocc; a.ldc = ldc; a.ldk = ldk; a.nc = ncomp(L); a.L = L; a.depth = D;
+    a.nbox = nbox; a.first_box = D >= 2 ? t->level_off[2] : nbox; a.nleaf = nleaf; a.leaf0 = t->level_off[D];
+    a.nrow = (int)t->leaf_aos.size();
+    a.level_off = t->level_off.data();
+    a.prec = prec; a.C = C; a.K = K; a.Ex_dev = Ex;
+    a.row_ptr = d.row_ptr; a.ent_col = d.ent_col; a.ent_val = d.ent_val;
+    a.leaf_rowoff = d.leaf_rowoff; a.leaf_aos = d.leaf_aos;
+    a.ao_row_ptr = d.ao_row_ptr; a.ao_rows = d.ao_rows;
+    a.child_ptr = d.child_ptr; a.child_list = d.child_list; a.m2m_op = d.m2m_op; a.l2l_op = d.l2l_op;
+    a.parent = d.parent;
+    a.m2l_ptr = d.m2l_ptr; a.m2l_src = d.m2l_src; a.m2l_op = d.m2l_op; a.m2l_lmax = nullptr;
+    a.pair_vals = prec == OCCK_FP64 ? (const void*)d.pair_vals : (const void*)d.pair_vals_f;
+    a.ops = prec == OCCK_FP64 ? (const void*)d.ops : (const void*)d.ops_f;
+    a.ct = ct; a.w = w; a.obox = obox; a.mbox = mbox; a.kb = kb; a.part = part;
+    a.leaf_rowoff_host = t->leaf_rowoff.data();
+    a.max_rows = max_rows;
+    a.l2p_nsplit = 1;
+    a.ev = nullptr;
+    a.lscale = d.lscale; a.box_scale = d.box_scale;
+    a.err_word = err_word;
+    a.tr_pan = nullptr; a.ops_scaled = nullptr; a.tr_nlev = D + 1; a.tr_on = 0; a.tr_mask = 0;
+    a.sm_count = ctx->sm_count;
+    a.inv_h_leaf = (float)(1.0 / t->h[D]);
+    a.box_level = d.box_level;
+    a.learned = 0;
+    return a;
+}
+}  // namespace occk
+
 extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int nocc,
                                        const double* C_dev, int ldc, int prec, int lmax_policy,
                                        double* K_dev, int ldk, double* Ex_dev, double* Ex_host,
@@ -705,7 +745,11 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     size_t bytes_ct = es * (size_t)t->nao * nocc;
     size_t bytes_w = es * (size_t)nc * nrow * nocc;
     size_t bytes_box = es * nstore * nc * P;
-    size_t bytes_kb = 8 * (size_t)nrow * nocc;
+    // FP32 SIMT step (e) writes one copy of KB (a split of the (lm, j) range
+    // into several copies, summed by the K reduction, is supported by the
+    // kernels; measured slower on GB300 for the leaf sizes here)
+    int l2p_nsplit = 1;
+    size_t bytes_kb = 8 * (size_t)nrow * nocc * l2p_nsplit;
     size_t bytes_part = 8 * (size_t)(4096 + 2);
     if ((e = ensure(ctx->ct, bytes_ct)) != cudaSuccess ||
         (e = ensure(ctx->w, bytes_w)) != cudaSuccess ||
@@ -738,6 +782,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.kb = (double*)ctx->kb.p; a.part = (double*)ctx->part.p;
     a.leaf_rowoff_host = t->leaf_rowoff.data();
     a.max_rows = max_rows;
+    a.l2p_nsplit = l2p_nsplit;
     a.learned = 0;
     ctx->ranks_valid = 0;
     const int nm2l = (int)t->m2l_tgt.size();

@@ -158,8 +158,11 @@ using occk::TItem;
 
 extern "C" void occk_batch_destroy(occk_batch* b);
 
+// mode 0: level-synchronous persistent kernels over all systems' work items;
+// mode 1: each system's own pipeline (the single-system kernels) on one of
+// several forked streams, joined at the end (a fork-join graph when captured)
 struct BatchCfg {
-    int lmc = 9, bps = 8, tile = 128;
+    int lmc = 9, bps = 8, tile = 128, mode = 0;
 };
 
 struct occk_batch {
@@ -194,6 +197,13 @@ struct occk_batch {
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
     int sm_count = 0;
+    // mode 1: per-system pipelines on forked streams, largest system first
+    std::vector<occk::FmmArgs> fargs;
+    std::vector<int> order;
+    std::vector<cudaStream_t> fs;
+    std::vector<cudaEvent_t> fev;
+    cudaEvent_t ev_fork = nullptr;
+    int* err = nullptr;
 };
 
 namespace {
@@ -326,7 +336,23 @@ cudaError_t enqueue_typed(occk_batch* b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t enqueue_streams(occk_batch* b, cudaStream_t s) {
+    const int ns = (int)b->fs.size();
+    cudaError_t e = cudaEventRecord(b->ev_fork, s);
+    for (int j = 0; j < ns && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(b->fs[j], b->ev_fork, 0);
+    for (size_t k = 0; k < b->order.size() && e == cudaSuccess; ++k) {
+        const int sys = b->order[k];
+        e = occk::run_farfield(b->fargs[sys], b->fs[k % ns]);
+    }
+    for (int j = 0; j < ns && e == cudaSuccess; ++j) {
+        e = cudaEventRecord(b->fev[j], b->fs[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->fev[j], 0);
+    }
+    return e;
+}
+
 cudaError_t enqueue(occk_batch* b, cudaStream_t s) {
+    if (b->cfg.mode == 1) return enqueue_streams(b, s);
     if (b->built_lmc != b->cfg.lmc) {
         cudaError_t e = build_translate_items(b, b->cfg.lmc);
         if (e != cudaSuccess) return e;
@@ -405,7 +431,9 @@ extern "C" occk_status occk_batch_create(occk_ctx* ctx, int nsys, occk_tree* con
         o[s].obox = take(es * (size_t)(nbox - first) * nc * P + 8);
         o[s].mbox = take(es * (size_t)(nbox - first) * nc * P + 8);
         o[s].kb = take(8 * nrow * nocc[s]);
-        o[s].part = take(8 * (size_t)occk::kRedBlocks);
+        // room for the persistent reduction's partials and for those of the
+        // single-system pipeline (mode 1)
+        o[s].part = take(8 * (size_t)std::max(occk::kRedBlocks, occk::kFarfieldPartials));
     }
     size_t eoff = take(8 * (size_t)nsys);
     cudaError_t e = cudaMalloc(&b->arena, tot);
@@ -505,6 +533,29 @@ extern "C" occk_status occk_batch_create(occk_ctx* ctx, int nsys, occk_tree* con
     b->cfg.lmc = occk::translate_chunk_batch(nc);
     b->cfg.tile = prec == OCCK_FP64 ? 64 : 128;
     if (e == cudaSuccess) e = build_translate_items(b, b->cfg.lmc);
+    // per-system pipelines (mode 1): arguments over the same arena buffers,
+    // systems ordered by decreasing work and dealt round-robin to the streams
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        std::vector<std::pair<double, int>> work;
+        for (int s = 0; s < nsys; ++s) {
+            const SysDesc& d = b->h_sys[s];
+            b->fargs.push_back(occk::simt_args(ctx, trees[s], nocc[s], prec, d.C, d.ldc, d.K, d.ldk, b->E + s, d.ct,
+                                               d.w, d.obox, d.mbox, d.kb, d.part, b->err));
+            work.push_back({-(double)d.P * (double)(d.nbox + d.nrow), s});
+        }
+        std::sort(work.begin(), work.end());
+        for (auto& w : work) b->order.push_back(w.second);
+        const int ns = std::min(nsys, 8);
+        b->fs.resize(ns, nullptr);
+        b->fev.resize(ns, nullptr);
+        for (int j = 0; j < ns && e == cudaSuccess; ++j) {
+            e = cudaStreamCreateWithFlags(&b->fs[j], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fev[j], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
@@ -525,6 +576,12 @@ extern "C" void occk_batch_destroy(occk_batch* b) {
     if (b->cs) cudaStreamDestroy(b->cs);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
+    for (auto st : b->fs)
+        if (st) cudaStreamDestroy(st);
+    for (auto ev : b->fev)
+        if (ev) cudaEventDestroy(ev);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->err) cudaFree(b->err);
     free_items(b);
     for (void* p : {(void*)b->d_sys, (void*)b->it_tr, (void*)b->it_half, (void*)b->it_full64, (void*)b->it_full128,
                     (void*)b->it_l2p64, (void*)b->it_l2p128, (void*)b->it_red, (void*)b->en_sys, b->arena})
@@ -578,18 +635,32 @@ extern "C" occk_status occk_batch_run(occk_batch* b, int use_graph, void* stream
     return OCCK_OK;
 }
 
+extern "C" occk_status occk_batch_set_config(occk_batch* b, const int* cfg) {
+    if (!b || !cfg) return OCCK_ERR_ARG;
+    const int lmc = cfg[0], bps = cfg[1], tile = cfg[2], mode = cfg[3];
+    if ((lmc != 4 && lmc != 9 && lmc != 16 && lmc != 21 && lmc != 25) || bps < 1 || bps > 64 ||
+        (tile != 64 && tile != 128) || (mode != 0 && mode != 1))
+        return bfail(b->ctx, OCCK_ERR_ARG, "batch config out of range");
+    b->cfg.lmc = lmc;
+    b->cfg.bps = bps;
+    b->cfg.tile = tile;
+    b->cfg.mode = mode;
+    b->graph_valid = false;
+    return OCCK_OK;
+}
+
 extern "C" occk_status occk_batch_tune(occk_batch* b, const char* cache_path, int* cfg_out, void* stream) {
     if (!b) return OCCK_ERR_ARG;
     occk_ctx* ctx = b->ctx;
     cudaSetDevice(ctx->device);
     const std::string key = cfg_key(b);
-    // cache lookup: lines "key lmc bps tile"
+    // cache lookup: lines "key lmc bps tile mode"
     std::map<std::string, BatchCfg> cache;
     if (cache_path) {
         std::ifstream f(cache_path);
         std::string k;
         BatchCfg c;
-        while (f >> k >> c.lmc >> c.bps >> c.tile) cache[k] = c;
+        while (f >> k >> c.lmc >> c.bps >> c.tile >> c.mode) cache[k] = c;
     }
     auto it = cache.find(key);
     if (it != cache.end()) {
@@ -614,6 +685,7 @@ extern "C" occk_status occk_batch_tune(occk_batch* b, const char* cache_path, in
             return best;
         };
         BatchCfg best = b->cfg;
+        best.mode = 0;
         float tb = time_cfg(best);
         for (int lmc : {4, 9, 16, 21, 25}) {
             BatchCfg c = best;
@@ -635,13 +707,21 @@ extern "C" occk_status occk_batch_tune(occk_batch* b, const char* cache_path, in
                 if (t < tb) { tb = t; best = c; }
             }
         }
+        {
+            BatchCfg c = best;
+            c.mode = 1;
+            float t = time_cfg(c);
+            if (t < tb) { tb = t; best = c; }
+        }
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
         b->cfg = best;
         cache[key] = best;
         if (cache_path) {
             std::ofstream f(cache_path);
-            for (auto& kv : cache) f << kv.first << " " << kv.second.lmc << " " << kv.second.bps << " " << kv.second.tile << "\n";
+            for (auto& kv : cache)
+                f << kv.first << " " << kv.second.lmc << " " << kv.second.bps << " " << kv.second.tile << " "
+                  << kv.second.mode << "\n";
         }
     }
     b->graph_valid = false;
@@ -653,6 +733,7 @@ extern "C" occk_status occk_batch_tune(occk_batch* b, const char* cache_path, in
         cfg_out[0] = b->cfg.lmc;
         cfg_out[1] = b->cfg.bps;
         cfg_out[2] = b->cfg.tile;
+        cfg_out[3] = b->cfg.mode;
     }
     return OCCK_OK;
 }

@@ -71,15 +71,18 @@ k_l2p_r32(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, con
 }
 
 __global__ void __launch_bounds__(256)
-k_l2p_r96f(const int* __restrict__ leaf_rowoff, const float* __restrict__ W, const float* __restrict__ Mbox,
-           int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
-    body::l2p_rect_body_f(blockIdx.x, blockIdx.y, blockIdx.z, leaf_rowoff, W, Mbox, nocc, nrow, nc, leaf_store0, KB);
+k_l2p_r96f(int nsplit, const int* __restrict__ leaf_rowoff, const float* __restrict__ W,
+           const float* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+    body::l2p_rect_body_f(blockIdx.x, blockIdx.y, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
+                          leaf_store0, KB);
 }
 
 __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
                            const double* __restrict__ KB, int nao, int nocc, const double* __restrict__ C, int ldc,
-                           double* __restrict__ K, int ldk, double* __restrict__ part) {
-    body::reduce_body(blockIdx.x, 0, gridDim.x, ao_row_ptr, ao_rows, KB, nao, nocc, C, ldc, K, ldk, part);
+                           double* __restrict__ K, int ldk, double* __restrict__ part, int nsplit,
+                           size_t split_stride) {
+    body::reduce_body(blockIdx.x, 0, gridDim.x, ao_row_ptr, ao_rows, KB, nao, nocc, C, ldc, K, ldk, part, nsplit,
+                      split_stride);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,7 +185,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
                                                                  a.nrow, nc, nt, Ob, leaf_store0);
     } else {
-        constexpr int BM = 128, BK = 8, TM = 8;
+        constexpr int BM = 128, BK = 16, TM = 8;
         int nt = (nocc + BM - 1) / BM;
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
@@ -270,14 +273,16 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         k_l2p_r32<<<g, 256, 0, s>>>(a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow, nc,
                                     leaf_store0, a.kb);
     } else {
-        dim3 g((a.max_rows + 95) / 96, (nocc + 127) / 128, a.nleaf);
-        k_l2p_r96f<<<g, 256, 0, s>>>(a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
+        const int nsplit = a.l2p_nsplit;
+        dim3 g((a.max_rows + 95) / 96, (nocc + 127) / 128, a.nleaf * nsplit);
+        k_l2p_r96f<<<g, 256, 0, s>>>(nsplit, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
                                      leaf_store0, a.kb);
     }
     mark(6);
-    constexpr int kRedBlocks = 1024;
+    constexpr int kRedBlocks = kFarfieldPartials;
+    const int nsplit = (sizeof(T) == 4 && !tcm) ? a.l2p_nsplit : 1;
     k_reduce_K<<<kRedBlocks, 256, 0, s>>>(a.ao_row_ptr, a.ao_rows, a.kb, a.nao, nocc, a.C, a.ldc, a.K,
-                                          a.ldk, a.part);
+                                          a.ldk, a.part, nsplit, (size_t)a.nrow * nocc);
     k_final_energy<<<1, 256, 0, s>>>(a.part, kRedBlocks, a.Ex_dev);
     mark(OCCK_NSTAGE);
     return cudaGetLastError();

@@ -176,6 +176,7 @@ struct FmmArgs {
     void* ct; void* w; void* obox; void* mbox; double* kb; double* part;
     const int* leaf_rowoff_host;     // host copy (max rows)
     int max_rows;
+    int l2p_nsplit;                  // FP32 SIMT step (e): K-range splits (KB holds that many copies)
     cudaEvent_t* ev;                 // OCCK_NSTAGE+1 events or nullptr
     // tensor-core forms
     const float* lscale;             // [nc] sqrt((l+m)!(l-m)!) / h_leaf^l
@@ -198,6 +199,13 @@ struct FmmArgs {
     const int* m2l_tgt; const int* box_key; const int* box_level; const double* hlev;
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
+// partial energies run_farfield writes to FmmArgs::part (its K reduction blocks)
+constexpr int kFarfieldPartials = 1024;
+// Arguments of the SIMT FP64/FP32 path for one tree with caller-provided
+// workspaces (the batch's per-system pipelines; host.cpp).
+FmmArgs simt_args(const occk_ctx* ctx, const occk_tree* t, int nocc, int prec, const double* C, int ldc, double* K,
+                  int ldk, double* Ex, void* ct, void* w, void* obox, void* mbox, double* kb, double* part,
+                  int* err_word);
 size_t workspace_elems_w(const FmmArgs& a);
 
 cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s);

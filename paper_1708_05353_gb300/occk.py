@@ -77,6 +77,7 @@ _SIGS = {
     "occk_probe_fma_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_translate_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "occk_device_status": (ctypes.c_int, [_vp, _vp]),
     "occk_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                          ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -321,10 +322,15 @@ class Batch:
         self.ctx.check(lib().occk_batch_run(self._h, 1 if use_graph else 0, _stream_ptr(stream)), "occk_batch_run")
 
     def tune(self, cache_path=None, stream=None):
-        cfg = (ctypes.c_int * 3)()
+        cfg = (ctypes.c_int * 4)()
         self.ctx.check(lib().occk_batch_tune(self._h, cache_path.encode() if cache_path else None, cfg,
                                              _stream_ptr(stream)), "occk_batch_tune")
-        return dict(chunk=cfg[0], blocks_per_sm=cfg[1], tile=cfg[2])
+        return dict(chunk=cfg[0], blocks_per_sm=cfg[1], tile=cfg[2], mode=cfg[3])
+
+    def set_config(self, chunk=9, blocks_per_sm=8, tile=128, mode=0):
+        """Configuration without tuning (the values occk_batch_tune reports)."""
+        cfg = (ctypes.c_int * 4)(chunk, blocks_per_sm, tile, mode)
+        self.ctx.check(lib().occk_batch_set_config(self._h, cfg), "occk_batch_set_config")
 
     def close(self):
         if self._h:

@@ -1,8 +1,9 @@
-"""Batched far field: uneven systems in one persistent, graph-captured launch
-sequence must reproduce each system's single-system result (FP64: 1e-12
-relative; FP32: 1e-5), include a system with no far field (depth 1), replay
-from the CUDA graph bit-identically, match the FP64 oracle, and the
-autotuner must write and reuse its cache."""
+"""Batched far field: uneven systems, in either batch mode (one persistent,
+level-synchronous launch sequence over all systems, or every system's own
+pipeline on forked streams), graph-captured, must reproduce each system's
+single-system result (FP64: 1e-12 relative; FP32: 1e-5), include a system
+with no far field (depth 1), replay from the CUDA graph bit-identically, match
+the FP64 oracle, and the autotuner must write and reuse its cache."""
 import os
 
 import numpy as np
@@ -54,12 +55,16 @@ def _read(b, systems):
     return out
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_batch_matches_single(prec, tol):
+def test_batch_matches_single(prec, tol, mode):
+    """Both batch modes: level-synchronous persistent kernels (0) and every
+    system's own pipeline on forked streams (1)."""
     from paper_1708_05353_gb300 import occk
     ctx = occk.Context(0)
     systems = _systems()
     trees, b = _batch(ctx, systems, prec)
+    b.set_config(tile=64 if prec == "fp64" else 128, mode=mode)
     b.run(use_graph=False)
     torch.cuda.synchronize()
     got = _read(b, systems)
@@ -74,11 +79,13 @@ def test_batch_matches_single(prec, tol):
         assert abs(E - Es) <= tol * abs(Es)
 
 
-def test_batch_graph_replay_and_oracle():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_graph_replay_and_oracle(mode):
     from paper_1708_05353_gb300 import occk
     ctx = occk.Context(0)
     systems = _systems()
     trees, b = _batch(ctx, systems, "fp64")
+    b.set_config(tile=64, mode=mode)
     b.run(use_graph=False)
     torch.cuda.synchronize()
     ref = _read(b, systems)
@@ -102,9 +109,9 @@ def test_batch_autotune_cache(tmp_path):
     path = str(tmp_path / "tune.txt")
     cfg = b.tune(path)
     assert os.path.exists(path)
-    assert cfg["chunk"] in (4, 9, 16, 21, 25) and cfg["tile"] in (64, 128)
+    assert cfg["chunk"] in (4, 9, 16, 21, 25) and cfg["tile"] in (64, 128) and cfg["mode"] in (0, 1)
     line = open(path).read().split()
-    assert [int(x) for x in line[1:4]] == [cfg["chunk"], cfg["blocks_per_sm"], cfg["tile"]]
+    assert [int(x) for x in line[1:5]] == [cfg["chunk"], cfg["blocks_per_sm"], cfg["tile"], cfg["mode"]]
     # cached: the same configuration without re-timing
     assert b.tune(path) == cfg
     b.run(use_graph=True)
