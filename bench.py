@@ -422,10 +422,14 @@ def main():
             E64 = float(Ex.item())
             K64 = K.clone()
         else:
+            Kmain, Emain = K.clone(), float(Ex.item())
             occk.farfield_K(ctx, tree, Cf, prec="fp64", K=K, Ex=Ex)
             E64 = float(Ex.item())
             K64 = K.clone()
         kmax = float(K64.abs().max().item())
+        if args.prec != "fp64":
+            result["error_vs_fp64"] = {"abs_dE_Eh": abs(Emain - E64),
+                                       "rel_dK": float((Kmain - K64).abs().max().item()) / kmax}
         var = {}
         for vp in [v for v in args.variants.split(",") if v and v != args.prec]:
             for _ in range(2):

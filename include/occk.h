@@ -175,9 +175,10 @@ occk_status occk_set_edge_lmax(occk_ctx* ctx, occk_tree* tree, const int* ranks,
  *          ranks are chosen on the device for the budget of
  *          occk_set_learned_tau (falls back to 0 without a model or when the
  *          tree's lmax < 2)
- * Requires occk_pair_multipoles on this tree.  Workspaces are owned by the
- * context and grow on demand (allocation happens outside any timed loop on
- * the first call with a given shape). */
+ * Requires occk_pair_multipoles on this tree and 1 <= nocc <= 65535 (stored
+ * occupied pairs i <= j are indexed in 32 bits; OCCK_ERR_SHAPE above).
+ * Workspaces are owned by the context and grow on demand (allocation happens
+ * outside any timed loop on the first call with a given shape). */
 occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tree, int nocc,
                             const double* C_dev, int ldc, int prec, int lmax_policy,
                             double* K_dev, int ldk, double* Ex_dev, double* Ex_host,

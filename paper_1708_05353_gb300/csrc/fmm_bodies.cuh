@@ -463,9 +463,10 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nspl
                 const int e = threadIdx.x + 256 * m;
                 const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
                 const int i = i0 + row, j = k0 + kk;
-                Bs[kk][row] = (i < nocc && j < nocc)
-                                  ? w * Ml[i <= j ? tri_index(i, j, nocc) : tri_index(j, i, nocc)]
-                                  : 0.f;
+                // packed index of (min, max) in 32-bit arithmetic (P < 2^32)
+                const unsigned a = (unsigned)min(i, j), bb = (unsigned)max(i, j);
+                const unsigned q = ((a * (2u * (unsigned)nocc + 1u - a)) >> 1) + (bb - a);
+                Bs[kk][row] = (i < nocc && j < nocc) ? w * Ml[q] : 0.f;
             }
             __syncthreads();
             if (warp_live) {

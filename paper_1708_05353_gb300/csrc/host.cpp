@@ -724,6 +724,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device bound to this context or tree");
     if (t->lmax < 0) return fail(ctx, OCCK_ERR_STATE, "call occk_pair_multipoles first");
     if (nocc <= 0 || !C_dev || !K_dev) return fail(ctx, OCCK_ERR_ARG, "nocc <= 0 or null C/K");
+    if (nocc > 65535) return fail(ctx, OCCK_ERR_SHAPE, "nocc above 65535 (pair indices are 32-bit)");
     if (ldc < t->nao || ldk < t->nao) return fail(ctx, OCCK_ERR_SHAPE, "ldc/ldk < nao");
     if (prec < OCCK_FP64 || prec > OCCK_FP16X3) return fail(ctx, OCCK_ERR_ARG, "unknown precision");
     if (lmax_policy < 0 || lmax_policy > 2) return fail(ctx, OCCK_ERR_ARG, "lmax_policy must be 0, 1 or 2");
