@@ -419,18 +419,22 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
 
 // FP32 step (e): 96 AO rows x 128 orbitals per block (256 threads, thread
 // tile 6 rows x 8 orbitals, the orbitals in two groups of 4 at tx*4 and
-// 64 + tx*4 so that a quarter warp's 16-byte loads are conflict-free; K step 16).  A leaf of up to 96 AOs is
+// 64 + tx*4 so that a quarter warp's 16-byte loads are conflict-free; K step
+// 32).  The (lm, j) range may be split over `nsplit` blocks, each writing its
+// own copy of KB (summed by the K reduction), so that the grid covers the GPU
+// in several waves instead of one and a sliver.  A leaf of up to 96 AOs is
 // one row tile, so each element of the packed Mcal is read once per leaf;
 // shared-memory operands are read as float2/float4 (5 loads per 48 FMAs).
 __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nsplit, const int* __restrict__ leaf_rowoff,
                                                 const float* __restrict__ W, const float* __restrict__ Mbox,
                                                 int nocc, int nrow, int nc, int leaf_store0,
                                                 double* __restrict__ KB) {
-    constexpr int BR = 96, BI = 128, BK = 16, TR = 6, TI = 8;
+    constexpr int BR = 96, BI = 128, BK = 32, TR = 6, TI = 8;
     __shared__ __align__(16) float As[BK][BR + 4];
     __shared__ __align__(16) float Bs[BK][BI + 4];
-    (void)nsplit;   // one block covers the whole (lm, j) range of its tile
-    const int B = bz;
+    // block z = leaf * nsplit + split: the split covers its share of the
+    // flattened (lm, j-chunk) range and writes its own copy of KB
+    const int B = bz / nsplit, ks = bz % nsplit;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
     const int r0 = bx * BR, i0 = by * BI;
     if (r0 >= nr) return;
@@ -443,52 +447,53 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nspl
         for (int b = 0; b < TI; ++b) acc[a][b] = 0.f;
     // rows of this warp: r0 + 12 w .. r0 + 12 w + 11
     const bool warp_live = r0 + (threadIdx.x >> 5) * 2 * TR < nr;
-    for (int lm = 0; lm < nc; ++lm) {
+    const int jt = (nocc + BK - 1) / BK, nkt = nc * jt;
+    const int kt0 = (int)((long long)nkt * ks / nsplit), kt1 = (int)((long long)nkt * (ks + 1) / nsplit);
+    for (int kt = kt0; kt < kt1; ++kt) {
+        const int lm = kt / jt, k0 = (kt - lm * jt) * BK;
         int l = 0;
         while ((l + 1) * (l + 1) <= lm) ++l;
         const float w = (lm == l * l) ? 2.f : (((lm - l * l) & 1) ? 4.f : -4.f);
         const float* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
         const float* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
-        for (int k0 = 0; k0 < nocc; k0 += BK) {
 #pragma unroll
-            for (int m = 0; m < (BR * BK) / 256; ++m) {
-                const int e = threadIdx.x + 256 * m;
-                const int row = e / BK, kk = e % BK;
-                const int r = r0 + row, j = k0 + kk;
-                As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.f;
-            }
-            const bool below = k0 + BK <= i0;
-#pragma unroll
-            for (int m = 0; m < (BI * BK) / 256; ++m) {
-                const int e = threadIdx.x + 256 * m;
-                const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
-                const int i = i0 + row, j = k0 + kk;
-                // packed index of (min, max) in 32-bit arithmetic (P < 2^32)
-                const unsigned a = (unsigned)min(i, j), bb = (unsigned)max(i, j);
-                const unsigned q = ((a * (2u * (unsigned)nocc + 1u - a)) >> 1) + (bb - a);
-                Bs[kk][row] = (i < nocc && j < nocc) ? w * Ml[q] : 0.f;
-            }
-            __syncthreads();
-            if (warp_live) {
-#pragma unroll
-                for (int kk = 0; kk < BK; ++kk) {
-                    const float2 a0 = *reinterpret_cast<const float2*>(&As[kk][ty * TR]);
-                    const float2 a1 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 2]);
-                    const float2 a2 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 4]);
-                    // columns tx*4.. and 64 + tx*4..: each quarter warp reads
-                    // 128 contiguous bytes (no bank conflict)
-                    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-                    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
-                    const float av[6] = {a0.x, a0.y, a1.x, a1.y, a2.x, a2.y};
-                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                    for (int x = 0; x < TR; ++x)
-#pragma unroll
-                        for (int y = 0; y < TI; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
-                }
-            }
-            __syncthreads();
+        for (int m = 0; m < (BR * BK) / 256; ++m) {
+            const int e = threadIdx.x + 256 * m;
+            const int row = e / BK, kk = e % BK;
+            const int r = r0 + row, j = k0 + kk;
+            As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.f;
         }
+        const bool below = k0 + BK <= i0;
+#pragma unroll
+        for (int m = 0; m < (BI * BK) / 256; ++m) {
+            const int e = threadIdx.x + 256 * m;
+            const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
+            const int i = i0 + row, j = k0 + kk;
+            // packed index of (min, max) in 32-bit arithmetic (P < 2^32)
+            const unsigned a = (unsigned)min(i, j), bb = (unsigned)max(i, j);
+            const unsigned q = ((a * (2u * (unsigned)nocc + 1u - a)) >> 1) + (bb - a);
+            Bs[kk][row] = (i < nocc && j < nocc) ? w * Ml[q] : 0.f;
+        }
+        __syncthreads();
+        if (warp_live) {
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const float2 a0 = *reinterpret_cast<const float2*>(&As[kk][ty * TR]);
+                const float2 a1 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 2]);
+                const float2 a2 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 4]);
+                // columns tx*4.. and 64 + tx*4..: each quarter warp reads
+                // 128 contiguous bytes (no bank conflict)
+                const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+                const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+                const float av[6] = {a0.x, a0.y, a1.x, a1.y, a2.x, a2.y};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int x = 0; x < TR; ++x)
+#pragma unroll
+                    for (int y = 0; y < TI; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+            }
+        }
+        __syncthreads();
     }
 #pragma unroll
     for (int x = 0; x < TR; ++x) {
@@ -497,7 +502,7 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nspl
 #pragma unroll
         for (int y = 0; y < TI; ++y) {
             const int i = i0 + (y >> 2) * 64 + tx * 4 + (y & 3);
-            if (i < nocc) KB[(size_t)(rb0 + r) * nocc + i] = (double)acc[x][y];
+            if (i < nocc) KB[(size_t)ks * nrow * nocc + (size_t)(rb0 + r) * nocc + i] = (double)acc[x][y];
         }
     }
 }

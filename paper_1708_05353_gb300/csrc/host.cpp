@@ -746,10 +746,22 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     size_t bytes_ct = es * (size_t)t->nao * nocc;
     size_t bytes_w = es * (size_t)nc * nrow * nocc;
     size_t bytes_box = es * nstore * nc * P;
-    // FP32 SIMT step (e) writes one copy of KB (a split of the (lm, j) range
-    // into several copies, summed by the K reduction, is supported by the
-    // kernels; measured slower on GB300 for the leaf sizes here)
+    // FP32 SIMT step (e): split the (lm, j) range until the grid covers the
+    // GPU about eight times (two 256-thread blocks per SM); each split writes
+    // its own copy of KB, summed by the K reduction.  Measured on GB300
+    // (C150H302 L 2 and 6, (H2O)100 L 4): 1.3-1.6x faster than one split,
+    // including the longer reduction
     int l2p_nsplit = 1;
+    if (prec == OCCK_FP32) {
+        long long tiles = 0;
+        for (int B = 0; B < nleaf; ++B) tiles += (t->leaf_rowoff[B + 1] - t->leaf_rowoff[B] + 95) / 96;
+        tiles *= (nocc + 127) / 128;
+        const long long want = 8LL * std::max(ctx->sm_count, 1) * 2;
+        const int nkt = nc * ((nocc + 31) / 32);
+        l2p_nsplit = (int)std::min<long long>((want + tiles - 1) / std::max<long long>(tiles, 1), 8);
+        l2p_nsplit = std::max(1, std::min(l2p_nsplit, nkt / 8));
+        if (ctx->l2p_split > 0) l2p_nsplit = std::min(ctx->l2p_split, std::max(1, nkt));
+    }
     size_t bytes_kb = 8 * (size_t)nrow * nocc * l2p_nsplit;
     size_t bytes_part = 8 * (size_t)(4096 + 2);
     if ((e = ensure(ctx->ct, bytes_ct)) != cudaSuccess ||
@@ -1098,6 +1110,13 @@ extern "C" occk_status occk_device_status(occk_ctx* ctx, void* stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_device_status");
     if (werr) return fail(ctx, OCCK_ERR_TIMEOUT, "a tensor-core wait gave up in the last call");
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (nsplit < 0 || nsplit > 64) return fail(ctx, OCCK_ERR_ARG, "nsplit must be 0..64");
+    ctx->l2p_split = nsplit;
     return OCCK_OK;
 }
 

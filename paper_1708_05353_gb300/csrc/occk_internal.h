@@ -139,6 +139,7 @@ struct occk_ctx {
     std::vector<double> tp_scd;             // [2][nlev][nc] scales of the last panel build (host)
     int last_scaled = 0;                    // last run kept O and Mcal in scaled form
     int tr_engine = -1;                     // occk_set_translate_engine mask
+    int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
     // stage timers
     int timing = 0;
     cudaEvent_t ev[OCCK_NSTAGE + 1] = {};

@@ -78,6 +78,7 @@ _SIGS = {
     "occk_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_translate_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "occk_set_l2p_split": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_device_status": (ctypes.c_int, [_vp, _vp]),
     "occk_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                          ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -178,6 +179,10 @@ class Context:
         """Translations of the mixed forms on the tensor core: bit 0 M2M, bit 1
         M2L, bit 2 L2L; -1 chooses by expansion rank."""
         self.check(lib().occk_set_translate_engine(self._h, int(mask)), "occk_set_translate_engine")
+
+    def set_l2p_split(self, nsplit: int = 0):
+        """K-range splits of the FP32 SIMT step (e); 0 chooses automatically."""
+        self.check(lib().occk_set_l2p_split(self._h, int(nsplit)), "occk_set_l2p_split")
 
     def set_timing(self, on: bool):
         self.check(lib().occk_set_timing(self._h, 1 if on else 0), "occk_set_timing")
