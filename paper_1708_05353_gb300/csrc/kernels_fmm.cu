@@ -173,6 +173,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         pa.KB = a.kb; pa.lscale = a.lscale;
         pa.nocc = nocc; pa.nrow = a.nrow; pa.nc = nc; pa.leaf_store0 = leaf_store0;
         pa.scaled = a.tr_on; pa.inv_h_leaf = a.inv_h_leaf;
+        pa.nsplit = a.l2p_nsplit;
         pa.err = a.err_word;
         pa.panA = a.pan_a2A;
         pa.panB = a.pan_a2B;
@@ -280,7 +281,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     mark(6);
     constexpr int kRedBlocks = kFarfieldPartials;
-    const int nsplit = (sizeof(T) == 4 && !tcm) ? a.l2p_nsplit : 1;
+    const int nsplit = sizeof(T) == 4 ? a.l2p_nsplit : 1;
     k_reduce_K<<<kRedBlocks, 256, 0, s>>>(a.ao_row_ptr, a.ao_rows, a.kb, a.nao, nocc, a.C, a.ldc, a.K,
                                           a.ldk, a.part, nsplit, (size_t)a.nrow * nocc);
     k_final_energy<<<1, 256, 0, s>>>(a.part, kRedBlocks, a.Ex_dev);

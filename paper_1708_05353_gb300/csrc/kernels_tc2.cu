@@ -317,24 +317,27 @@ __device__ __forceinline__ bool pgemm_tile(const uint8_t* Apanels, const uint8_t
     return ok;
 }
 
+// blockIdx.z = leaf * nsplit + split: a split runs its share of the K panels
+// and writes its own copy of KB (the K reduction adds the copies)
 template <int P>
 __global__ void __launch_bounds__(192, 1)
-k_pgemm_l2p(const int* __restrict__ leaf_rowoff, int nocc, Plan pl, const uint8_t* __restrict__ Apan,
-            const uint8_t* __restrict__ Bpan, double* __restrict__ KB, int* err) {
-    const int rt = blockIdx.x, it = blockIdx.y, B = blockIdx.z;
+k_pgemm_l2p(const int* __restrict__ leaf_rowoff, int nocc, int nrow, int nsplit, Plan pl,
+            const uint8_t* __restrict__ Apan, const uint8_t* __restrict__ Bpan, double* __restrict__ KB, int* err) {
+    const int rt = blockIdx.x, it = blockIdx.y, B = blockIdx.z / nsplit, ks = blockIdx.z % nsplit;
     if (rt >= pl.rtA[B]) return;
-    const uint8_t* A = Apan + (size_t)(pl.offA[B] + (long long)rt * pl.KC) * Q<P>::pbytes;
-    const uint8_t* Bp = Bpan + (size_t)(((long long)B * pl.it + it) * pl.KC) * Q<P>::pbytes;
+    const int kc0 = (int)((long long)pl.KC * ks / nsplit), kc1 = (int)((long long)pl.KC * (ks + 1) / nsplit);
+    const uint8_t* A = Apan + (size_t)(pl.offA[B] + (long long)rt * pl.KC + kc0) * Q<P>::pbytes;
+    const uint8_t* Bp = Bpan + (size_t)(((long long)B * pl.it + it) * pl.KC + kc0) * Q<P>::pbytes;
     float acc[128];
 #pragma unroll
     for (int q = 0; q < 128; ++q) acc[q] = 0.f;
-    const bool ok = pgemm_tile<P>(A, Bp, pl.KC, acc, err);
+    const bool ok = pgemm_tile<P>(A, Bp, kc1 - kc0, acc, err);
     const int warp = threadIdx.x >> 5;
     if (!ok || warp < 2) return;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
     const int r = rt * 128 + (warp & 3) * 32 + (threadIdx.x & 31);
     if (r >= nr) return;
-    double* out = KB + (size_t)(rb0 + r) * nocc;
+    double* out = KB + (size_t)ks * nrow * nocc + (size_t)(rb0 + r) * nocc;
 #pragma unroll
     for (int q = 0; q < 128; ++q) {
         const int i = it * 128 + q;
@@ -435,8 +438,9 @@ cudaError_t l2p_typed(const PanelArgs& a, cudaStream_t s) {
     dim3 gA(a.KC, a.max_rt, a.nleaf), gB(a.KC, a.it, a.nleaf);
     k_panel_l2p_A<P><<<gA, 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, pl, a.lscale, a.panA);
     k_panel_l2p_B<P><<<gB, 128, 0, s>>>(a.Mbox, a.nocc, a.nc, a.leaf_store0, pl, a.lscale, a.panB);
-    dim3 g(a.max_rt, a.it, a.nleaf);
-    k_pgemm_l2p<P><<<g, 192, Q<P>::smem, s>>>(a.leaf_rowoff, a.nocc, pl, a.panA, a.panB, a.KB, a.err);
+    dim3 g(a.max_rt, a.it, a.nleaf * a.nsplit);
+    k_pgemm_l2p<P><<<g, 192, Q<P>::smem, s>>>(a.leaf_rowoff, a.nocc, a.nrow, a.nsplit, pl, a.panA, a.panB, a.KB,
+                                              a.err);
     return cudaGetLastError();
 }
 

@@ -177,7 +177,7 @@ struct FmmArgs {
     void* ct; void* w; void* obox; void* mbox; double* kb; double* part;
     const int* leaf_rowoff_host;     // host copy (max rows)
     int max_rows;
-    int l2p_nsplit;                  // FP32 SIMT step (e): K-range splits (KB holds that many copies)
+    int l2p_nsplit;                  // step (e) K-range splits, FP32 and mixed forms (KB holds that many copies)
     cudaEvent_t* ev;                 // OCCK_NSTAGE+1 events or nullptr
     // tensor-core forms
     const float* lscale;             // [nc] sqrt((l+m)!(l-m)!) / h_leaf^l
@@ -240,6 +240,7 @@ struct PanelArgs {
     const float* lscale;
     int nocc, nrow, nc, leaf_store0;
     int scaled; float inv_h_leaf;          // scaled storage of O and Mcal (see kernels_tc_translate.cu)
+    int nsplit;                            // step (e): K-range splits (KB copies)
     uint8_t* panA; uint8_t* panB;
     int* err;
 };

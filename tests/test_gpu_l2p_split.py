@@ -1,7 +1,6 @@
-"""FP32 step (e) with its K range split over several blocks (Eq. kri summed in
-pieces, each into its own copy of the per-leaf K rows): any split count gives
-the unsplit result to FP32 accuracy, and the automatic choice matches the
-FP64 path."""
+"""Step (e) with its K range split over several blocks (Eq. kri summed in
+pieces, each into its own copy of the per-leaf K rows), in FP32 and on the
+tensor core: any split count matches the FP64 path to the form's accuracy."""
 import numpy as np
 import pytest
 
@@ -13,8 +12,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("fp16x3", 1e-5)])
 @pytest.mark.parametrize("nsplit", [1, 2, 3, 8])
-def test_l2p_split_matches(nsplit):
+def test_l2p_split_matches(nsplit, prec, tol):
     from paper_1708_05353_gb300 import occk
     ctx = occk.Context(0)
     s = inputs.alkane(20, lmax=4, seed_k=4)
@@ -23,7 +23,7 @@ def test_l2p_split_matches(nsplit):
     C = torch.tensor(s.C, dtype=torch.float64, device="cuda:0")
     K64, E64 = occk.farfield_K(ctx, tree, C, prec="fp64", want_energy_host=True)
     ctx.set_l2p_split(nsplit)
-    K, E = occk.farfield_K(ctx, tree, C, prec="fp32", want_energy_host=True)
+    K, E = occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
     ctx.set_l2p_split(0)
-    assert rel_err(K.cpu().numpy(), K64.cpu().numpy()) < 1e-4
-    assert abs(E - E64) <= 1e-5 * abs(E64)
+    assert rel_err(K.cpu().numpy(), K64.cpu().numpy()) < tol
+    assert abs(E - E64) <= tol * abs(E64)
