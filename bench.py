@@ -120,9 +120,19 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def function_source(path, name):
+    """Text of the C++ function `name` in `path`: from its signature line to the
+    first closing brace at column 0."""
+    text = open(path).read()
+    i = text.index(" " + name + "(")
+    i = text.rfind("\n", 0, i) + 1
+    j = text.index("\n}\n", i) + 3
+    return text[i:j]
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source."""
+    was taken on the current source of the kernel's function."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -131,7 +141,8 @@ def traffic_for(kernel):
         if not rec:
             return None
         src = os.path.join(ROOT, "paper_1708_05353_gb300", "csrc", rec["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        body = function_source(src, rec["function"])
+        sha = hashlib.sha256(body.encode()).hexdigest()[:16]
         if sha != rec["source_sha"]:
             return None
         return rec["bytes_per_launch"] * rec.get("scale_to_bench", 1.0)

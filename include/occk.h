@@ -331,13 +331,13 @@ occk_status occk_device_status(occk_ctx* ctx, void* stream);
  * outside -1..7.  No paper counterpart: an implementation choice. */
 occk_status occk_set_translate_engine(occk_ctx* ctx, int mask);
 
-/* K-range splits of step (e) in FP32 and the tensor-core forms: each of
- * nsplit blocks of a tile sums a share of the (lm, j) range into its own copy
- * of the per-leaf K rows, which the K reduction adds up (in a fixed order).
- * nsplit = 0 (default) chooses enough splits for about eight waves of the
- * grid (two SIMT blocks or one tensor-core CTA per SM), at most 8; 1..64
- * forces a count.  FP64 never splits.  OCCK_ERR_ARG outside 0..64.  No paper
- * counterpart: an implementation choice. */
+/* K-range splits of step (e): each of nsplit blocks of a tile sums a share of
+ * the (lm, j) range into its own copy of the per-leaf K rows, which the K
+ * reduction adds up (in a fixed order).  nsplit = 0 (default) chooses enough
+ * splits for about eight waves of the grid (four FP64 or two FP32 SIMT blocks,
+ * or one tensor-core CTA per SM), at most 8; 1..64 forces a count.
+ * OCCK_ERR_ARG outside 0..64.  No paper counterpart: an implementation
+ * choice. */
 occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit);
 
 /* D = A B^T on the tensor-core engine used by the mixed forms, for checking

@@ -346,14 +346,17 @@ __device__ __forceinline__ void l2p_body(int bx, int by, int bz, const int* __re
 }
 
 // FP64 step (e) with a 32-row x 128-column block tile (thread tile 2 x 8):
-// same sum as l2p_body, less padding on leaves with a few dozen AOs.
-__device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int* __restrict__ leaf_rowoff,
+// same sum as l2p_body, less padding on leaves with a few dozen AOs.  Block
+// z = leaf * nsplit + split: the split covers its share of the flattened
+// (lm, j-chunk) range and writes its own copy of KB (summed by the K
+// reduction), so that short grids still fill the GPU.
+__device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit, const int* __restrict__ leaf_rowoff,
                                               const double* __restrict__ W, const double* __restrict__ Mbox,
                                               int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
     constexpr int BR = 32, BI = 128, BK = 8, TR = 2, TI = 8;
     __shared__ double As[BK][BR + 1];
     __shared__ double Bs[BK][BI + 1];
-    const int B = bz;
+    const int B = bz / nsplit, ks = bz % nsplit;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
     const int r0 = bx * BR, i0 = by * BI;
     if (r0 >= nr) return;
@@ -364,31 +367,33 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
     for (int a = 0; a < TR; ++a)
 #pragma unroll
         for (int b = 0; b < TI; ++b) acc[a][b] = 0.0;
-    for (int lm = 0; lm < nc; ++lm) {
+    const int jt = (nocc + BK - 1) / BK, nkt = nc * jt;
+    const int kt0 = (int)((long long)nkt * ks / nsplit), kt1 = (int)((long long)nkt * (ks + 1) / nsplit);
+    for (int kt = kt0; kt < kt1; ++kt) {
+        const int lm = kt / jt, k0 = (kt - lm * jt) * BK;
         int l = 0;
         while ((l + 1) * (l + 1) <= lm) ++l;
         const double w = (lm == l * l) ? 2.0 : (((lm - l * l) & 1) ? 4.0 : -4.0);
         const double* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
         const double* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
-        for (int k0 = 0; k0 < nocc; k0 += BK) {
-            {   // A: 32 rows x 8 columns, one element per thread
-                const int row = threadIdx.x / BK, kk = threadIdx.x % BK;
-                const int r = r0 + row, j = k0 + kk;
-                As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.0;
-            }
-            // B: 128 rows (i) x 8 columns (j) of the symmetric Mcal, read from
-            // the packed upper triangle; thread order follows the stored rows
-            const bool below = k0 + BK <= i0;
-            for (int e = threadIdx.x; e < BK * BI; e += 256) {
-                const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
-                const int i = i0 + row, j = k0 + kk;
-                Bs[kk][row] = (i < nocc && j < nocc)
-                                  ? w * Ml[i <= j ? tri_index(i, j, nocc) : tri_index(j, i, nocc)]
-                                  : 0.0;
-            }
-            __syncthreads();
-            // a warp covers rows r0 + 4w .. r0 + 4w + 3: skip warps past the leaf's rows
-            if (r0 + (threadIdx.x >> 5) * 2 * TR < nr) {
+        {   // A: 32 rows x 8 columns, one element per thread
+            const int row = threadIdx.x / BK, kk = threadIdx.x % BK;
+            const int r = r0 + row, j = k0 + kk;
+            As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.0;
+        }
+        // B: 128 rows (i) x 8 columns (j) of the symmetric Mcal, read from
+        // the packed upper triangle; thread order follows the stored rows
+        const bool below = k0 + BK <= i0;
+        for (int e = threadIdx.x; e < BK * BI; e += 256) {
+            const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
+            const int i = i0 + row, j = k0 + kk;
+            Bs[kk][row] = (i < nocc && j < nocc)
+                              ? w * Ml[i <= j ? tri_index(i, j, nocc) : tri_index(j, i, nocc)]
+                              : 0.0;
+        }
+        __syncthreads();
+        // a warp covers rows r0 + 4w .. r0 + 4w + 3: skip warps past the leaf's rows
+        if (r0 + (threadIdx.x >> 5) * 2 * TR < nr) {
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
                 double a[TR], b[TI];
@@ -401,9 +406,8 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
 #pragma unroll
                     for (int y = 0; y < TI; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
             }
-            }
-            __syncthreads();
         }
+        __syncthreads();
     }
 #pragma unroll
     for (int x = 0; x < TR; ++x) {
@@ -412,7 +416,7 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, const int*
 #pragma unroll
         for (int y = 0; y < TI; ++y) {
             const int i = i0 + tx + 16 * y;
-            if (i < nocc) KB[(size_t)(rb0 + r) * nocc + i] = acc[x][y];
+            if (i < nocc) KB[(size_t)ks * nrow * nocc + (size_t)(rb0 + r) * nocc + i] = acc[x][y];
         }
     }
 }

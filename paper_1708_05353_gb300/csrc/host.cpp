@@ -746,23 +746,23 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     size_t bytes_ct = es * (size_t)t->nao * nocc;
     size_t bytes_w = es * (size_t)nc * nrow * nocc;
     size_t bytes_box = es * nstore * nc * P;
-    // FP32 SIMT step (e): split the (lm, j) range until the grid covers the
-    // GPU about eight times (two 256-thread blocks per SM); each split writes
-    // its own copy of KB, summed by the K reduction.  Measured on GB300
-    // (C150H302 L 2 and 6, (H2O)100 L 4): 1.3-1.6x faster than one split,
-    // including the longer reduction
-    // The tensor-core step (e) (one 128 x 128 tile per CTA, one CTA per SM)
-    // splits its K panels the same way.
+    // Step (e): split the (lm, j) range until the grid covers the GPU about
+    // eight times; each split writes its own copy of KB, summed by the K
+    // reduction.  Tiles and resident blocks per SM: FP64 32 rows x 128 (four
+    // 256-thread blocks), FP32 96 x 128 (two), tensor core 128 x 128 (one
+    // CTA).  Measured on GB300 (C150H302 L 2 and 6, (H2O)100 L 4): FP32
+    // 1.3-1.6x faster than one split, including the longer reduction.
     int l2p_nsplit = 1;
-    if (prec == OCCK_FP32 || occk::tc_mode(prec) >= 0) {
-        const bool tcl = prec != OCCK_FP32;
-        const int rows = tcl ? 128 : 96;
+    {
+        const bool tcl = occk::tc_mode(prec) >= 0;
+        const int rows = tcl ? 128 : (prec == OCCK_FP64 ? 32 : 96);
+        const int bps = tcl ? 1 : (prec == OCCK_FP64 ? 4 : 2);
+        const int bk = tcl ? 128 / occk::panel_elem_bytes(prec) : (prec == OCCK_FP64 ? 8 : 32);
         long long tiles = 0;
         for (int B = 0; B < nleaf; ++B) tiles += (t->leaf_rowoff[B + 1] - t->leaf_rowoff[B] + rows - 1) / rows;
         tiles *= (nocc + 127) / 128;
-        const long long want = 8LL * std::max(ctx->sm_count, 1) * (tcl ? 1 : 2);
-        const int nkt = tcl ? nc * ((nocc + 128 / occk::panel_elem_bytes(prec) - 1) / (128 / occk::panel_elem_bytes(prec)))
-                            : nc * ((nocc + 31) / 32);
+        const long long want = 8LL * std::max(ctx->sm_count, 1) * bps;
+        const int nkt = nc * ((nocc + bk - 1) / bk);
         l2p_nsplit = (int)std::min<long long>((want + tiles - 1) / std::max<long long>(tiles, 1), 8);
         l2p_nsplit = std::max(1, std::min(l2p_nsplit, nkt / 8));
         if (ctx->l2p_split > 0) l2p_nsplit = std::min(ctx->l2p_split, std::max(1, nkt));

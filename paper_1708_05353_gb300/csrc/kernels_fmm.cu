@@ -65,9 +65,10 @@ k_l2p(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const T* __r
 }
 
 __global__ void __launch_bounds__(256)
-k_l2p_r32(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const double* __restrict__ Mbox,
-          int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
-    body::l2p_rect_body(blockIdx.x, blockIdx.y, blockIdx.z, leaf_rowoff, W, Mbox, nocc, nrow, nc, leaf_store0, KB);
+k_l2p_r32(int nsplit, const int* __restrict__ leaf_rowoff, const double* __restrict__ W,
+          const double* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+    body::l2p_rect_body(blockIdx.x, blockIdx.y, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
+                        leaf_store0, KB);
 }
 
 __global__ void __launch_bounds__(256)
@@ -270,9 +271,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     } else if constexpr (sizeof(T) == 8) {
         // 32 AO rows x 128 orbitals per block: leaves hold ~70-600 AOs, and a
         // 64-row tile would spend a third of the DFMA on padding
-        dim3 g((a.max_rows + 31) / 32, (nocc + 127) / 128, a.nleaf);
-        k_l2p_r32<<<g, 256, 0, s>>>(a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow, nc,
-                                    leaf_store0, a.kb);
+        dim3 g((a.max_rows + 31) / 32, (nocc + 127) / 128, a.nleaf * a.l2p_nsplit);
+        k_l2p_r32<<<g, 256, 0, s>>>(a.l2p_nsplit, a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow,
+                                    nc, leaf_store0, a.kb);
     } else {
         const int nsplit = a.l2p_nsplit;
         dim3 g((a.max_rows + 95) / 96, (nocc + 127) / 128, a.nleaf * nsplit);
@@ -281,7 +282,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     mark(6);
     constexpr int kRedBlocks = kFarfieldPartials;
-    const int nsplit = sizeof(T) == 4 ? a.l2p_nsplit : 1;
+    const int nsplit = a.l2p_nsplit;
     k_reduce_K<<<kRedBlocks, 256, 0, s>>>(a.ao_row_ptr, a.ao_rows, a.kb, a.nao, nocc, a.C, a.ldc, a.K,
                                           a.ldk, a.part, nsplit, (size_t)a.nrow * nocc);
     k_final_energy<<<1, 256, 0, s>>>(a.part, kRedBlocks, a.Ex_dev);
