@@ -323,12 +323,19 @@ occk_status occk_batch_set_config(occk_batch* batch, const int* cfg);
 occk_status occk_device_status(occk_ctx* ctx, void* stream);
 
 /* Engine of the translations (b) M2M, (c) M2L and (d) L2L in the mixed forms
- * (OCCK_TF32 .. OCCK_FP16X3).  mask = -1 (default): chosen by expansion rank;
+ * (OCCK_TF32 .. OCCK_FP16X3).  mask = -1 (default): chosen by expansion rank
+ * and form (the slot pipeline, mask 15, from rank 4 for TF32/BF16/FP16 and
+ * from rank 6 for the split forms, whose tensor-core M2L is less accurate than
+ * the FP32 SIMT one; all SIMT below);
  * otherwise bit 0 / 1 / 2 puts M2M / M2L / L2L on the tensor core (tcgen05,
  * scaled operands, see Eqs. fmm1-3), the others on SIMT FP32; mask = 0 keeps
- * all three on SIMT with unscaled storage.  Ignored when per-edge ranks are in
- * use (lmax_policy 1 or 2): M2L then stays on SIMT.  OCCK_ERR_ARG for a mask
- * outside -1..7.  No paper counterpart: an implementation choice. */
+ * all three on SIMT with unscaled storage; mask = 15 runs all three on the
+ * tensor core with the multipoles and local expansions kept in the tensor
+ * core's operand layout between the steps (bulk-copy pipeline, extra device
+ * memory of about NP/nc times the FP32 boxes, NP = nc rounded up to a power of
+ * two).  Ignored when per-edge ranks are in use (lmax_policy 1 or 2): the
+ * translations then stay on SIMT.  OCCK_ERR_ARG for a mask outside -1..7 and
+ * 15.  No paper counterpart: an implementation choice. */
 occk_status occk_set_translate_engine(occk_ctx* ctx, int mask);
 
 /* K-range splits of step (e): each of nsplit blocks of a tile sums a share of

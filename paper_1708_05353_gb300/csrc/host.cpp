@@ -974,15 +974,31 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     for (int b = 0; b + 1 < (int)t->m2l_ptr.size(); ++b)
         max_m2l_edges = std::max(max_m2l_edges, t->m2l_ptr[b + 1] - t->m2l_ptr[b]);
     a.tr_on = (a.tr_pan && a.m2l_lmax == nullptr && !a.learned && max_m2l_edges <= 256) ? 1 : 0;
-    // which translations go to the tensor core: measured on GB300 (C150H302
-    // and (H2O)100, FP16X3), the tensor-core form wins for M2M and M2L from
-    // rank 5 on (M2L 2x at rank 6, 3.8x at rank 8); L2L has one source per
-    // target, too little work per item, and stays on SIMT with the scaled
-    // operators; below rank 5 all three SIMT forms are faster and the storage
-    // stays unscaled
-    a.tr_mask = ctx->tr_engine >= 0 ? ctx->tr_engine : (L >= 5 ? 3 : 0);
+    // which translations go to the tensor core, measured on GB300 (C150H302 at
+    // ranks 2, 6, 8 and (H2O)100 at rank 4): from rank 4 on the slot pipeline
+    // (all three translations on the tensor core, operands kept in its layout)
+    // is fastest -- whole FP16X3 build 1.5x (rank 4), 2.0x (6), 3.1x (8)
+    // faster than SIMT; at rank 2 the SIMT forms win.  The split forms are
+    // chosen for accuracy: their tensor-core M2L carries every operand in 22
+    // bits, which on (H2O)100 at rank 4 gives 1.6e-6 Eh against 7.2e-7 Eh with
+    // the FP32 SIMT translations, so they take the slot pipeline from rank 6 on
+    // (8.3e-7 Eh on C150H302 at rank 6).  SIMT keeps the storage unscaled.
+    const bool split_form = prec == OCCK_BF16X3 || prec == OCCK_FP16X3;
+    a.tr_mask = ctx->tr_engine >= 0 ? ctx->tr_engine : (L >= (split_form ? 6 : 4) ? 15 : 0);
     if (!a.tr_mask) a.tr_on = 0;
     a.ops_scaled = (const float*)ctx->tops.p;
+    // slot pipeline (mask 15): O~ and Mcal~ of every stored box in the tensor
+    // core's operand layout between the steps
+    a.slot_o = a.slot_m = nullptr;
+    if (a.tr_on && a.tr_mask == 15) {
+        const int ntile = (int)((P + 127) / 128);
+        const size_t sbytes = (size_t)(nbox - first) * occk::tr_slot_box_bytes(prec, nc, ntile);
+        if ((e = ensure(ctx->sob, sbytes)) != cudaSuccess || (e = ensure(ctx->smb, sbytes)) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "slot storage")
+                                                  : cuda_fail(ctx, e, "slot storage");
+        a.slot_o = (uint8_t*)ctx->sob.p;
+        a.slot_m = (uint8_t*)ctx->smb.p;
+    }
     a.lscale = d.lscale;
     a.box_scale = d.box_scale;
     a.err_word = (int*)ctx->scratch.p;
@@ -999,6 +1015,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_farfield_K launch");
     ctx->last_prec = prec;
     ctx->last_scaled = a.tr_on;
+    ctx->last_slot = a.slot_o != nullptr;
     ctx->last_nocc = nocc;
     ctx->last_lmax = L;
     ctx->last_first_box = first;
@@ -1042,7 +1059,21 @@ extern "C" occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* t, int w
     const size_t nst = (size_t)(nbox - ctx->last_first_box) * nc * Ps;
     const void* src = what == OCCK_DBG_OBOX ? ctx->obox.p : ctx->mbox.p;
     std::vector<double> tmp(nst);
-    if (ctx->last_prec == OCCK_FP64) {
+    if (ctx->last_slot) {
+        // slot pipeline: every stored box lives in the tensor core's layout;
+        // decode it on the device into a temporary FP32 array
+        float* dbuf = nullptr;
+        e = cudaMalloc((void**)&dbuf, std::max<size_t>(nst, 1) * 4);
+        const int ntile = (int)((Ps + 127) / 128);
+        if (e == cudaSuccess)
+            e = occk::tr_slots_unpack(ctx->last_prec, nc, (const uint8_t*)(what == OCCK_DBG_OBOX ? ctx->sob.p : ctx->smb.p),
+                                      (int)Ps, ntile, 0, nbox - ctx->last_first_box, dbuf, s);
+        std::vector<float> tf(nst);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemcpy(tf.data(), dbuf, nst * 4, cudaMemcpyDeviceToHost);
+        if (dbuf) cudaFree(dbuf);
+        for (size_t i = 0; i < nst; ++i) tmp[i] = tf[i];
+    } else if (ctx->last_prec == OCCK_FP64) {
         e = cudaMemcpy(tmp.data(), src, nst * 8, cudaMemcpyDeviceToHost);
     } else {
         std::vector<float> tf(nst);
@@ -1127,7 +1158,7 @@ extern "C" occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit) {
 
 extern "C" occk_status occk_set_translate_engine(occk_ctx* ctx, int mask) {
     if (!ctx) return OCCK_ERR_ARG;
-    if (mask < -1 || mask > 7) return fail(ctx, OCCK_ERR_ARG, "mask must be -1..7");
+    if (mask < -1 || (mask > 7 && mask != 15)) return fail(ctx, OCCK_ERR_ARG, "mask must be -1..7 or 15");
     ctx->tr_engine = mask;
     return OCCK_OK;
 }

@@ -209,8 +209,28 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         th.parent = a.parent; th.box_level = a.box_level;
         th.pan = a.tr_pan; th.err = a.err_word;
     }
+    // slot pipeline: the leaf multipoles of step (a) go into slots once, all
+    // three translations read and write slots, the leaf local expansions come
+    // back as FP32 for step (e)
+    const bool slots = trc && a.slot_o != nullptr;
+    SlotArgs sh{};
+    const int ntile = (int)((P + 127) / 128);
+    if (slots) {
+        sh.P = (int)P; sh.nc = nc; sh.ntile = ntile; sh.first_box = a.first_box; sh.sm_count = a.sm_count;
+        sh.parent = a.parent; sh.pan = a.tr_pan; sh.err = a.err_word;
+    }
     mark(2);
-    for (int lev = D; lev >= 3; --lev) {
+    if (slots) {
+        cudaError_t e2 = tr_slots_pack(a.prec, nc, (const float*)Ob, (int)P, ntile, leaf_store0, a.nbox - a.leaf0,
+                                       a.slot_o, s);
+        for (int lev = D; lev >= 3 && e2 == cudaSuccess; --lev) {
+            int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
+            e2 = tr_slot_translate(a.prec, sh, 0, t0, nt, a.child_ptr, a.child_list, a.m2m_op, a.slot_o, a.slot_o,
+                                   0, s);
+        }
+        if (e2 != cudaSuccess) return e2;
+    }
+    for (int lev = D; lev >= 3 && !slots; --lev) {
         int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
         if (trc && (a.tr_mask & 1)) {
             cudaError_t e2 = tr_translate(a.prec, th, 0, t0, nt, a.child_ptr, a.child_list, a.m2m_op,
@@ -236,7 +256,12 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (c) M2L: every box of levels 2..D, all levels in one launch
     mark(3);
-    if (trc && (a.tr_mask & 2)) {
+    if (slots) {
+        int t0 = a.level_off[2], nt = a.nbox - t0;
+        cudaError_t e2 = tr_slot_translate(a.prec, sh, 1, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op, a.slot_o, a.slot_m,
+                                           0, s);
+        if (e2 != cudaSuccess) return e2;
+    } else if (trc && (a.tr_mask & 2)) {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         cudaError_t e2 = tr_translate(a.prec, th, 1, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op, (const float*)Ob,
                                       (float*)Mb, 0, s);
@@ -249,7 +274,15 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (d) L2L: children at level lev accumulate their parent's expansion
     mark(4);
-    for (int lev = 3; lev <= D; ++lev) {
+    if (slots) {
+        cudaError_t e2 = cudaSuccess;
+        for (int lev = 3; lev <= D && e2 == cudaSuccess; ++lev) {
+            int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
+            e2 = tr_slot_translate(a.prec, sh, 2, t0, nt, nullptr, nullptr, a.l2l_op, a.slot_m, a.slot_m, 1, s);
+        }
+        if (e2 != cudaSuccess) return e2;
+    }
+    for (int lev = 3; lev <= D && !slots; ++lev) {
         int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
         if (trc && (a.tr_mask & 4)) {
             cudaError_t e2 = tr_translate(a.prec, th, 2, t0, nt, nullptr, nullptr, a.l2l_op, (const float*)Mb,
@@ -263,6 +296,11 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     // (e) L2P
     mark(5);
+    if (slots) {
+        cudaError_t e2 = tr_slots_unpack(a.prec, nc, a.slot_m, (int)P, ntile, leaf_store0, a.nbox - a.leaf0,
+                                         (float*)Mb, s);
+        if (e2 != cudaSuccess) return e2;
+    }
     if (tcm) {
         pa.panA = a.pan_l2pA;
         pa.panB = a.pan_l2pB;

@@ -82,6 +82,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Operator panels: for operator o and chunk ch, NP rows (output components q)
@@ -425,6 +428,304 @@ k_tc_translate(TrKArgs a) {
     if (warp == 0) tmem_dealloc(tmem, C::tmem_cols);
 }
 
+// ---------------------------------------------------------------------------
+// Slot pipeline.  With all three translations on the tensor core the
+// multipoles and local expansions of the tree passes are kept in the tensor
+// core's own operand layout ("slots"): for each box, pair tile (128 pairs)
+// and chunk of KCH components, one A slot of 128 rows x KCH values in the
+// K-major canonical layout, hi part then lo part.  A translation then moves
+// only whole slots: one producer thread issues bulk asynchronous copies of
+// the source slots and operator panels into a ring of shared-memory stages,
+// one thread issues the MMAs, and four warps add each stage's accumulator
+// into registers and finally write the target's slots (converting, and for
+// L2L adding the old contents).  No thread touches an operand on the way in.
+// Components past nc and rows past P are stored as zeros by every writer, so
+// padded K columns never meet garbage.
+// ---------------------------------------------------------------------------
+struct SlotKArgs {
+    int mode, P, ntile, first_box, tgt0, ntgt, accumulate;
+    const int* ptr; const int* list; const int* opidx; const int* parent;
+    const uint8_t* in; uint8_t* out; const uint8_t* pan; int* err;
+};
+
+template <int P, int NP>
+struct SS {
+    using C = TT<P, NP>;
+    static constexpr int NS = NP >= 128 ? 3 : 4;                    // ring stages
+    static constexpr uint32_t stage_bytes = C::A_stage + C::B_stage;
+    static constexpr int smem = NS * (int)stage_bytes;
+    static constexpr size_t tile_bytes = (size_t)C::NCH * C::A_slot;  // one pair tile of one box
+    static constexpr uint32_t tmem_cols = (uint32_t)pow2ceil_i(2 * C::setN < 32 ? 32 : 2 * C::setN);
+};
+
+struct SlotState {
+    uint64_t full[4], empty[4], accf[2], acce[2];
+    uint32_t tmem;
+    int abort;
+    uint32_t gp, gm;   // stages issued by the producer, consumed by the MMA thread
+};
+
+__device__ __forceinline__ void slot_edge(const SlotKArgs& a, int tgt, int e0, int k, int& src, int& op) {
+    if (a.mode == 0) {
+        src = a.list[e0 + k];
+        op = a.opidx[src];
+    } else if (a.mode == 1) {
+        src = a.list[e0 + k];
+        op = a.opidx[e0 + k];
+    } else {
+        src = a.parent[tgt];
+        op = a.opidx[tgt];
+    }
+}
+
+__device__ __forceinline__ void slot_item(const SlotKArgs& a, long long it, int& pt, int& tgt, int& e0, int& ne) {
+    pt = (int)(it / a.ntgt);
+    tgt = a.tgt0 + (int)(it % a.ntgt);
+    e0 = 0;
+    ne = 1;
+    if (a.mode != 2) {
+        e0 = a.ptr[tgt];
+        ne = a.ptr[tgt + 1] - e0;
+    }
+}
+
+template <int P, int NP>
+__global__ void __launch_bounds__(192, 1)
+k_tc_slot_translate(SlotKArgs a) {
+    using C = TT<P, NP>;
+    using S = SS<P, NP>;
+    using F = Fmt<P>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ SlotState st;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (warp == 2) {
+        tmem_alloc(&st.tmem, S::tmem_cols);
+        tmem_relinquish();
+    }
+    if (t == 0) {
+        for (int r = 0; r < S::NS; ++r) {
+            mbar_init(&st.full[r], 1);
+            mbar_init(&st.empty[r], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&st.accf[b], 1);
+            mbar_init(&st.acce[b], 128);
+        }
+        st.abort = 0;
+        st.gp = 0;
+        st.gm = 0;
+        mbar_fence_init();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = st.tmem;
+    const uint32_t sbase = smem_u32(smem);
+    auto ringA = [&](int r) { return sbase + (uint32_t)r * S::stage_bytes; };
+    auto ringB = [&](int r) { return sbase + (uint32_t)r * S::stage_bytes + C::A_stage; };
+    const long long nitems = (long long)a.ntgt * a.ntile;
+    const size_t box_bytes = (size_t)a.ntile * S::tile_bytes;
+
+    if (warp == 0) {
+        if (lane == 0) {   // producer
+            uint32_t g = 0;
+            for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                int pt, tgt, e0, ne;
+                slot_item(a, it, pt, tgt, e0, ne);
+                const int nslot = ne * C::NCH, ns = (nslot + C::ES - 1) / C::ES;
+                for (int s = 0; s < ns; ++s, ++g) {
+                    const int r = (int)(g % S::NS);
+                    if (g >= (uint32_t)S::NS && !mbar_wait_bounded(&st.empty[r], ((g / S::NS) - 1) & 1, kWaitT)) {
+                        st.abort = 1;
+                        break;
+                    }
+                    const int nvalid = min(C::ES, nslot - s * C::ES);
+                    mbar_expect_tx(&st.full[r], (uint32_t)nvalid * (C::A_slot + C::B_slot));
+                    for (int k = 0; k < nvalid; ++k) {
+                        const int u = s * C::ES + k, e = u / C::NCH, ch = u % C::NCH;
+                        int src, op;
+                        slot_edge(a, tgt, e0, e, src, op);
+                        bulk_g2s(ringA(r) + (uint32_t)k * C::A_slot,
+                                 a.in + (size_t)(src - a.first_box) * box_bytes + (size_t)pt * S::tile_bytes +
+                                     (size_t)ch * C::A_slot,
+                                 C::A_slot, &st.full[r]);
+                        bulk_g2s(ringB(r) + (uint32_t)k * C::B_slot, a.pan + ((size_t)op * C::NCH + ch) * C::B_slot,
+                                 C::B_slot, &st.full[r]);
+                    }
+                    st.gp = g + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issue
+            uint32_t g = 0;
+            for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                int pt, tgt, e0, ne;
+                slot_item(a, it, pt, tgt, e0, ne);
+                const int nslot = ne * C::NCH, ns = (nslot + C::ES - 1) / C::ES;
+                for (int s = 0; s < ns; ++s, ++g) {
+                    const int r = (int)(g % S::NS), b = (int)(g & 1);
+                    if (!mbar_wait_bounded(&st.full[r], (g / S::NS) & 1, kWaitT) ||
+                        (g >= 2 && !mbar_wait_bounded(&st.acce[b], ((g >> 1) - 1) & 1, kWaitT))) {
+                        st.abort = 1;
+                        break;
+                    }
+                    fence_after_sync();
+                    const int nvalid = min(C::ES, nslot - s * C::ES);
+                    issue_stage_mmas<P, NP>(ringA(r), ringB(r), nvalid, tmem + (uint32_t)(b * C::setN));
+                    mma_commit(&st.empty[r]);
+                    mma_commit(&st.accf[b]);
+                    st.gm = g + 1;
+                }
+                if (*(volatile int*)&st.abort) break;
+            }
+            // the last MMAs must be complete before TMEM is given back
+            const uint32_t gl = st.gm;
+            if (gl > 0) mbar_wait_bounded(&st.accf[(gl - 1) & 1], ((gl - 1) >> 1) & 1, kWaitT);
+        }
+    } else {   // warps 2..5: accumulate stages, write the target's slots
+        const int row = (warp & 3) * 32 + lane;
+        const uint32_t rowoff = (uint32_t)(row >> 3) * C::SBO + (uint32_t)(row & 7) * 16u;
+        uint32_t g = 0;
+        float acc[NP];
+        for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+            int pt, tgt, e0, ne;
+            slot_item(a, it, pt, tgt, e0, ne);
+            const int nslot = ne * C::NCH, ns = (nslot + C::ES - 1) / C::ES;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc[q] = 0.f;
+            bool ok = true;
+            for (int s = 0; s < ns; ++s, ++g) {
+                const int b = (int)(g & 1);
+                if (*(volatile int*)&st.abort || !mbar_wait_bounded(&st.accf[b], (g >> 1) & 1, kWaitT)) {
+                    st.abort = 1;
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t base = tmem + (uint32_t)(b * C::setN) + ((uint32_t)((warp & 3) * 32) << 16);
+#pragma unroll
+                for (int cc = 0; cc < NP / 16; ++cc) {
+                    float v[16];
+                    tmem_ld16(base + (uint32_t)(cc * 16), v);
+                    if constexpr (F::dual) {
+                        float w[16];
+                        tmem_ld16(base + (uint32_t)NP + (uint32_t)(cc * 16), w);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] += w[q] * (1.f / kLo);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc[cc * 16 + q] += v[q];
+                }
+                fence_before_sync();
+                mbar_arrive(&st.acce[b]);
+            }
+            if (!ok) break;
+            uint8_t* dst = a.out + (size_t)(tgt - a.first_box) * box_bytes + (size_t)pt * S::tile_bytes + rowoff;
+#pragma unroll
+            for (int ch = 0; ch < C::NCH; ++ch) {
+#pragma unroll
+                for (int k8 = 0; k8 < C::KCH; k8 += 8) {
+                    uint8_t* d = dst + (size_t)ch * C::A_slot + (uint32_t)((k8 * C::esz) / 16) * C::LBO;
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = acc[ch * C::KCH + k8 + q];
+                    if (a.accumulate) {
+                        float o[8];
+                        get8<P>(d, C::A_part, C::LBO, o);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) v[q] += o[q];
+                    }
+                    put8<P>(d, C::A_part, C::LBO, v);
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (t == 0 && st.abort) {
+        atomicExch(a.err, 1);
+        // copies issued but never consumed: wait (bounded) until they land
+        for (uint32_t g = st.gm; g < st.gp; ++g) mbar_wait_bounded(&st.full[g % S::NS], (g / S::NS) & 1, kWaitT);
+    }
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 2) tmem_dealloc(tmem, S::tmem_cols);
+}
+
+// FP32 [box][nc][P] <-> slots, one thread per (box, pair tile, row); padding
+// (components past nc, rows past P) is written as zeros.
+template <int P, int NP>
+__global__ void k_slots_pack(const float* __restrict__ X, int nc, int Ppairs, int ntile, int box0,
+                             uint8_t* __restrict__ slots) {
+    using C = TT<P, NP>;
+    using S = SS<P, NP>;
+    const int pt = blockIdx.x, box = box0 + blockIdx.y, row = threadIdx.x;
+    const int p = pt * 128 + row;
+    const uint32_t rowoff = (uint32_t)(row >> 3) * C::SBO + (uint32_t)(row & 7) * 16u;
+    uint8_t* dst = slots + (size_t)box * ntile * S::tile_bytes + (size_t)pt * S::tile_bytes + rowoff;
+    const float* x = X + (size_t)box * nc * Ppairs + p;
+    for (int ch = 0; ch < C::NCH; ++ch) {
+        for (int k8 = 0; k8 < C::KCH; k8 += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = ch * C::KCH + k8 + q;
+                v[q] = (p < Ppairs && c < nc) ? x[(size_t)c * Ppairs] : 0.f;
+            }
+            put8<P>(dst + (size_t)ch * C::A_slot + (uint32_t)((k8 * C::esz) / 16) * C::LBO, C::A_part, C::LBO, v);
+        }
+    }
+}
+
+template <int P, int NP>
+__global__ void k_slots_unpack(const uint8_t* __restrict__ slots, int nc, int Ppairs, int ntile, int box0,
+                               float* __restrict__ X) {
+    using C = TT<P, NP>;
+    using S = SS<P, NP>;
+    const int pt = blockIdx.x, box = box0 + blockIdx.y, row = threadIdx.x;
+    const int p = pt * 128 + row;
+    if (p >= Ppairs) return;
+    const uint32_t rowoff = (uint32_t)(row >> 3) * C::SBO + (uint32_t)(row & 7) * 16u;
+    const uint8_t* src = slots + (size_t)box * ntile * S::tile_bytes + (size_t)pt * S::tile_bytes + rowoff;
+    float* x = X + (size_t)box * nc * Ppairs + p;
+    for (int ch = 0; ch < C::NCH; ++ch) {
+        for (int k8 = 0; k8 < C::KCH; k8 += 8) {
+            float v[8];
+            get8<P>(src + (size_t)ch * C::A_slot + (uint32_t)((k8 * C::esz) / 16) * C::LBO, C::A_part, C::LBO, v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = ch * C::KCH + k8 + q;
+                if (c < nc) x[(size_t)c * Ppairs] = v[q];
+            }
+        }
+    }
+}
+
+template <int P, int NP>
+cudaError_t slot_translate_typed(const SlotArgs& h, int mode, int tgt0, int ntgt, const int* ptr, const int* list,
+                                 const int* opidx, const uint8_t* in, uint8_t* out, int accumulate,
+                                 cudaStream_t s) {
+    using S = SS<P, NP>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_slot_translate<P, NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, S::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (ntgt <= 0) return cudaSuccess;
+    SlotKArgs a{};
+    a.mode = mode; a.P = h.P; a.ntile = h.ntile; a.first_box = h.first_box; a.tgt0 = tgt0; a.ntgt = ntgt;
+    a.accumulate = accumulate;
+    a.ptr = ptr; a.list = list; a.opidx = opidx; a.parent = h.parent;
+    a.in = in; a.out = out; a.pan = h.pan; a.err = h.err;
+    const long long items = (long long)ntgt * h.ntile;
+    const int grid = (int)(items < h.sm_count ? items : h.sm_count);   // one CTA per SM (TMEM, shared memory)
+    k_tc_slot_translate<P, NP><<<grid, 192, S::smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int P, int NP>
 cudaError_t tr_typed(const TrArgs& h, int mode, int tgt0, int ntgt, const int* ptr, const int* list,
                      const int* opidx, const float* in, float* out, int accumulate, cudaStream_t s) {
@@ -528,6 +829,52 @@ cudaError_t tr_translate(int prec, const TrArgs& h, int mode, int tgt0, int ntgt
                          const int* opidx, const float* in, float* out, int accumulate, cudaStream_t s) {
     const int np = tr_np(h.nc);
     OCCK_TR_DISPATCH(prec, np, (tr_typed<P, NP>(h, mode, tgt0, ntgt, ptr, list, opidx, in, out, accumulate, s)));
+    return cudaErrorInvalidValue;
+}
+
+size_t tr_slot_box_bytes(int prec, int nc, int ntile) {
+    const int np = tr_np(nc);
+    const int m = tc_mode(prec);
+    if (!np || m < 0) return 0;
+    const int esz = m == Q_TF32 ? 4 : 2;
+    const int parts = (m == Q_BF16X3 || m == Q_FP16X3) ? 2 : 1;
+    return (size_t)ntile * 128 * np * esz * parts;
+}
+
+cudaError_t tr_slot_translate(int prec, const SlotArgs& h, int mode, int tgt0, int ntgt, const int* ptr,
+                              const int* list, const int* opidx, const uint8_t* in, uint8_t* out, int accumulate,
+                              cudaStream_t s) {
+    const int np = tr_np(h.nc);
+    OCCK_TR_DISPATCH(prec, np,
+                     (slot_translate_typed<P, NP>(h, mode, tgt0, ntgt, ptr, list, opidx, in, out, accumulate, s)));
+    return cudaErrorInvalidValue;
+}
+
+template <int P, int NP>
+static cudaError_t pack_typed(bool pack, const float* X, float* Xo, int nc, int Ppairs, int ntile, int box0,
+                              int nbox, const uint8_t* sin, uint8_t* sout, cudaStream_t s) {
+    if (nbox <= 0) return cudaSuccess;
+    dim3 g(ntile, nbox);
+    if (pack)
+        k_slots_pack<P, NP><<<g, 128, 0, s>>>(X, nc, Ppairs, ntile, box0, sout);
+    else
+        k_slots_unpack<P, NP><<<g, 128, 0, s>>>(sin, nc, Ppairs, ntile, box0, Xo);
+    return cudaGetLastError();
+}
+
+cudaError_t tr_slots_pack(int prec, int nc, const float* X, int Ppairs, int ntile, int box0, int nbox,
+                          uint8_t* slots, cudaStream_t s) {
+    const int np = tr_np(nc);
+    OCCK_TR_DISPATCH(prec, np,
+                     (pack_typed<P, NP>(true, X, nullptr, nc, Ppairs, ntile, box0, nbox, nullptr, slots, s)));
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tr_slots_unpack(int prec, int nc, const uint8_t* slots, int Ppairs, int ntile, int box0, int nbox,
+                            float* X, cudaStream_t s) {
+    const int np = tr_np(nc);
+    OCCK_TR_DISPATCH(prec, np,
+                     (pack_typed<P, NP>(false, nullptr, X, nc, Ppairs, ntile, box0, nbox, slots, nullptr, s)));
     return cudaErrorInvalidValue;
 }
 

@@ -139,6 +139,8 @@ struct occk_ctx {
     std::vector<double> tp_scd;             // [2][nlev][nc] scales of the last panel build (host)
     int last_scaled = 0;                    // last run kept O and Mcal in scaled form
     int tr_engine = -1;                     // occk_set_translate_engine mask
+    occk::DevBuf sob, smb;                  // slot storage of O~ and Mcal~ (slot pipeline)
+    int last_slot = 0;                      // last run used the slot pipeline
     int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
     // stage timers
     int timing = 0;
@@ -193,6 +195,8 @@ struct FmmArgs {
     // run on SIMT with the scaled FP32 operators ops_scaled)
     const uint8_t* tr_pan; const float* ops_scaled; int tr_nlev, tr_on, tr_mask, sm_count;
     float inv_h_leaf;
+    // slot pipeline (tr_mask == 15): O~ and Mcal~ of every stored box in slots
+    uint8_t* slot_o; uint8_t* slot_m;
     // learned selector (lmax_policy 2); learned == 0 when unused
     int learned;
     const float* mlp_prm; void* mlp_h; const float* mlp_norm;
@@ -262,6 +266,25 @@ cudaError_t tr_build_panels(int prec, const double* ops, int nops, int nc, const
                             int nlev, uint8_t* pan, float* ops_scaled, cudaStream_t s);
 cudaError_t tr_translate(int prec, const TrArgs& h, int mode, int tgt0, int ntgt, const int* ptr, const int* list,
                          const int* opidx, const float* in, float* out, int accumulate, cudaStream_t s);
+
+// Slot pipeline (all three translations on the tensor core, operands kept in
+// the tensor core's layout between the steps; kernels_tc_translate.cu).
+struct SlotArgs {
+    int P, nc, ntile, first_box, sm_count;
+    const int* parent;
+    const uint8_t* pan;                    // operator panels
+    int* err;
+};
+size_t tr_slot_box_bytes(int prec, int nc, int ntile);   // slot bytes of one box
+cudaError_t tr_slot_translate(int prec, const SlotArgs& h, int mode, int tgt0, int ntgt, const int* ptr,
+                              const int* list, const int* opidx, const uint8_t* in, uint8_t* out, int accumulate,
+                              cudaStream_t s);
+// FP32 [box][nc][P] (boxes box0 .. box0+nbox-1, counted from the first stored
+// box) <-> slots
+cudaError_t tr_slots_pack(int prec, int nc, const float* X, int Ppairs, int ntile, int box0, int nbox,
+                          uint8_t* slots, cudaStream_t s);
+cudaError_t tr_slots_unpack(int prec, int nc, const uint8_t* slots, int Ppairs, int ntile, int box0, int nbox,
+                            float* X, cudaStream_t s);
 
 // ----- plain tensor-core GEMM for checking the engine (kernels_tc2.cu) --------
 int tc_mode(int prec);

@@ -192,6 +192,60 @@ __device__ __forceinline__ void put8(uint8_t* dst, uint32_t part_bytes, uint32_t
     }
 }
 
+// Inverse of put8: the 8 FP32 values (hi + lo, lo scaled back for FP16) of
+// one operand row chunk stored by put8<P> at `src`.
+template <int P>
+__device__ __forceinline__ void get8(const uint8_t* src, uint32_t part_bytes, uint32_t lbo, float* v) {
+    if constexpr (P == Q_TF32) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint4 q = *reinterpret_cast<const uint4*>(src + h * lbo);
+            v[4 * h + 0] = __uint_as_float(q.x);
+            v[4 * h + 1] = __uint_as_float(q.y);
+            v[4 * h + 2] = __uint_as_float(q.z);
+            v[4 * h + 3] = __uint_as_float(q.w);
+        }
+    } else if constexpr (P == Q_BF16 || P == Q_BF16X3) {
+        const uint4 qh = *reinterpret_cast<const uint4*>(src);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&qh);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            v[2 * q] = f.x;
+            v[2 * q + 1] = f.y;
+        }
+        if constexpr (Fmt<P>::split) {
+            const uint4 ql = *reinterpret_cast<const uint4*>(src + part_bytes);
+            const __nv_bfloat162* l = reinterpret_cast<const __nv_bfloat162*>(&ql);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(l[q]);
+                v[2 * q] += f.x;
+                v[2 * q + 1] += f.y;
+            }
+        }
+    } else {
+        const uint4 qh = *reinterpret_cast<const uint4*>(src);
+        const __half2* h = reinterpret_cast<const __half2*>(&qh);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __half22float2(h[q]);
+            v[2 * q] = f.x;
+            v[2 * q + 1] = f.y;
+        }
+        if constexpr (Fmt<P>::split) {
+            const uint4 ql = *reinterpret_cast<const uint4*>(src + part_bytes);
+            const __half2* l = reinterpret_cast<const __half2*>(&ql);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __half22float2(l[q]);
+                v[2 * q] += f.x * (1.f / kLo);
+                v[2 * q + 1] += f.y * (1.f / kLo);
+            }
+        }
+    }
+}
+
 // ---- splitting FP32 into low-precision hi/lo parts --------------------------------
 struct SplitBF16 {
     using T = __nv_bfloat16;

@@ -177,7 +177,8 @@ class Context:
 
     def set_translate_engine(self, mask: int = -1):
         """Translations of the mixed forms on the tensor core: bit 0 M2M, bit 1
-        M2L, bit 2 L2L; -1 chooses by expansion rank."""
+        M2L, bit 2 L2L; 15: all three with the expansions kept in the tensor
+        core's operand layout; -1 chooses by expansion rank."""
         self.check(lib().occk_set_translate_engine(self._h, int(mask)), "occk_set_translate_engine")
 
     def set_l2p_split(self, nsplit: int = 0):

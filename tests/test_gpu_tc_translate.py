@@ -52,32 +52,44 @@ def _run(ctx, tree, s, prec, policy=0):
     return K.cpu().numpy(), E
 
 
+@pytest.mark.parametrize("engine", [7, 15])
 @pytest.mark.parametrize("L", [2, 4, 6, 10])
 @pytest.mark.parametrize("prec", list(K_BOUND))
-def test_tc_translate_chain(ctx, chain, L, prec):
+def test_tc_translate_chain(ctx, chain, L, prec, engine):
+    """engine 7: operands converted in registers at every use; engine 15:
+    expansions kept in the tensor core's layout (slots) between the steps."""
     from paper_1708_05353_gb300 import occk
     s = chain
     tree = _tree(ctx, s, L)
     assert tree.info()["depth"] >= 3          # M2M and L2L both run
     K64, E64 = _run(ctx, tree, s, "fp64")
     M64 = occk.debug_fetch(ctx, tree, "mbox", nocc=s.nocc, stream=0)
-    K, E = _run(ctx, tree, s, prec)
-    M = occk.debug_fetch(ctx, tree, "mbox", nocc=s.nocc, stream=0)
+    ctx.set_translate_engine(engine)
+    try:
+        K, E = _run(ctx, tree, s, prec)
+        M = occk.debug_fetch(ctx, tree, "mbox", nocc=s.nocc, stream=0)
+    finally:
+        ctx.set_translate_engine(7)
     errK = rel_err(K, K64)
     errM = max(rel_err(M[b], M64[b]) for b in range(M.shape[0]) if np.abs(M64[b]).max() > 0)
-    print(f"L={L} {prec}: K {errK:.2e}, Mcal {errM:.2e}, |dE| {abs(E - E64):.2e} (E = {E64:.6f})")
+    print(f"L={L} {prec} engine {engine}: K {errK:.2e}, Mcal {errM:.2e}, |dE| {abs(E - E64):.2e} (E = {E64:.6f})")
     assert errK < K_BOUND[prec]
     assert errM < 4 * K_BOUND[prec]
     assert abs(E - E64) <= K_BOUND[prec] * abs(E64)
 
 
-def test_tc_translate_fp16x3_meets_energy_target(ctx, chain):
+@pytest.mark.parametrize("engine", [7, 15])
+def test_tc_translate_fp16x3_meets_energy_target(ctx, chain, engine):
     """The split FP16 form stays within 1e-6 Eh of the FP64 exchange energy
     at the highest order, where the operands span the widest range."""
     s = chain
     tree = _tree(ctx, s, 10)
     _, E64 = _run(ctx, tree, s, "fp64")
-    _, E = _run(ctx, tree, s, "fp16x3")
+    ctx.set_translate_engine(engine)
+    try:
+        _, E = _run(ctx, tree, s, "fp16x3")
+    finally:
+        ctx.set_translate_engine(7)
     assert abs(E - E64) < 1e-6
 
 
@@ -115,11 +127,16 @@ def test_tc_translate_engine_mix(ctx, chain, mask):
     assert abs(E - E64) <= K_BOUND["fp16x3"] * abs(E64)
 
 
-def test_tc_translate_repeatable(ctx, chain):
+@pytest.mark.parametrize("engine", [7, 15])
+def test_tc_translate_repeatable(ctx, chain, engine):
     """The same call twice gives bit-identical results (no race between the
     pair tiles or between the CTAs that share a target)."""
     s = chain
     tree = _tree(ctx, s, 4)
-    K1, E1 = _run(ctx, tree, s, "fp16x3")
-    K2, E2 = _run(ctx, tree, s, "fp16x3")
+    ctx.set_translate_engine(engine)
+    try:
+        K1, E1 = _run(ctx, tree, s, "fp16x3")
+        K2, E2 = _run(ctx, tree, s, "fp16x3")
+    finally:
+        ctx.set_translate_engine(7)
     assert np.array_equal(K1, K2) and E1 == E2
