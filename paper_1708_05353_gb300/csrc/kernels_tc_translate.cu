@@ -436,9 +436,10 @@ k_tc_translate(TrKArgs a) {
 // K-major canonical layout, hi part then lo part.  A translation then moves
 // only whole slots: one producer thread issues bulk asynchronous copies of
 // the source slots and operator panels into a ring of shared-memory stages,
-// one thread issues the MMAs, and four warps add each stage's accumulator
-// into registers and finally write the target's slots (converting, and for
-// L2L adding the old contents).  No thread touches an operand on the way in.
+// one thread issues the MMAs, and eight warps (two per TMEM lane quarter,
+// each owning half of the output columns) add each stage's accumulator into
+// registers and finally write the target's slots (converting, and for L2L
+// adding the old contents).  No thread touches an operand on the way in.
 // Components past nc and rows past P are stored as zeros by every writer, so
 // padded K columns never meet garbage.
 // ---------------------------------------------------------------------------
@@ -489,8 +490,10 @@ __device__ __forceinline__ void slot_item(const SlotKArgs& a, long long it, int&
     }
 }
 
+constexpr int kSlotThreads = 320;   // producer warp, MMA warp, 8 epilogue warps
+
 template <int P, int NP>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kSlotThreads, 1)
 k_tc_slot_translate(SlotKArgs a) {
     using C = TT<P, NP>;
     using S = SS<P, NP>;
@@ -509,7 +512,7 @@ k_tc_slot_translate(SlotKArgs a) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&st.accf[b], 1);
-            mbar_init(&st.acce[b], 128);
+            mbar_init(&st.acce[b], kSlotThreads - 64);
         }
         st.abort = 0;
         st.gp = 0;
@@ -583,17 +586,22 @@ k_tc_slot_translate(SlotKArgs a) {
             const uint32_t gl = st.gm;
             if (gl > 0) mbar_wait_bounded(&st.accf[(gl - 1) & 1], ((gl - 1) >> 1) & 1, kWaitT);
         }
-    } else {   // warps 2..5: accumulate stages, write the target's slots
-        const int row = (warp & 3) * 32 + lane;
+    } else {   // warps 2..9: accumulate stages, write the target's slots
+        // TMEM lane quarter of this warp (warp w may read lanes 32 (w % 4)..),
+        // and which half of the output columns it owns (N >= 32)
+        const int row = (warp & 3) * 32 + lane, half = (warp - 2) >> 2;
+        constexpr int NPH = NP >= 32 ? NP / 2 : NP;
+        const bool has_cols = half < NP / NPH;
+        const int col0 = half * NPH;
         const uint32_t rowoff = (uint32_t)(row >> 3) * C::SBO + (uint32_t)(row & 7) * 16u;
         uint32_t g = 0;
-        float acc[NP];
+        float acc[NPH];
         for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
             int pt, tgt, e0, ne;
             slot_item(a, it, pt, tgt, e0, ne);
             const int nslot = ne * C::NCH, ns = (nslot + C::ES - 1) / C::ES;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) acc[q] = 0.f;
+            for (int q = 0; q < NPH; ++q) acc[q] = 0.f;
             bool ok = true;
             for (int s = 0; s < ns; ++s, ++g) {
                 const int b = (int)(g & 1);
@@ -603,42 +611,44 @@ k_tc_slot_translate(SlotKArgs a) {
                     break;
                 }
                 fence_after_sync();
-                const uint32_t base = tmem + (uint32_t)(b * C::setN) + ((uint32_t)((warp & 3) * 32) << 16);
+                if (has_cols) {
+                    const uint32_t base =
+                        tmem + (uint32_t)(b * C::setN + col0) + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
-                for (int cc = 0; cc < NP / 16; ++cc) {
-                    float v[16];
-                    tmem_ld16(base + (uint32_t)(cc * 16), v);
-                    if constexpr (F::dual) {
-                        float w[16];
-                        tmem_ld16(base + (uint32_t)NP + (uint32_t)(cc * 16), w);
+                    for (int cc = 0; cc < NPH / 16; ++cc) {
+                        float v[16];
+                        tmem_ld16(base + (uint32_t)(cc * 16), v);
+                        if constexpr (F::dual) {
+                            float w[16];
+                            tmem_ld16(base + (uint32_t)NP + (uint32_t)(cc * 16), w);
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) v[q] += w[q] * (1.f / kLo);
+                            for (int q = 0; q < 16; ++q) v[q] += w[q] * (1.f / kLo);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) acc[cc * 16 + q] += v[q];
                     }
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) acc[cc * 16 + q] += v[q];
                 }
                 fence_before_sync();
                 mbar_arrive(&st.acce[b]);
             }
             if (!ok) break;
+            if (!has_cols) continue;
             uint8_t* dst = a.out + (size_t)(tgt - a.first_box) * box_bytes + (size_t)pt * S::tile_bytes + rowoff;
+            auto chunk = [&](int k8) {   // 8 columns col0 + k8 .. : never straddle a K chunk
+                const int c = col0 + k8, ch = c / C::KCH, cc = c % C::KCH;
+                return dst + (size_t)ch * C::A_slot + (uint32_t)((cc * C::esz) / 16) * C::LBO;
+            };
+            if (a.accumulate) {   // every old value is read before the first store
 #pragma unroll
-            for (int ch = 0; ch < C::NCH; ++ch) {
+                for (int k8 = 0; k8 < NPH; k8 += 8) {
+                    float o[8];
+                    get8<P>(chunk(k8), C::A_part, C::LBO, o);
 #pragma unroll
-                for (int k8 = 0; k8 < C::KCH; k8 += 8) {
-                    uint8_t* d = dst + (size_t)ch * C::A_slot + (uint32_t)((k8 * C::esz) / 16) * C::LBO;
-                    float v[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = acc[ch * C::KCH + k8 + q];
-                    if (a.accumulate) {
-                        float o[8];
-                        get8<P>(d, C::A_part, C::LBO, o);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) v[q] += o[q];
-                    }
-                    put8<P>(d, C::A_part, C::LBO, v);
+                    for (int q = 0; q < 8; ++q) acc[k8 + q] += o[q];
                 }
             }
+#pragma unroll
+            for (int k8 = 0; k8 < NPH; k8 += 8) put8<P>(chunk(k8), C::A_part, C::LBO, acc + k8);
         }
     }
     fence_before_sync();
@@ -722,7 +732,7 @@ cudaError_t slot_translate_typed(const SlotArgs& h, int mode, int tgt0, int ntgt
     a.in = in; a.out = out; a.pan = h.pan; a.err = h.err;
     const long long items = (long long)ntgt * h.ntile;
     const int grid = (int)(items < h.sm_count ? items : h.sm_count);   // one CTA per SM (TMEM, shared memory)
-    k_tc_slot_translate<P, NP><<<grid, 192, S::smem, s>>>(a);
+    k_tc_slot_translate<P, NP><<<grid, kSlotThreads, S::smem, s>>>(a);
     return cudaGetLastError();
 }
 
