@@ -175,6 +175,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         pa.nocc = nocc; pa.nrow = a.nrow; pa.nc = nc; pa.leaf_store0 = leaf_store0;
         pa.scaled = a.tr_on; pa.inv_h_leaf = a.inv_h_leaf;
         pa.nsplit = a.l2p_nsplit;
+        pa.sm_count = a.sm_count;
         pa.err = a.err_word;
         pa.panA = a.pan_a2A;
         pa.panB = a.pan_a2B;

@@ -20,6 +20,7 @@
 //   (a) O[B][lm][i <= j] = (1 / s_lm) sum_r C_ri (W[lm][r][j] s_lm)
 // with s_lm = sqrt((l+m)!(l-m)!) / h^l at the leaf level, which brings every
 // component to O(1) for the 16-bit formats.
+#include <algorithm>
 #include <cstdio>
 
 #include "occk_internal.h"
@@ -317,6 +318,209 @@ __device__ __forceinline__ bool pgemm_tile(const uint8_t* Apanels, const uint8_t
     return ok;
 }
 
+// Persistent form of the panel GEMM: one CTA per SM walks a list of output
+// tiles (it = blockIdx.x, + gridDim.x, ...); the stage ring, its mbarrier
+// phases and the two TMEM accumulators carry on across tiles, so a tile with
+// a short K (a leaf of a few dozen AOs) costs no set-up of its own.
+// src(it, A, B, nk) gives a tile's panels; epi(it, row, acc) stores a row.
+struct PPState {
+    uint64_t full[4], empty[4], accf[2], acce[2];
+    uint32_t tmem;
+    int abort;
+    uint32_t gp, gm;   // stages issued by the producer, consumed by the MMA thread
+};
+
+template <int P, typename Src, typename Epi>
+__device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi epi, int* err_word) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ PPState st;
+    constexpr int S = Q<P>::stages;
+    constexpr uint32_t kBuf = Q<P>::dual ? 256u : 128u;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (warp == 2) {
+        tmem_alloc(&st.tmem, 2 * kBuf);
+        tmem_relinquish();
+    }
+    if (t == 0) {
+        for (int r = 0; r < S; ++r) {
+            mbar_init(&st.full[r], 1);
+            mbar_init(&st.empty[r], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&st.accf[b], 1);
+            mbar_init(&st.acce[b], 128);
+        }
+        st.abort = 0;
+        st.gp = 0;
+        st.gm = 0;
+        mbar_fence_init();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = st.tmem;
+    const uint32_t sbase = smem_u32(smem);
+    auto stageA = [&](int r) { return sbase + (uint32_t)(2 * r) * Q<P>::pbytes; };
+    auto stageB = [&](int r) { return sbase + (uint32_t)(2 * r + 1) * Q<P>::pbytes; };
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                const uint8_t *A, *B;
+                int nk;
+                src(it, A, B, nk);
+                for (int kc = 0; kc < nk; ++kc, ++g) {
+                    const int r = (int)(g % S);
+                    if (g >= (uint32_t)S && !mbar_wait_bounded(&st.empty[r], ((g / S) - 1) & 1, kWait)) {
+                        st.abort = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&st.full[r], 2u * Q<P>::pbytes);
+                    bulk_g2s(stageA(r), A + (size_t)kc * Q<P>::pbytes, Q<P>::pbytes, &st.full[r]);
+                    bulk_g2s(stageB(r), B + (size_t)kc * Q<P>::pbytes, Q<P>::pbytes, &st.full[r]);
+                    st.gp = g + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(128, 128, Q<P>::fmt);
+            uint32_t g = 0;
+            for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                const uint8_t *A, *B;
+                int nk;
+                src(it, A, B, nk);
+                for (int kc = 0; kc < nk; ++kc, ++g) {
+                    const int r = (int)(g % S), b = (int)(g & 1);
+                    if (!mbar_wait_bounded(&st.full[r], (g / S) & 1, kWait) ||
+                        (g >= 2 && !mbar_wait_bounded(&st.acce[b], ((g >> 1) - 1) & 1, kWait))) {
+                        st.abort = 1;
+                        break;
+                    }
+                    fence_after_sync();
+                    issue_panel_mmas<P>(stageA(r), stageB(r), tmem + (uint32_t)b * kBuf, idesc);
+                    mma_commit(&st.empty[r]);
+                    mma_commit(&st.accf[b]);
+                    st.gm = g + 1;
+                }
+            }
+            const uint32_t gl = st.gm;   // the last MMAs finish before TMEM is given back
+            if (gl > 0) mbar_wait_bounded(&st.accf[(gl - 1) & 1], ((gl - 1) >> 1) & 1, kWait);
+        }
+    } else {
+        const int q4 = warp & 3;   // TMEM lane quarter of this warp
+        uint32_t g = 0;
+        float acc[128];
+        for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const uint8_t *A, *B;
+            int nk;
+            src(it, A, B, nk);
+#pragma unroll
+            for (int q = 0; q < 128; ++q) acc[q] = 0.f;
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc, ++g) {
+                const int b = (int)(g & 1);
+                if (*(volatile int*)&st.abort || !mbar_wait_bounded(&st.accf[b], (g >> 1) & 1, kWait)) {
+                    st.abort = 1;
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t base = tmem + (uint32_t)b * kBuf + ((uint32_t)(q4 * 32) << 16);
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    float v[16];
+                    tmem_ld16(base + (uint32_t)(cc * 16), v);
+                    if constexpr (Q<P>::dual) {
+                        float w[16];
+                        tmem_ld16(base + 128u + (uint32_t)(cc * 16), w);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] += w[q] * (1.f / kLo);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc[cc * 16 + q] += v[q];
+                }
+                fence_before_sync();
+                mbar_arrive(&st.acce[b]);
+            }
+            if (!ok) break;
+            epi(it, q4 * 32 + lane, acc);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (t == 0 && st.abort) {
+        atomicExch(err_word, 1);
+        // copies issued but never consumed: wait (bounded) until they land
+        for (uint32_t g = st.gm; g < st.gp; ++g) mbar_wait_bounded(&st.full[g % S], (g / S) & 1, kWait);
+    }
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 2) tmem_dealloc(tmem, 2 * kBuf);
+}
+
+// Step (a), persistent: tiles ordered (triangular tile fastest, then lm,
+// then leaf), so concurrently running CTAs share panels in L2.  Dynamic shared
+// memory: the stage ring plus four 32 x 33 FP32 staging tiles.
+template <int P>
+constexpr int kA2pSmem = Q<P>::smem + 4 * 32 * 33 * 4;
+
+template <int P>
+__global__ void __launch_bounds__(192, 1)
+k_pgemm_a2p(int nocc, int nc, int ntile, int leaf_store0, int nleaf, Plan pl, const uint8_t* __restrict__ Apan,
+            const uint8_t* __restrict__ Bpan, const float* __restrict__ lscale, float* __restrict__ Obox, int* err) {
+    const int ntt = ntile * (ntile + 1) / 2;
+    const long long nitems = (long long)ntt * nleaf * nc;
+    const size_t P2 = (size_t)nocc * (nocc + 1) / 2;
+    auto decode = [&](long long it, int& ti, int& tj, int& B, int& lm) {
+        int tt = (int)(it % ntt);
+        const long long rest = it / ntt;
+        lm = (int)(rest % nc);
+        B = (int)(rest / nc);
+        ti = 0;
+        while (tt >= ntile - ti) {
+            tt -= ntile - ti;
+            ++ti;
+        }
+        tj = ti + tt;
+    };
+    auto src = [&](long long it, const uint8_t*& A, const uint8_t*& Bp, int& nk) {
+        int ti, tj, B, lm;
+        decode(it, ti, tj, B, lm);
+        const int kca = pl.kca[B];
+        A = Apan + (size_t)(pl.offAa[B] + (long long)ti * kca) * Q<P>::pbytes;
+        Bp = Bpan + (size_t)(pl.offBa[B] + ((long long)lm * pl.it + tj) * kca) * Q<P>::pbytes;
+        nk = kca;
+    };
+    // Epilogue through a per-warp 32 x 32 staging tile: a thread holds one
+    // row of the output tile, but packed rows are contiguous in j, so each
+    // warp writes its 32 rows 32 columns at a time, one row per store
+    // instruction (128 contiguous bytes) instead of 32 rows per instruction.
+    auto epi = [&](long long it, int row, const float* acc) {
+        extern __shared__ __align__(1024) uint8_t smem[];
+        int ti, tj, B, lm;
+        decode(it, ti, tj, B, lm);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        float* tile = reinterpret_cast<float*>(smem + Q<P>::smem) + (warp - 2) * 32 * 33;
+        float* O = Obox + ((size_t)(leaf_store0 + B) * nc + lm) * P2;
+        const float inv = pl.scaled ? 1.f : 1.f / lscale[lm];   // scaled storage keeps O~ = O s_lm
+        const int r0 = ti * 128 + (row & ~31);                  // first row of this warp
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) tile[lane * 33 + q] = acc[cc * 32 + q] * inv;
+            __syncwarp();
+            const int j = tj * 128 + cc * 32 + lane;
+            for (int r = 0; r < 32; ++r) {
+                const int i = r0 + r;
+                if (i < nocc && j < nocc && j >= i) O[tri_ix(i, i, nocc) - (size_t)i + (size_t)j] = tile[r * 33 + lane];
+            }
+            __syncwarp();
+        }
+    };
+    pgemm_persistent<P>(nitems, src, epi, err);
+}
+
 // blockIdx.z = leaf * nsplit + split: a split runs its share of the K panels
 // and writes its own copy of KB (the K reduction adds the copies)
 template <int P>
@@ -332,48 +536,25 @@ k_pgemm_l2p(const int* __restrict__ leaf_rowoff, int nocc, int nrow, int nsplit,
 #pragma unroll
     for (int q = 0; q < 128; ++q) acc[q] = 0.f;
     const bool ok = pgemm_tile<P>(A, Bp, kc1 - kc0, acc, err);
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (!ok || warp < 2) return;
+    // the stage ring is idle now: each flush warp transposes its 32 rows
+    // through a 32 x 33 tile so that a store instruction writes 32 consecutive
+    // K entries of one row
+    extern __shared__ __align__(1024) uint8_t smem[];
+    float* tile = reinterpret_cast<float*>(smem) + (warp - 2) * 32 * 33;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
-    const int r = rt * 128 + (warp & 3) * 32 + (threadIdx.x & 31);
-    if (r >= nr) return;
-    double* out = KB + (size_t)ks * nrow * nocc + (size_t)(rb0 + r) * nocc;
+    const int r0 = rt * 128 + (warp & 3) * 32;
+    double* out = KB + (size_t)ks * nrow * nocc + (size_t)rb0 * nocc;
 #pragma unroll
-    for (int q = 0; q < 128; ++q) {
-        const int i = it * 128 + q;
-        if (i < nocc) out[i] = (double)acc[q];
-    }
-}
-
-template <int P>
-__global__ void __launch_bounds__(192, 1)
-k_pgemm_a2(int nocc, int nc, int ntile, int leaf_store0, Plan pl, const uint8_t* __restrict__ Apan,
-           const uint8_t* __restrict__ Bpan, const float* __restrict__ lscale, float* __restrict__ Obox, int* err) {
-    const int B = blockIdx.y / nc, lm = blockIdx.y % nc;
-    int tt = blockIdx.x, ti = 0;
-    while (tt >= ntile - ti) {
-        tt -= ntile - ti;
-        ++ti;
-    }
-    const int tj = ti + tt;
-    const int kca = pl.kca[B];
-    const uint8_t* A = Apan + (size_t)(pl.offAa[B] + (long long)ti * kca) * Q<P>::pbytes;
-    const uint8_t* Bp = Bpan + (size_t)(pl.offBa[B] + ((long long)lm * pl.it + tj) * kca) * Q<P>::pbytes;
-    float acc[128];
+    for (int cc = 0; cc < 4; ++cc) {
 #pragma unroll
-    for (int q = 0; q < 128; ++q) acc[q] = 0.f;
-    const bool ok = pgemm_tile<P>(A, Bp, kca, acc, err);
-    const int warp = threadIdx.x >> 5;
-    if (!ok || warp < 2) return;
-    const int i = ti * 128 + (warp & 3) * 32 + (threadIdx.x & 31);
-    if (i >= nocc) return;
-    const size_t P2 = (size_t)nocc * (nocc + 1) / 2;
-    float* O = Obox + ((size_t)(leaf_store0 + B) * nc + lm) * P2;
-    const float inv = pl.scaled ? 1.f : 1.f / lscale[lm];   // scaled storage keeps O~ = O s_lm
-#pragma unroll
-    for (int q = 0; q < 128; ++q) {
-        const int j = tj * 128 + q;
-        if (j < nocc && j >= i) O[tri_ix(i, j, nocc)] = acc[q] * inv;
+        for (int q = 0; q < 32; ++q) tile[lane * 33 + q] = acc[cc * 32 + q];
+        __syncwarp();
+        const int i = it * 128 + cc * 32 + lane;
+        for (int r = 0; r < 32; ++r)
+            if (r0 + r < nr && i < nocc) out[(size_t)(r0 + r) * nocc + i] = (double)tile[r * 33 + lane];
+        __syncwarp();
     }
 }
 
@@ -423,7 +604,7 @@ cudaError_t attrs() {
     if (done) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_pgemm_l2p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q<P>::smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pgemm_a2<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q<P>::smem);
+        e = cudaFuncSetAttribute(k_pgemm_a2p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kA2pSmem<P>);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pgemm_plain<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q<P>::smem);
     if (e == cudaSuccess) done = true;
@@ -452,9 +633,10 @@ cudaError_t a2_typed(const PanelArgs& a, cudaStream_t s) {
     dim3 gA(a.max_kca, a.it, a.nleaf), gB(a.max_kca, a.it * a.nc, a.nleaf);
     k_panel_a2_A<P><<<gA, 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, a.Ct, a.nocc, pl, a.panA);
     k_panel_a2_B<P><<<gB, 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, a.nc, pl, a.lscale, a.panB);
-    dim3 g(a.it * (a.it + 1) / 2, a.nleaf * a.nc);
-    k_pgemm_a2<P><<<g, 192, Q<P>::smem, s>>>(a.nocc, a.nc, a.it, a.leaf_store0, pl, a.panA, a.panB, a.lscale,
-                                             a.Obox, a.err);
+    const long long items = (long long)(a.it * (a.it + 1) / 2) * a.nleaf * a.nc;
+    const int grid = (int)std::min<long long>(items, std::max(a.sm_count, 1));
+    k_pgemm_a2p<P><<<grid, 192, kA2pSmem<P>, s>>>(a.nocc, a.nc, a.it, a.leaf_store0, a.nleaf, pl, a.panA, a.panB,
+                                                 a.lscale, a.Obox, a.err);
     return cudaGetLastError();
 }
 

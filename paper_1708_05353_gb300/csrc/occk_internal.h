@@ -245,6 +245,7 @@ struct PanelArgs {
     int nocc, nrow, nc, leaf_store0;
     int scaled; float inv_h_leaf;          // scaled storage of O and Mcal (see kernels_tc_translate.cu)
     int nsplit;                            // step (e): K-range splits (KB copies)
+    int sm_count;                          // persistent grids
     uint8_t* panA; uint8_t* panB;
     int* err;
 };
