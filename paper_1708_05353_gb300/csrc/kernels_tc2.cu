@@ -322,7 +322,9 @@ __device__ __forceinline__ bool pgemm_tile(const uint8_t* Apanels, const uint8_t
 // tiles (it = blockIdx.x, + gridDim.x, ...); the stage ring, its mbarrier
 // phases and the two TMEM accumulators carry on across tiles, so a tile with
 // a short K (a leaf of a few dozen AOs) costs no set-up of its own.
-// src(it, A, B, nk) gives a tile's panels; epi(it, row, acc) stores a row.
+// src(it, A, B, nk) gives a tile's panels; epi(it, row, col0, acc) stores
+// columns col0 .. col0 + 128/(NF/4) - 1 of a row.  NF epilogue warps (4 or 8:
+// with 8, two per TMEM lane quarter, each owning half of the columns).
 struct PPState {
     uint64_t full[4], empty[4], accf[2], acce[2];
     uint32_t tmem;
@@ -330,8 +332,9 @@ struct PPState {
     uint32_t gp, gm;   // stages issued by the producer, consumed by the MMA thread
 };
 
-template <int P, typename Src, typename Epi>
+template <int P, int NF, typename Src, typename Epi>
 __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi epi, int* err_word) {
+    constexpr int NCOL = 128 / (NF / 4);   // output columns per epilogue thread
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ PPState st;
     constexpr int S = Q<P>::stages;
@@ -348,7 +351,7 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&st.accf[b], 1);
-            mbar_init(&st.acce[b], 128);
+            mbar_init(&st.acce[b], 32 * NF);
         }
         st.abort = 0;
         st.gp = 0;
@@ -408,15 +411,16 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
             if (gl > 0) mbar_wait_bounded(&st.accf[(gl - 1) & 1], ((gl - 1) >> 1) & 1, kWait);
         }
     } else {
-        const int q4 = warp & 3;   // TMEM lane quarter of this warp
+        const int q4 = warp & 3;                      // TMEM lane quarter of this warp
+        const int col0 = ((warp - 2) >> 2) * NCOL;    // its share of the columns
         uint32_t g = 0;
-        float acc[128];
+        float acc[NCOL];
         for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
             const uint8_t *A, *B;
             int nk;
             src(it, A, B, nk);
 #pragma unroll
-            for (int q = 0; q < 128; ++q) acc[q] = 0.f;
+            for (int q = 0; q < NCOL; ++q) acc[q] = 0.f;
             bool ok = true;
             for (int kc = 0; kc < nk; ++kc, ++g) {
                 const int b = (int)(g & 1);
@@ -426,9 +430,9 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
                     break;
                 }
                 fence_after_sync();
-                const uint32_t base = tmem + (uint32_t)b * kBuf + ((uint32_t)(q4 * 32) << 16);
+                const uint32_t base = tmem + (uint32_t)b * kBuf + (uint32_t)col0 + ((uint32_t)(q4 * 32) << 16);
 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
+                for (int cc = 0; cc < NCOL / 16; ++cc) {
                     float v[16];
                     tmem_ld16(base + (uint32_t)(cc * 16), v);
                     if constexpr (Q<P>::dual) {
@@ -444,7 +448,7 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
                 mbar_arrive(&st.acce[b]);
             }
             if (!ok) break;
-            epi(it, q4 * 32 + lane, acc);
+            epi(it, q4 * 32 + lane, col0, acc);
         }
     }
     fence_before_sync();
@@ -460,13 +464,15 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
 }
 
 // Step (a), persistent: tiles ordered (triangular tile fastest, then lm,
-// then leaf), so concurrently running CTAs share panels in L2.  Dynamic shared
-// memory: the stage ring plus four 32 x 33 FP32 staging tiles.
+// then leaf), so concurrently running CTAs share panels in L2.  Eight
+// epilogue warps; dynamic shared memory: the stage ring plus eight 32 x 33
+// FP32 staging tiles.
+constexpr int kA2pThreads = 64 + 8 * 32;
 template <int P>
-constexpr int kA2pSmem = Q<P>::smem + 4 * 32 * 33 * 4;
+constexpr int kA2pSmem = Q<P>::smem + 8 * 32 * 33 * 4;
 
 template <int P>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kA2pThreads, 1)
 k_pgemm_a2p(int nocc, int nc, int ntile, int leaf_store0, int nleaf, Plan pl, const uint8_t* __restrict__ Apan,
             const uint8_t* __restrict__ Bpan, const float* __restrict__ lscale, float* __restrict__ Obox, int* err) {
     const int ntt = ntile * (ntile + 1) / 2;
@@ -496,7 +502,7 @@ k_pgemm_a2p(int nocc, int nc, int ntile, int leaf_store0, int nleaf, Plan pl, co
     // row of the output tile, but packed rows are contiguous in j, so each
     // warp writes its 32 rows 32 columns at a time, one row per store
     // instruction (128 contiguous bytes) instead of 32 rows per instruction.
-    auto epi = [&](long long it, int row, const float* acc) {
+    auto epi = [&](long long it, int row, int col0, const float* acc) {
         extern __shared__ __align__(1024) uint8_t smem[];
         int ti, tj, B, lm;
         decode(it, ti, tj, B, lm);
@@ -506,11 +512,11 @@ k_pgemm_a2p(int nocc, int nc, int ntile, int leaf_store0, int nleaf, Plan pl, co
         const float inv = pl.scaled ? 1.f : 1.f / lscale[lm];   // scaled storage keeps O~ = O s_lm
         const int r0 = ti * 128 + (row & ~31);                  // first row of this warp
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
+        for (int cc = 0; cc < 2; ++cc) {
 #pragma unroll
             for (int q = 0; q < 32; ++q) tile[lane * 33 + q] = acc[cc * 32 + q] * inv;
             __syncwarp();
-            const int j = tj * 128 + cc * 32 + lane;
+            const int j = tj * 128 + col0 + cc * 32 + lane;
             for (int r = 0; r < 32; ++r) {
                 const int i = r0 + r;
                 if (i < nocc && j < nocc && j >= i) O[tri_ix(i, i, nocc) - (size_t)i + (size_t)j] = tile[r * 33 + lane];
@@ -518,7 +524,7 @@ k_pgemm_a2p(int nocc, int nc, int ntile, int leaf_store0, int nleaf, Plan pl, co
             __syncwarp();
         }
     };
-    pgemm_persistent<P>(nitems, src, epi, err);
+    pgemm_persistent<P, 8>(nitems, src, epi, err);
 }
 
 // blockIdx.z = leaf * nsplit + split: a split runs its share of the K panels
@@ -635,7 +641,7 @@ cudaError_t a2_typed(const PanelArgs& a, cudaStream_t s) {
     k_panel_a2_B<P><<<gB, 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, a.nc, pl, a.lscale, a.panB);
     const long long items = (long long)(a.it * (a.it + 1) / 2) * a.nleaf * a.nc;
     const int grid = (int)std::min<long long>(items, std::max(a.sm_count, 1));
-    k_pgemm_a2p<P><<<grid, 192, kA2pSmem<P>, s>>>(a.nocc, a.nc, a.it, a.leaf_store0, a.nleaf, pl, a.panA, a.panB,
+    k_pgemm_a2p<P><<<grid, kA2pThreads, kA2pSmem<P>, s>>>(a.nocc, a.nc, a.it, a.leaf_store0, a.nleaf, pl, a.panA, a.panB,
                                                  a.lscale, a.Obox, a.err);
     return cudaGetLastError();
 }
