@@ -46,24 +46,54 @@ template <typename T, int LMC>
 __device__ __forceinline__ void half_body(int bx, int by, int bz, const int* __restrict__ row_ptr, const int* __restrict__ ent_col,
                        const int* __restrict__ ent_val, const T* __restrict__ vals, int nc,
                        const T* __restrict__ Ct, int nocc, int nrow, T* __restrict__ W) {
+    // One block per (AO row, chunk of LMC components).  The row's pair values
+    // and partner AOs are staged in shared memory (CH entries at a time); in
+    // FP32 each thread accumulates JPT = 4 orbitals j, so every shared value
+    // feeds 4 FMAs (FP64 is DFMA-bound and keeps one orbital per thread).
+    constexpr int JPT = sizeof(T) == 4 ? 4 : 1, CH = 64;
+    __shared__ T sv[CH][LMC];
+    __shared__ int scol[CH];
     const int row = bx;
     const int c0 = by * LMC;
     const int e0 = row_ptr[row], e1 = row_ptr[row + 1];
     const int ncl = min(LMC, nc - c0);
-    for (int j = threadIdx.x; j < nocc; j += blockDim.x) {
-        T acc[LMC];
+    const int nth = blockDim.x;
+    for (int jb = 0; jb < nocc; jb += nth * JPT) {
+        T acc[JPT][LMC];
 #pragma unroll
-        for (int q = 0; q < LMC; ++q) acc[q] = T(0);
-        for (int e = e0; e < e1; ++e) {
-            const T cs = Ct[(size_t)ent_col[e] * nocc + j];
-            const T* v = vals + (size_t)ent_val[e] * nc + c0;
+        for (int u = 0; u < JPT; ++u)
 #pragma unroll
-            for (int q = 0; q < LMC; ++q)
-                if (q < ncl) acc[q] += v[q] * cs;
+            for (int q = 0; q < LMC; ++q) acc[u][q] = T(0);
+        for (int ec = e0; ec < e1; ec += CH) {
+            const int n = min(CH, e1 - ec);
+            __syncthreads();
+            for (int x = threadIdx.x; x < n * LMC; x += nth) {
+                const int k = x / LMC, q = x - k * LMC;
+                sv[k][q] = q < ncl ? vals[(size_t)ent_val[ec + k] * nc + c0 + q] : T(0);
+            }
+            for (int x = threadIdx.x; x < n; x += nth) scol[x] = ent_col[ec + x];
+            __syncthreads();
+            for (int k = 0; k < n; ++k) {
+                const T* crow = Ct + (size_t)scol[k] * nocc + jb + threadIdx.x;
+                T cs[JPT];
+#pragma unroll
+                for (int u = 0; u < JPT; ++u) cs[u] = jb + threadIdx.x + u * nth < nocc ? crow[u * nth] : T(0);
+#pragma unroll
+                for (int q = 0; q < LMC; ++q) {
+                    const T w = sv[k][q];
+#pragma unroll
+                    for (int u = 0; u < JPT; ++u) acc[u][q] += w * cs[u];
+                }
+            }
         }
 #pragma unroll
-        for (int q = 0; q < LMC; ++q)
-            if (q < ncl) W[((size_t)(c0 + q) * nrow + row) * nocc + j] = acc[q];
+        for (int u = 0; u < JPT; ++u) {
+            const int jj = jb + threadIdx.x + u * nth;
+            if (jj >= nocc) continue;
+#pragma unroll
+            for (int q = 0; q < LMC; ++q)
+                if (q < ncl) W[((size_t)(c0 + q) * nrow + row) * nocc + jj] = acc[u][q];
+        }
     }
 }
 
