@@ -19,5 +19,7 @@ Modules
   fmm     occ-FMM-K: MO transforms (Eq. motrans), occupied M2M/M2L/L2L, K^ff_ri
           (Eq. kri) and the exchange energy
   brute   brute-force far-field exchange from exact ERIs
+  fmm_j   far-field Coulomb matrix J^ff_rs by the FMM (Sec. II, Eq. fmmc and
+          the J^ff formula) and its exact far-box counterpart
   mlp     reference forward/backward/Adam of the lmax-selector MLP
 """
