@@ -468,6 +468,25 @@ def main():
                        "stage_ms": {k: round(v, 4) for k, v in vst.items()}}
         result["variants"] = var
         result["variants_reference"] = "errors against the FP64 GPU path of the same run (E = %.10f Eh)" % E64
+    # ---- far-field Coulomb matrix on the same tree and rank (FP64), density
+    # D = 2 C C^T made outside the timed region
+    Dm = occk.fortran(2.0 * C @ C.t())
+    J = occk.empty_fortran(system.basis.nao, system.basis.nao, torch.float64, dev)
+    Ej = torch.empty((), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        occk.farfield_J(ctx, tree, Dm, J=J, Ej=Ej)
+    jev = []
+    for k in range(max(3, args.steps)):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        occk.farfield_J(ctx, tree, Dm, J=J, Ej=Ej)
+        b.record(stream)
+        jev.append((a, b))
+    torch.cuda.synchronize()
+    result["coulomb_j"] = {"ms": round(sum(a.elapsed_time(b) for a, b in jev) / len(jev), 4),
+                           "E_J": float(Ej.item()), "lmax": L, "dtype": "f64",
+                           "what": "far-field J^ff and E_J on the same tree, D = 2 C C^T"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(system, L, args.cpu_cols)
     if rank == 0:

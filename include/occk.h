@@ -322,6 +322,22 @@ occk_status occk_batch_set_config(occk_batch* batch, const int* cfg);
  * a tensor-core kernel gave up (its results are then invalid), else OK. */
 occk_status occk_device_status(occk_ctx* ctx, void* stream);
 
+/* The far-field Coulomb matrix (paper, Sec. II: the density-contracted box
+ * multipoles, Eq. fmmc, and J^ff_rs = sum_lm O^{rs,X}_lm Mcal_lm(X)), in FP64,
+ * on the same tree, pair multipoles and operators as the exchange:
+ *   D_dev  [nao x nao] column-major FP64 device density matrix (symmetric,
+ *          for closed shells 2 C C^T), leading dimension ldd >= nao
+ *   J_dev  [nao x nao] column-major FP64 device output, ldj >= nao: J^ff on
+ *          every kept AO pair (both orders), zero elsewhere (near-field and
+ *          screened pairs are outside this far field)
+ *   Ej_dev FP64 device scalar output (nullable): E_J^ff = 1/2 sum_rs D_rs J_rs
+ *   Ej_host FP64 host output (nullable); when non-null the call synchronises
+ *          `stream`
+ * Requires occk_pair_multipoles on this tree (its rank is used).  Workspaces
+ * are owned by the context.  OCCK_ERR_SHAPE if ldd or ldj < nao. */
+occk_status occk_farfield_J(occk_ctx* ctx, const occk_tree* tree, const double* D_dev, int ldd, double* J_dev,
+                            int ldj, double* Ej_dev, double* Ej_host, void* stream);
+
 /* Engine of the translations (b) M2M, (c) M2L and (d) L2L in the mixed forms
  * (OCCK_TF32 .. OCCK_FP16X3).  mask = -1 (default): chosen by expansion rank
  * and form (the slot pipeline, mask 15, from rank 4 for TF32/BF16/FP16 and

@@ -1031,6 +1031,53 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     return OCCK_OK;
 }
 
+extern "C" occk_status occk_farfield_J(occk_ctx* ctx, const occk_tree* tc, const double* D_dev, int ldd,
+                                       double* J_dev, int ldj, double* Ej_dev, double* Ej_host, void* stream) {
+    if (!ctx || !tc) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    occk_tree* t = const_cast<occk_tree*>(tc);
+    if (ctx->device < 0 || t->device != ctx->device)
+        return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device bound to this context or tree");
+    if (t->lmax < 0) return fail(ctx, OCCK_ERR_STATE, "call occk_pair_multipoles first");
+    if (!D_dev || !J_dev) return fail(ctx, OCCK_ERR_ARG, "null D or J");
+    if (ldd < t->nao || ldj < t->nao) return fail(ctx, OCCK_ERR_SHAPE, "ldd/ldj < nao");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    const int L = t->lmax, nc = occk::ncomp(L), D = t->depth;
+    const int nbox = (int)t->parent.size();
+    const int first = D >= 2 ? t->level_off[2] : nbox;
+    const int nleaf = (int)t->leaf_rowoff.size() - 1;
+    const size_t nstore = (size_t)(nbox - first);
+    if ((e = ensure(ctx->jbox, 8 * (2 * nstore * nc + nleaf + 1) + 64)) != cudaSuccess ||
+        (e = ensure(ctx->edev, 8)) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "far-field J workspaces")
+                                              : cuda_fail(ctx, e, "far-field J workspaces");
+    auto& d = t->dev;
+    occk::JArgs a{};
+    a.nao = t->nao; a.nc = nc; a.L = L; a.depth = D; a.nbox = nbox; a.first_box = first; a.nleaf = nleaf;
+    a.leaf0 = t->level_off[D];
+    a.level_off = t->level_off.data();
+    a.leaf_rowoff = d.leaf_rowoff; a.leaf_aos = d.leaf_aos; a.row_ptr = d.row_ptr; a.ent_col = d.ent_col;
+    a.ent_val = d.ent_val;
+    a.child_ptr = d.child_ptr; a.child_list = d.child_list; a.m2m_op = d.m2m_op; a.l2l_op = d.l2l_op;
+    a.parent = d.parent; a.m2l_ptr = d.m2l_ptr; a.m2l_src = d.m2l_src; a.m2l_op = d.m2l_op;
+    a.vals = d.pair_vals; a.ops = d.ops;
+    a.D = D_dev; a.ldd = ldd; a.J = J_dev; a.ldj = ldj;
+    a.Ej_dev = Ej_dev ? Ej_dev : (double*)ctx->edev.p;
+    double* jb = (double*)ctx->jbox.p;
+    a.ob = jb;
+    a.mb = jb + nstore * nc;
+    a.part = jb + 2 * nstore * nc;
+    e = occk::run_farfield_J(a, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_farfield_J launch");
+    if (Ej_host) {
+        e = cudaMemcpyAsync(Ej_host, a.Ej_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "energy copy");
+    }
+    return OCCK_OK;
+}
+
 extern "C" occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* t, int what, void* out,
                                         size_t bytes, void* stream) {
     if (!ctx || !t || !out) return fail(ctx, OCCK_ERR_ARG, "null argument");

@@ -329,7 +329,133 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Far-field Coulomb matrix (Sec. II, Eq. fmmc and the J^ff formula), FP64:
+// density multipoles of the leaves, the tree passes on one density channel
+// (k_translate with one "pair"), then J^ff on every kept AO pair.
+// ---------------------------------------------------------------------------
+
+// q[leaf][lm] = sum over the leaf's ordered entries (r, s) of D_rs O^{rs}_lm
+// (both orderings of a pair are entries, as in the half transform).
+__global__ void __launch_bounds__(256)
+k_j_density(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const int* __restrict__ row_ptr,
+            const int* __restrict__ ent_col, const int* __restrict__ ent_val, const double* __restrict__ vals, int nc,
+            const double* __restrict__ D, int ldd, double* __restrict__ q) {
+    const int B = blockIdx.x, lm = blockIdx.y;
+    const int r0 = leaf_rowoff[B], r1 = leaf_rowoff[B + 1];
+    double acc = 0.0;
+    for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+        const int r = leaf_aos[row];
+        for (int e = row_ptr[row]; e < row_ptr[row + 1]; ++e)
+            acc += D[(size_t)ent_col[e] * ldd + r] * vals[(size_t)ent_val[e] * nc + lm];
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) q[(size_t)B * nc + lm] = red[0];
+}
+
+// J^ff_rs = sum_lm w_lm O^{rs}_lm Mcal_lm(X) on the leaf's entries (real form:
+// w = 1 for m = 0, 2 for Re m > 0, -2 for Im m > 0), and the leaf's part of
+// E_J = 1/2 sum_rs D_rs J_rs.
+__global__ void __launch_bounds__(256)
+k_j_l2p(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const int* __restrict__ row_ptr,
+        const int* __restrict__ ent_col, const int* __restrict__ ent_val, const double* __restrict__ vals, int nc,
+        const double* __restrict__ Mleaf, const double* __restrict__ D, int ldd, double* __restrict__ J, int ldj,
+        double* __restrict__ part) {
+    const int B = blockIdx.x;
+    __shared__ double wm[body::kNcMax];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= c) ++l;
+        const double w = c == l * l ? 1.0 : (((c - l * l) & 1) ? 2.0 : -2.0);
+        wm[c] = w * Mleaf[(size_t)B * nc + c];
+    }
+    __syncthreads();
+    const int r0 = leaf_rowoff[B], r1 = leaf_rowoff[B + 1];
+    double e_acc = 0.0;
+    for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+        const int r = leaf_aos[row];
+        for (int e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
+            const int sidx = ent_col[e];
+            const double* v = vals + (size_t)ent_val[e] * nc;
+            double j = 0.0;
+            for (int c = 0; c < nc; ++c) j += v[c] * wm[c];
+            J[(size_t)sidx * ldj + r] = j;
+            e_acc += D[(size_t)sidx * ldd + r] * j;
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = e_acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[B] = red[0];
+}
+
+__global__ void k_zero_square(double* M, int ld, int n) {
+    const long long tot = (long long)n * n;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < tot; x += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(x / n), r = (int)(x - (long long)c * n);
+        M[(size_t)c * ld + r] = 0.0;
+    }
+}
+
+__global__ void k_j_energy(const double* __restrict__ part, int n, double* __restrict__ E) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) s += part[x];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *E = 0.5 * red[0];
+}
+
 }  // namespace
+
+cudaError_t run_farfield_J(const JArgs& a, cudaStream_t s) {
+    k_zero_square<<<256, 256, 0, s>>>(a.J, a.ldj, a.nao);
+    if (a.depth < 2 || a.nleaf == 0) {
+        cudaMemsetAsync(a.Ej_dev, 0, sizeof(double), s);
+        return cudaGetLastError();
+    }
+    const int nc = a.nc, D = a.depth;
+    const int leaf_store0 = a.leaf0 - a.first_box;
+    double* Ob = a.ob;
+    double* Mb = a.mb;
+    k_j_density<<<dim3(a.nleaf, nc), 256, 0, s>>>(a.leaf_rowoff, a.leaf_aos, a.row_ptr, a.ent_col, a.ent_val, a.vals,
+                                                  nc, a.D, a.ldd, Ob + (size_t)leaf_store0 * nc);
+    const int LMC = translate_chunk(nc);
+    const int nchunk = (nc + LMC - 1) / LMC;
+    for (int lev = D; lev >= 3; --lev) {
+        const int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
+        launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 0, 1, nc, a.L, a.first_box, t0, a.child_ptr,
+                                 a.child_list, a.m2m_op, nullptr, a.parent, a.ops, Ob, Ob, 0);
+    }
+    {
+        const int t0 = a.level_off[2], nt = a.nbox - t0;
+        launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 1, 1, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
+                                 a.m2l_op, nullptr, a.parent, a.ops, Ob, Mb, 0);
+    }
+    for (int lev = 3; lev <= D; ++lev) {
+        const int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
+        launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 2, 1, nc, a.L, a.first_box, t0, nullptr, nullptr,
+                                 a.l2l_op, nullptr, a.parent, a.ops, Mb, Mb, 1);
+    }
+    k_j_l2p<<<a.nleaf, 256, 0, s>>>(a.leaf_rowoff, a.leaf_aos, a.row_ptr, a.ent_col, a.ent_val, a.vals, nc,
+                                    Mb + (size_t)leaf_store0 * nc, a.D, a.ldd, a.J, a.ldj, a.part);
+    k_j_energy<<<1, 256, 0, s>>>(a.part, a.nleaf, a.Ej_dev);
+    return cudaGetLastError();
+}
 
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s) {
     if (a.prec == OCCK_FP64) return run_typed<double>(a, s);

@@ -140,6 +140,7 @@ struct occk_ctx {
     int last_scaled = 0;                    // last run kept O and Mcal in scaled form
     int tr_engine = -1;                     // occk_set_translate_engine mask
     occk::DevBuf sob, smb;                  // slot storage of O~ and Mcal~ (slot pipeline)
+    occk::DevBuf jbox;                      // far-field J: density multipoles, local expansions, partials
     int last_slot = 0;                      // last run used the slot pipeline
     int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
     // stage timers
@@ -204,6 +205,21 @@ struct FmmArgs {
     const int* m2l_tgt; const int* box_key; const int* box_level; const double* hlev;
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
+// Far-field Coulomb matrix (FP64; kernels_fmm.cu).
+struct JArgs {
+    int nao, nc, L, depth, nbox, first_box, nleaf, leaf0;
+    const int* level_off;            // host
+    const int* leaf_rowoff; const int* leaf_aos; const int* row_ptr; const int* ent_col; const int* ent_val;
+    const int* child_ptr; const int* child_list; const int* m2m_op; const int* l2l_op; const int* parent;
+    const int* m2l_ptr; const int* m2l_src; const int* m2l_op;
+    const double* vals; const double* ops;
+    const double* D; int ldd;        // column-major density matrix
+    double* J; int ldj;              // column-major output
+    double* Ej_dev;
+    double* ob; double* mb;          // [stored boxes][nc] density multipoles, local expansions
+    double* part;                    // [nleaf]
+};
+cudaError_t run_farfield_J(const JArgs& a, cudaStream_t s);
 // partial energies run_farfield writes to FmmArgs::part (its K reduction blocks)
 constexpr int kFarfieldPartials = 1024;
 // Arguments of the SIMT FP64/FP32 path for one tree with caller-provided

@@ -79,6 +79,8 @@ _SIGS = {
     "occk_set_translate_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "occk_set_l2p_split": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_farfield_J": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                       ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_device_status": (ctypes.c_int, [_vp, _vp]),
     "occk_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                          ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -298,6 +300,26 @@ def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K
                                ctypes.byref(eh) if want_energy_host else None, _stream_ptr(stream))
     ctx.check(rc, "occk_farfield_K")
     return K, (eh.value if want_energy_host else Ex)
+
+
+def farfield_J(ctx: Context, tree: Tree, D, J=None, Ej=None, want_energy_host: bool = False, stream=None):
+    """occk_farfield_J on torch CUDA tensors.  D: [nao, nao] float64 symmetric
+    density (a column-major copy is made if needed).  Returns (J, Ej) with J
+    column-major [nao, nao] and Ej a 0-d device tensor (or a float when
+    want_energy_host)."""
+    import torch
+    D = fortran(D)
+    nao = D.shape[0]
+    if J is None:
+        J = empty_fortran(nao, nao, torch.float64, D.device)
+    if Ej is None:
+        Ej = torch.empty((), dtype=torch.float64, device=D.device)
+    eh = ctypes.c_double()
+    rc = lib().occk_farfield_J(ctx._h, tree._h, _vp(D.data_ptr()), ld(D), _vp(J.data_ptr()), ld(J),
+                               _vp(Ej.data_ptr()), ctypes.byref(eh) if want_energy_host else None,
+                               _stream_ptr(stream))
+    ctx.check(rc, "occk_farfield_J")
+    return J, (eh.value if want_energy_host else Ej)
 
 
 # ---- batches ---------------------------------------------------------------------
