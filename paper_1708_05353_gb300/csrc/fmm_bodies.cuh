@@ -216,6 +216,10 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
 // mode 0: M2M, sources = children of tgt, operator m2m_op[child], lower in l
 // mode 1: M2L, sources = interaction list of tgt, operator m2l_op[e], rank lmax_e
 // mode 2: L2L, source = parent of tgt, operator l2l_op[tgt], upper in l
+// mode 3: M2L and L2L of one level in one pass: the interaction list as in
+//         mode 1, then the parent's finished local expansion (read from
+//         `parent_in`, operator l2l_opidx[tgt]) when the parent is stored
+//         (level >= 3); the target is written once, with no read-modify-write
 // grid (pair blocks, targets, lm chunks).
 // ---------------------------------------------------------------------------
 // Pairs per thread of the translations: FP32 reuses each operator entry read
@@ -228,7 +232,8 @@ template <typename T, int LMC>
 __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode, int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr,
             const int* __restrict__ list, const int* __restrict__ opidx, const int* __restrict__ lmax_e,
             const int* __restrict__ parent, const T* __restrict__ ops, const T* __restrict__ in,
-            T* __restrict__ out, int accumulate) {
+            T* __restrict__ out, int accumulate, const int* __restrict__ l2l_opidx = nullptr,
+            const T* parent_in = nullptr) {
     constexpr int PPT = translate_ppt<T>();
     __shared__ T sop[kNcMax][LMC];      // [input component][output component of the chunk]
     const int tgt = tgt0 + by;
@@ -245,7 +250,7 @@ __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode,
 #pragma unroll
         for (int q = 0; q < LMC; ++q)
             acc[k][q] = (accumulate && live[k] && q < ncl) ? o[(size_t)q * P + k * blockDim.x] : T(0);
-    int e0, e1;
+    int e0, e1, eend;
     if (mode == 2) {
         e0 = 0;
         e1 = 1;
@@ -253,29 +258,33 @@ __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode,
         e0 = ptr[tgt];
         e1 = ptr[tgt + 1];
     }
+    // mode 3: one more step for the parent's local expansion
+    eend = e1 + ((mode == 3 && parent[tgt] >= first_box) ? 1 : 0);
     // output rank range of this chunk
     int lhi = 0;
     while ((lhi + 1) * (lhi + 1) <= c0 + ncl - 1) ++lhi;
     int llo = 0;
     while ((llo + 1) * (llo + 1) <= c0) ++llo;
-    for (int e = e0; e < e1; ++e) {
+    for (int e = e0; e < eend; ++e) {
         int src, op, Le = L;
+        // the L2L step of mode 3 behaves as mode 2
+        const bool l2l = mode == 2 || e == e1;
         if (mode == 0) {
             src = list[e];
             op = opidx[src];
-        } else if (mode == 1) {
+        } else if (!l2l) {
             src = list[e];
             op = opidx[e];
             if (lmax_e) Le = lmax_e[e];
         } else {
             src = parent[tgt];
-            op = opidx[tgt];
+            op = mode == 2 ? opidx[tgt] : l2l_opidx[tgt];
         }
         const int ncr = (Le + 1) * (Le + 1);
         if (c0 >= ncr) continue;   // uniform across the block
         int cb0 = 0, cb1 = ncr;
         if (mode == 0) cb1 = min(ncr, (lhi + 1) * (lhi + 1));
-        if (mode == 2) cb0 = llo * llo;
+        if (l2l) cb0 = llo * llo;
         const T* Tm = ops + (size_t)op * nc * nc;
         __syncthreads();
         for (int x = threadIdx.x; x < LMC * (cb1 - cb0); x += blockDim.x) {
@@ -283,7 +292,7 @@ __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode,
             sop[c][q] = (q < ncl && c0 + q < ncr) ? Tm[(size_t)(c0 + q) * nc + c] : T(0);
         }
         __syncthreads();
-        const T* x = in + (size_t)(src - first_box) * nc * P + pb;
+        const T* x = (mode == 3 && l2l ? parent_in : in) + (size_t)(src - first_box) * nc * P + pb;
         for (int c = cb0; c < cb1; ++c) {
             T v[PPT];
 #pragma unroll

@@ -48,12 +48,12 @@ __global__ void __launch_bounds__(128)
 k_translate(int mode, int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr,
             const int* __restrict__ list, const int* __restrict__ opidx, const int* __restrict__ lmax_e,
             const int* __restrict__ parent, const T* __restrict__ ops, const T* __restrict__ in,
-            T* __restrict__ out, int accumulate) {
+            T* __restrict__ out, int accumulate, const int* __restrict__ l2l_opidx, const T* parent_in) {
     // blockIdx.x = target, blockIdx.y = pair block: consecutive blocks work on
     // the same pairs of different targets, so the source slices they share
     // stay in L2 (a pair block of every box of a level is well under 1 MB)
     body::translate_body<T, LMC>(blockIdx.y, blockIdx.x, blockIdx.z, mode, P, nc, L, first_box, tgt0, ptr, list,
-                                 opidx, lmax_e, parent, ops, in, out, accumulate);
+                                 opidx, lmax_e, parent, ops, in, out, accumulate, l2l_opidx, parent_in);
 }
 
 template <typename T, int BM, int BK, int TM>
@@ -214,6 +214,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     // three translations read and write slots, the leaf local expansions come
     // back as FP32 for step (e)
     const bool slots = trc && a.slot_o != nullptr;
+    // M2L and L2L both on the SIMT kernel: one fused pass per level
+    const bool fused = !slots && !(trc && (a.tr_mask & 2)) && !(trc && (a.tr_mask & 4));
     SlotArgs sh{};
     const int ntile = (int)((P + 127) / 128);
     if (slots) {
@@ -241,7 +243,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         }
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 0, (int)P, nc, a.L, a.first_box, t0, a.child_ptr,
-                                             a.child_list, a.m2m_op, nullptr, a.parent, tops, Ob, Ob, 0);
+                                             a.child_list, a.m2m_op, nullptr, a.parent, tops, Ob, Ob, 0,
+                                             (const int*)nullptr, (const T*)nullptr);
     }
     // learned ranks: features from the multipoles of every box, FP16 MLP,
     // budgeted choice; M2L then reads the per-edge ranks
@@ -267,11 +270,22 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         cudaError_t e2 = tr_translate(a.prec, th, 1, t0, nt, a.m2l_ptr, a.m2l_src, a.m2l_op, (const float*)Ob,
                                       (float*)Mb, 0, s);
         if (e2 != cudaSuccess) return e2;
+    } else if (fused) {
+        // (c) and (d) together, level by level: each target is written once
+        // from its interaction list and its parent's finished expansion
+        for (int lev = 2; lev <= D; ++lev) {
+            int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
+            if (nt <= 0) continue;
+            dim3 g(nt, pblocks, nchunk);
+            launch_translate<T>(LMC, g, s, 3, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
+                                a.m2l_op, lmax_e, a.parent, tops, Ob, Mb, 0, a.l2l_op, (const T*)Mb);
+        }
     } else {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 1, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
-                                             a.m2l_op, lmax_e, a.parent, tops, Ob, Mb, 0);
+                                             a.m2l_op, lmax_e, a.parent, tops, Ob, Mb, 0,
+                                             (const int*)nullptr, (const T*)nullptr);
     }
     // (d) L2L: children at level lev accumulate their parent's expansion
     mark(4);
@@ -283,7 +297,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         }
         if (e2 != cudaSuccess) return e2;
     }
-    for (int lev = 3; lev <= D && !slots; ++lev) {
+    for (int lev = 3; lev <= D && !slots && !fused; ++lev) {
         int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
         if (trc && (a.tr_mask & 4)) {
             cudaError_t e2 = tr_translate(a.prec, th, 2, t0, nt, nullptr, nullptr, a.l2l_op, (const float*)Mb,
@@ -293,7 +307,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         }
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 2, (int)P, nc, a.L, a.first_box, t0, nullptr, nullptr,
-                                             a.l2l_op, nullptr, a.parent, tops, Mb, Mb, 1);
+                                             a.l2l_op, nullptr, a.parent, tops, Mb, Mb, 1,
+                                             (const int*)nullptr, (const T*)nullptr);
     }
     // (e) L2P
     mark(5);
@@ -439,17 +454,20 @@ cudaError_t run_farfield_J(const JArgs& a, cudaStream_t s) {
     for (int lev = D; lev >= 3; --lev) {
         const int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
         launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 0, 1, nc, a.L, a.first_box, t0, a.child_ptr,
-                                 a.child_list, a.m2m_op, nullptr, a.parent, a.ops, Ob, Ob, 0);
+                                 a.child_list, a.m2m_op, nullptr, a.parent, a.ops, Ob, Ob, 0,
+                                 (const int*)nullptr, (const double*)nullptr);
     }
     {
         const int t0 = a.level_off[2], nt = a.nbox - t0;
         launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 1, 1, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
-                                 a.m2l_op, nullptr, a.parent, a.ops, Ob, Mb, 0);
+                                 a.m2l_op, nullptr, a.parent, a.ops, Ob, Mb, 0, (const int*)nullptr,
+                                 (const double*)nullptr);
     }
     for (int lev = 3; lev <= D; ++lev) {
         const int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
         launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 2, 1, nc, a.L, a.first_box, t0, nullptr, nullptr,
-                                 a.l2l_op, nullptr, a.parent, a.ops, Mb, Mb, 1);
+                                 a.l2l_op, nullptr, a.parent, a.ops, Mb, Mb, 1, (const int*)nullptr,
+                                 (const double*)nullptr);
     }
     k_j_l2p<<<a.nleaf, 256, 0, s>>>(a.leaf_rowoff, a.leaf_aos, a.row_ptr, a.ent_col, a.ent_val, a.vals, nc,
                                     Mb + (size_t)leaf_store0 * nc, a.D, a.ldd, a.J, a.ldj, a.part);
