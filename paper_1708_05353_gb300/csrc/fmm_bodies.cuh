@@ -293,15 +293,25 @@ __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode,
         }
         __syncthreads();
         const T* x = (mode == 3 && l2l ? parent_in : in) + (size_t)(src - first_box) * nc * P + pb;
-        for (int c = cb0; c < cb1; ++c) {
-            T v[PPT];
+        // CB input components at a time: all their loads are issued before
+        // the first FMA that needs them
+        constexpr int CB = (sizeof(T) == 4 && LMC <= 9) ? 8 : 4;
+        for (int cb = cb0; cb < cb1; cb += CB) {
+            T v[CB][PPT];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) v[k] = live[k] ? x[(size_t)c * P + k * blockDim.x] : T(0);
+            for (int u = 0; u < CB; ++u)
 #pragma unroll
-            for (int q = 0; q < LMC; ++q) {
-                const T w = sop[c][q];
+                for (int k = 0; k < PPT; ++k)
+                    v[u][k] = (cb + u < cb1 && live[k]) ? x[(size_t)(cb + u) * P + k * blockDim.x] : T(0);
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) acc[k][q] += w * v[k];
+            for (int u = 0; u < CB; ++u) {
+                if (cb + u >= cb1) break;      // uniform across the block
+#pragma unroll
+                for (int q = 0; q < LMC; ++q) {
+                    const T w = sop[cb + u][q];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) acc[k][q] += w * v[u][k];
+                }
             }
         }
     }
