@@ -21,6 +21,15 @@ Readings (the paper is silent or inconsistent):
 * Per-edge truncation (``lmax_edges``): the M2L operator of an edge keeps only
   output and input ranks <= L_e; M2M and L2L keep the full L.
 
+Occupied-pair screening (``pair_tau``; the paper's proposed extension to
+localised orbitals, Sec. IV): after step 1 a pair (i, j) whose pair-density
+multipoles are negligible over all leaves,
+    n_ij^2 = sum_X sum_{l, m=-l..l} |O^{ij,X}_lm|^2 < tau^2,
+is dropped: its multipoles are set to zero before step 2, so it has no local
+expansion and no part in K.  Pairs are independent in steps 2-5, so the
+energy changes by exactly the dropped pairs' own contributions
+e_ij = -sum_X sum_lm O^{ij,X}_lm Mcal^{ij}_lm(X).
+
 Everything runs for a subset I of occupied columns i when ``i_subset`` is
 given: K_{r,i in I} needs O^{ij}, Mcal^{ij} for i in I and all j only, so the
 result is exact for those columns.
@@ -79,7 +88,8 @@ def full_transform(tree, W, C, i_cols):
 
 
 def farfield(system_or_basis, C=None, L=None, tree=None, i_subset=None,
-             lmax_edges=None, pair_thresh=1e-14, return_parts=False, Opair=None, W=None):
+             lmax_edges=None, pair_thresh=1e-14, return_parts=False, Opair=None, W=None,
+             pair_tau=None):
     """Far-field K^ff (n_AO x |I|) and E^ff for the columns in ``i_subset``.
 
     ``Opair`` / ``W`` may carry step 0 and the first half of step 1 from an
@@ -107,6 +117,19 @@ def farfield(system_or_basis, C=None, L=None, tree=None, i_subset=None,
     if W is None:
         W = half_transform(basis, tree, Opair, C, L)
     Oleaf = full_transform(tree, W, C, i_cols)
+    # occupied-pair screening: drop pairs with negligible multipoles on every leaf
+    # (the norm of an unordered pair is taken from O^{ab}, a = min(i, j),
+    # b = max(i, j), so that (i, j) and (j, i) share one decision)
+    keep = None
+    norm2 = None
+    if pair_tau is not None and pair_tau > 0:
+        norm2 = np.zeros((nI, nocc))
+        upper = i_cols[:, None] <= np.arange(nocc)[None, :]
+        for S, Wb, Ob in zip(tree["ao_sets"], W, Oleaf):
+            Ot = np.einsum("rj,lri->lij", C[S], Wb[:, :, i_cols])      # O^{ji} for i in I
+            norm2 += np.sum(np.abs(np.where(upper[None], Ob, Ot)) ** 2, axis=0)
+        keep = norm2 >= pair_tau ** 2
+        Oleaf = [Ob * keep[None] for Ob in Oleaf]
 
     # multipoles O^{ij} of every box, [nbox, nlm, |I|, nocc]
     Obox = np.zeros((nbox, nlm, nI, nocc), dtype=np.complex128)
@@ -143,7 +166,7 @@ def farfield(system_or_basis, C=None, L=None, tree=None, i_subset=None,
     K = K.real
     E = -0.5 * float(np.sum(C[:, i_cols] * K))
     if return_parts:
-        return K, E, dict(tree=tree, W=W, Obox=Obox, Mbox=Mbox, Opair=Opair)
+        return K, E, dict(tree=tree, W=W, Obox=Obox, Mbox=Mbox, Opair=Opair, keep=keep, norm2=norm2)
     return K, E
 
 

@@ -345,6 +345,28 @@ def loewdin_occupied(basis: Basis, nocc: int, rng) -> np.ndarray:
     return np.ascontiguousarray(C0 @ (V * (1.0 / np.sqrt(w))) @ V.T)
 
 
+def localised_occupied(basis: Basis, nocc: int, rng, sigma: float = 3.0) -> np.ndarray:
+    """Localised occupied orbitals: orbital j starts as N(0,1) coefficients
+    under a Gaussian envelope exp(-|A - X_j|^2 / sigma^2) of the distance from
+    its AO's atom A to a centre atom X_j (centres evenly spaced along the
+    atoms sorted by their first principal coordinate), then the same Loewdin
+    orthonormalisation in the AO overlap metric as ``loewdin_occupied``.  The
+    orthonormalised orbitals keep exponentially decaying tails, so orbital
+    pairs far apart have negligible pair densities."""
+    S = overlap_matrix(basis)
+    xyz = basis.xyz
+    x0 = xyz - xyz.mean(axis=0)
+    axis = np.linalg.svd(x0, full_matrices=False)[2][0]
+    order = np.argsort(x0 @ axis, kind="stable")
+    centres = xyz[order[(np.arange(nocc) * len(order)) // nocc]]          # [nocc, 3]
+    ao_atom = np.repeat(basis.shell_atom, np.diff(basis.shell_ao_offset))
+    d2 = ((xyz[ao_atom][:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)   # [nao, nocc]
+    C0 = rng.normal(size=(basis.nao, nocc)) * np.exp(-d2 / sigma ** 2)
+    M = C0.T @ S @ C0
+    w, V = np.linalg.eigh(M)
+    return np.ascontiguousarray(C0 @ (V * (1.0 / np.sqrt(w))) @ V.T)
+
+
 def electrons(elements) -> int:
     return sum(ELECTRONS[e] for e in elements)
 
@@ -377,6 +399,23 @@ def alkane(ncarbon: int = 150, lmax: int = 2, seed_k: int = 2, nocc: int | None 
     C = loewdin_occupied(basis, nocc, np.random.default_rng(1000 * seed_k + 2 + ncarbon * 0))
     return System(f"C{ncarbon}H{2 * ncarbon + 2}", basis, nocc, C, depth=0,
                   target_atoms_per_leaf=8.0, lmax=lmax)
+
+
+def alkane_localised(ncarbon: int = 150, lmax: int = 2, seed_k: int = 2, sigma: float = 3.0) -> System:
+    """The alkane chain with localised occupied orbitals (the occupied-pair
+    screening workload): same geometry and basis as ``alkane``."""
+    s = alkane(ncarbon, lmax=lmax, seed_k=seed_k)
+    C = localised_occupied(s.basis, s.nocc, np.random.default_rng(1000 * seed_k + 7), sigma)
+    return System(f"C{ncarbon}H{2 * ncarbon + 2}-loc", s.basis, s.nocc, C, depth=0,
+                  target_atoms_per_leaf=8.0, lmax=lmax)
+
+
+def small_sp_localised(natom: int = 10, nocc: int = 8, spacing: float = 2.6, seed: int = 11,
+                       lmax: int = 2, depth: int = 3, sigma: float = 2.5) -> System:
+    """A small s/p line with localised occupied orbitals."""
+    s = small_sp(natom=natom, nocc=nocc, spacing=spacing, seed=seed, lmax=lmax, depth=depth)
+    C = localised_occupied(s.basis, nocc, np.random.default_rng(seed + 3), sigma)
+    return System(f"sp{natom}-loc", s.basis, nocc, C, depth=depth, target_atoms_per_leaf=8.0, lmax=lmax)
 
 
 def water(nmol: int = 100, lmax: int = 4, seed_k: int = 3, nocc: int | None = None,
