@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--cpu-cols", type=int, default=2)
     p.add_argument("--workload", default="chain", choices=["chain", "water", "batch"])
     p.add_argument("--batch-fp64", action="store_true", help="run the batch workload in FP64 (default FP32)")
+    p.add_argument("--screen-tau", type=float, default=1e-4,
+                   help="occupied-pair screening threshold timed on localised orbitals of the same chain "
+                        "(0: skip)")
     p.add_argument("--variants", default="fp64,fp32,tf32,bf16,fp16,bf16x3,fp16x3",
                    help="extra precisions timed beside the main one (comma list, or 'none')")
     return p.parse_args()
@@ -494,6 +497,51 @@ def main():
     result["coulomb_j"] = {"ms": round(sum(a.elapsed_time(b) for a, b in jev) / len(jev), 4),
                            "E_J": float(Ej.item()), "lmax": L, "dtype": "f64",
                            "what": "far-field J^ff and E_J on the same tree, D = 2 C C^T"}
+    # ---- occupied-pair screening: the same chain and tree with localised
+    # occupied orbitals, unscreened and screened, in the main precision
+    if args.screen_tau > 0 and args.workload == "chain" and args.prec in ("fp64", "fp32"):
+        sl = inputs.alkane_localised(args.ncarbon, lmax=L)
+        Cl = occk.fortran(torch.tensor(sl.C, dtype=torch.float64, device=dev))
+
+        def timed_loc(tau):
+            ctx.set_pair_screen(tau)
+            try:
+                for _ in range(3):
+                    occk.farfield_K(ctx, tree, Cl, prec=args.prec, K=K, Ex=Ex)
+                ev = []
+                nst = max(3, args.steps)
+                st = {k: 0.0 for k in occk.STAGES}
+                ctx.set_timing(True)
+                for k in range(nst):
+                    flush.fill_(float(k))
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    occk.farfield_K(ctx, tree, Cl, prec=args.prec, K=K, Ex=Ex)
+                    b.record(stream)
+                    ev.append((a, b))
+                    for n_, v_ in ctx.timings().items():
+                        st[n_] += v_ / nst
+                ctx.set_timing(False)
+                torch.cuda.synchronize()
+                kept = ctx.pair_screen_count()
+            finally:
+                ctx.set_pair_screen(0.0)
+            return (sum(a.elapsed_time(b) for a, b in ev) / len(ev), float(Ex.item()), K.clone(), kept,
+                    {k: round(v, 4) for k, v in st.items()})
+
+        ms0, E0, K0, _, st0 = timed_loc(0.0)
+        ms1, E1, K1, kept, st1 = timed_loc(args.screen_tau)
+        npair = system.nocc * (system.nocc + 1) // 2
+        result["pair_screen"] = {
+            "workload": sl.name + " (same geometry, basis and tree; localised occupied orbitals)",
+            "tau": args.screen_tau, "kept_pairs": kept, "pairs": npair,
+            "kept_fraction": round(kept / npair, 4),
+            "ms_unscreened": round(ms0, 4), "ms_screened": round(ms1, 4),
+            "speedup": round(ms0 / ms1, 3),
+            "stage_ms_unscreened": st0, "stage_ms_screened": st1,
+            "abs_dE_Eh": abs(E1 - E0),
+            "rel_dK": float((K1 - K0).abs().max().item()) / float(K0.abs().max().item()),
+            "dtype": "f64" if args.prec == "fp64" else args.prec}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(system, L, args.cpu_cols)
     if rank == 0:

@@ -322,6 +322,26 @@ occk_status occk_batch_set_config(occk_batch* batch, const int* cfg);
  * a tensor-core kernel gave up (its results are then invalid), else OK. */
 occk_status occk_device_status(occk_ctx* ctx, void* stream);
 
+/* Occupied-pair screening for localised occupied orbitals (the extension the
+ * paper proposes in Sec. IV).  With tau > 0, occk_farfield_K drops every
+ * occupied pair (i, j) whose pair-density multipoles are negligible on all
+ * leaves,  n_ij^2 = sum_X sum_{l, m=-l..l} |O^{ij,X}_lm|^2 < tau^2  (Eq.
+ * motrans gives O^{ij,X}), before M2M: M2M, M2L and L2L run on the kept pairs
+ * only and the dropped pairs have no local expansion and no part in K.  The
+ * norm of pair (i, j) is taken from the stored (min, max) ordering, so both
+ * orderings share one decision.
+ *   tau  absolute threshold, finite and >= 0; 0 turns screening off (default)
+ * Screening runs with OCCK_FP64 and OCCK_FP32 and lmax_policy 0 or 1; other
+ * precisions and the learned policy give OCCK_ERR_UNSUPPORTED while tau > 0.
+ * With screening on, occk_debug_fetch returns current values for the leaf
+ * boxes only.  OCCK_ERR_ARG for a negative, infinite or NaN tau. */
+occk_status occk_set_pair_screen(occk_ctx* ctx, double tau);
+
+/* Number of occupied pairs i <= j kept by the last occk_farfield_K call on
+ * this context (synchronises `stream`, the stream of that call), or -1 in
+ * *kept when that call did not screen. */
+occk_status occk_pair_screen_count(occk_ctx* ctx, long long* kept, void* stream);
+
 /* The far-field Coulomb matrix (paper, Sec. II: the density-contracted box
  * multipoles, Eq. fmmc, and J^ff_rs = sum_lm O^{rs,X}_lm Mcal_lm(X)), in FP64,
  * on the same tree, pair multipoles and operators as the exchange:

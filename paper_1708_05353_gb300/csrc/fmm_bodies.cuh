@@ -233,8 +233,13 @@ __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode,
             const int* __restrict__ list, const int* __restrict__ opidx, const int* __restrict__ lmax_e,
             const int* __restrict__ parent, const T* __restrict__ ops, const T* __restrict__ in,
             T* __restrict__ out, int accumulate, const int* __restrict__ l2l_opidx = nullptr,
-            const T* parent_in = nullptr) {
+            const T* parent_in = nullptr, const int* __restrict__ pcount = nullptr) {
     constexpr int PPT = translate_ppt<T>();
+    // pcount (device, nullable): only the first *pcount pairs of each row are
+    // live (compacted pairs after occupied-pair screening); P stays the row
+    // stride
+    const int Pl = pcount ? min(P, *pcount) : P;
+    if (bx * (int)blockDim.x * PPT >= Pl) return;     // uniform across the block
     __shared__ T sop[kNcMax][LMC];      // [input component][output component of the chunk]
     const int tgt = tgt0 + by;
     const int c0 = bz * LMC;
@@ -242,7 +247,7 @@ __device__ __forceinline__ void translate_body(int bx, int by, int bz, int mode,
     const int pb = bx * blockDim.x * PPT + threadIdx.x;      // pairs pb + k * blockDim.x
     bool live[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) live[k] = pb + k * (int)blockDim.x < P;
+    for (int k = 0; k < PPT; ++k) live[k] = pb + k * (int)blockDim.x < Pl;
     T acc[PPT][LMC];
     T* o = out + ((size_t)(tgt - first_box) * nc + c0) * P + pb;
 #pragma unroll

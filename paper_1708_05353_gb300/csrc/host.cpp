@@ -117,7 +117,8 @@ extern "C" void occk_destroy(occk_ctx* c) {
         for (occk::DevBuf* b : {&c->ct, &c->w, &c->obox, &c->mbox, &c->kb, &c->part, &c->edev,
                                 &c->scratch, &c->mlp_prm, &c->mlp_norm, &c->mlp_m, &c->mlp_v, &c->mlp_h,
                                 &c->mlp_grad, &c->mlp_ws, &c->feat, &c->pred, &c->ranks, &c->nrm, &c->gram,
-                                &c->pplan, &c->panels}) {
+                                &c->pplan, &c->panels, &c->tpan, &c->tscale, &c->tops, &c->sob, &c->smb,
+                                &c->jbox, &c->scr_o, &c->scr_m, &c->scr_aux}) {
             if (b->p) cudaFree(b->p);
             b->p = nullptr;
         }
@@ -826,6 +827,32 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.hlev = d.hlev;
         ctx->ranks_valid = 1;
     }
+    // occupied-pair screening: FP64 and FP32 (unscaled storage, SIMT tree
+    // passes); not with the learned selector, whose features read every box
+    a.screen = 0;
+    ctx->last_screen = 0;
+    if (ctx->screen_tau > 0) {
+        if (prec != OCCK_FP64 && prec != OCCK_FP32)
+            return fail(ctx, OCCK_ERR_UNSUPPORTED, "occupied-pair screening runs in FP64 and FP32 only");
+        if (a.learned) return fail(ctx, OCCK_ERR_UNSUPPORTED, "occupied-pair screening with the learned selector");
+        if ((e = ensure(ctx->scr_o, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
+            (e = ensure(ctx->scr_m, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
+            (e = ensure(ctx->scr_aux, 16 * P + 16 + 4 * ((P + 255) / 256))) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "pair screening workspaces")
+                                                  : cuda_fail(ctx, e, "pair screening workspaces");
+        char* x = (char*)ctx->scr_aux.p;
+        a.screen = 1;
+        a.screen_tau2 = ctx->screen_tau * ctx->screen_tau;
+        a.scr_o = ctx->scr_o.p;
+        a.scr_m = ctx->scr_m.p;
+        a.scr_norm = (double*)x;
+        a.scr_keep = (int*)(x + 8 * P);
+        a.scr_inv = (int*)(x + 12 * P);
+        a.scr_count = (int*)(x + 16 * P);
+        a.scr_bcount = (int*)(x + 16 * P + 16);
+        ctx->last_screen = 1;
+        ctx->last_screen_P = P;
+    }
     // panel plan of the tensor-core steps (a) and (e): panel counts per leaf
     if (occk::tc_mode(prec) >= 0) {
         const int esz = occk::panel_elem_bytes(prec), pbytes = occk::panel_bytes(prec);
@@ -1028,6 +1055,30 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         if (e != cudaSuccess) return cuda_fail(ctx, e, "energy copy");
         if (werr) return fail(ctx, OCCK_ERR_TIMEOUT, "a tensor-core wait gave up; results are invalid");
     }
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_pair_screen(occk_ctx* ctx, double tau) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (!(tau >= 0.0) || std::isinf(tau)) return fail(ctx, OCCK_ERR_ARG, "tau must be finite and >= 0");
+    ctx->screen_tau = tau;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_pair_screen_count(occk_ctx* ctx, long long* kept, void* stream) {
+    if (!ctx || !kept) return fail(ctx, OCCK_ERR_ARG, "null argument");
+    *kept = -1;
+    if (!ctx->last_screen || !ctx->scr_aux.p) return OCCK_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    // the count sits after the norms and the two maps (16 bytes per pair)
+    const size_t P = ctx->last_screen_P;
+    int n = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(&n, (const char*)ctx->scr_aux.p + 16 * P, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pair screening count");
+    *kept = n;
     return OCCK_OK;
 }
 

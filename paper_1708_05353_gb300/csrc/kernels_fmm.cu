@@ -48,12 +48,13 @@ __global__ void __launch_bounds__(128)
 k_translate(int mode, int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr,
             const int* __restrict__ list, const int* __restrict__ opidx, const int* __restrict__ lmax_e,
             const int* __restrict__ parent, const T* __restrict__ ops, const T* __restrict__ in,
-            T* __restrict__ out, int accumulate, const int* __restrict__ l2l_opidx, const T* parent_in) {
+            T* __restrict__ out, int accumulate, const int* __restrict__ l2l_opidx, const T* parent_in,
+            const int* __restrict__ pcount) {
     // blockIdx.x = target, blockIdx.y = pair block: consecutive blocks work on
     // the same pairs of different targets, so the source slices they share
     // stay in L2 (a pair block of every box of a level is well under 1 MB)
     body::translate_body<T, LMC>(blockIdx.y, blockIdx.x, blockIdx.z, mode, P, nc, L, first_box, tgt0, ptr, list,
-                                 opidx, lmax_e, parent, ops, in, out, accumulate, l2l_opidx, parent_in);
+                                 opidx, lmax_e, parent, ops, in, out, accumulate, l2l_opidx, parent_in, pcount);
 }
 
 template <typename T, int BM, int BK, int TM>
@@ -103,6 +104,157 @@ __global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) s += a[q];
     if (s == T(-1.2345)) out[threadIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Occupied-pair screening (the paper's proposed extension to localised
+// orbitals, Sec. IV): a pair p = (i <= j) is kept when
+//   n_p^2 = sum_leaves sum_lm w_lm O[leaf][lm][p]^2 >= tau^2,
+// w = 1 for m = 0 and 2 for the Re and Im components of m > 0 (the real form
+// of sum over m = -l..l of |O_lm|^2).  The tree passes then run on the kept
+// pairs, compacted to the front of every [box][lm] row.
+// ---------------------------------------------------------------------------
+// Pass 1a: partial norms over groups of kPairLG leaves, part[g][p], in the
+// storage type.  A block takes 8 x 256 consecutive pairs of one group and
+// walks its leaf-component rows, reading 8 KB contiguous from each.
+constexpr int kPairBlk = 256, kPairLG = 8, kPairPPT = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kPairBlk)
+k_pair_part(const T* __restrict__ Oleaf, int nleaf, int nc, long long P, T* __restrict__ part) {
+    __shared__ T wsh[body::kNcMax];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= c) ++l;
+        wsh[c] = c == l * l ? T(1) : T(2);
+    }
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * (kPairBlk * kPairPPT) + threadIdx.x;
+    const int B0 = blockIdx.y * kPairLG, B1 = min(nleaf, B0 + kPairLG);
+    T acc[kPairPPT];
+#pragma unroll
+    for (int k = 0; k < kPairPPT; ++k) acc[k] = T(0);
+    for (int r = B0 * nc; r < B1 * nc; ++r) {
+        const T w = wsh[r % nc];
+        const T* row = Oleaf + (size_t)r * P;
+        T x[kPairPPT];
+#pragma unroll
+        for (int k = 0; k < kPairPPT; ++k) {
+            const long long p = base + (long long)k * kPairBlk;
+            x[k] = p < P ? row[p] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kPairPPT; ++k) acc[k] += w * x[k] * x[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kPairPPT; ++k) {
+        const long long p = base + (long long)k * kPairBlk;
+        if (p < P) part[(size_t)blockIdx.y * P + p] = acc[k];
+    }
+}
+
+// Pass 1b (kPairBlk pairs per block): each pair's norm (the groups summed in
+// order, in FP64) and keep flag (stored in inv as 1 / 0), and the block's
+// count of kept pairs.
+template <typename T>
+__global__ void __launch_bounds__(kPairBlk)
+k_pair_flag(const T* __restrict__ part, int ngrp, long long P, double tau2, double* __restrict__ n2,
+            int* __restrict__ inv, int* __restrict__ bcount) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int keep = 0;
+    if (p < P) {
+        double acc = 0.0;
+        for (int g = 0; g < ngrp; ++g) acc += (double)part[(size_t)g * P + p];
+        n2[p] = acc;
+        keep = acc >= tau2;
+        inv[p] = keep;
+    }
+    const int n = __syncthreads_count(keep);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = n;
+}
+
+// Pass 2 (one block): exclusive scan of the block counts in place, total in
+// *count.
+__global__ void __launch_bounds__(1024) k_pair_scan(int* __restrict__ bcount, int nb, int* __restrict__ count) {
+    __shared__ int part[1024];
+    const int per = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+    int sum = 0;
+    for (int b = b0; b < b1; ++b) sum += bcount[b];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    // inclusive scan of the 1024 partial sums (Hillis-Steele)
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (int b = b0; b < b1; ++b) {
+        const int t = bcount[b];
+        bcount[b] = run;
+        run += t;
+    }
+    if (threadIdx.x == blockDim.x - 1) *count = part[threadIdx.x];
+}
+
+// Pass 3 (kPairBlk pairs per block): kept pairs in increasing order (keep[q]
+// = p) and the inverse map (inv[p] = q or -1).  Deterministic.
+__global__ void __launch_bounds__(kPairBlk)
+k_pair_compact(long long P, const int* __restrict__ boff, int* __restrict__ keep, int* __restrict__ inv) {
+    __shared__ int wsum[32];
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int flag = p < P ? inv[p] : 0;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the warp counts
+        const int nw = (int)(blockDim.x >> 5);
+        int v = (int)lane < nw ? wsum[lane] : 0;
+        const int own = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= (unsigned)off) v += u;
+        }
+        if ((int)lane < nw) wsum[lane] = v - own;
+    }
+    __syncthreads();
+    if (p < P) {
+        if (flag) {
+            const int q = boff[blockIdx.x] + wsum[warp] + __popc(m & ((1u << lane) - 1u));
+            keep[q] = (int)p;
+            inv[p] = q;
+        } else {
+            inv[p] = -1;
+        }
+    }
+}
+
+// dst[row][q] = src[row][keep[q]] for q < *count (rows of length P); a fixed
+// grid (the kept count is known on the device only) strides over q
+template <typename T>
+__global__ void k_pair_gather(const T* __restrict__ src, T* __restrict__ dst, long long P,
+                              const int* __restrict__ keep, const int* __restrict__ count) {
+    const long long n = *count;
+    const size_t row = (size_t)blockIdx.y * P;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x)
+        dst[row + q] = src[row + keep[q]];
+}
+
+// dst[row][p] = src[row][inv[p]], zero for dropped pairs
+template <typename T>
+__global__ void k_pair_scatter(const T* __restrict__ src, T* __restrict__ dst, long long P,
+                               const int* __restrict__ inv) {
+    const size_t row = (size_t)blockIdx.y * P;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int q = inv[p];
+        dst[row + p] = q >= 0 ? src[row + q] : T(0);
+    }
 }
 
 // Output components per block of k_translate: the instantiated width that
@@ -196,6 +348,31 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    // occupied-pair screening: the tree passes run on the kept pairs, whose
+    // leaf multipoles are gathered to the front of each row of scr_o
+    T* Ot = Ob;
+    T* Mt = Mb;
+    const int* pcnt = nullptr;
+    // gather / scatter grid: one row of blocks per leaf component, at most 16
+    // blocks along the pairs
+    const dim3 gpair((unsigned)std::min<long long>((P + 255) / 256, 16), (unsigned)(a.nleaf * nc));
+    if (a.screen) {
+        const int nb = (int)((P + kPairBlk - 1) / kPairBlk);
+        const int ngrp = (a.nleaf + kPairLG - 1) / kPairLG;
+        // the partial norms live in scr_m (idle until the tree passes; it
+        // holds at least nleaf x nc rows of P)
+        T* part = (T*)a.scr_m;
+        const dim3 gpart((unsigned)((P + kPairBlk * kPairPPT - 1) / (kPairBlk * kPairPPT)), (unsigned)ngrp);
+        k_pair_part<T><<<gpart, kPairBlk, 0, s>>>(Ob + (size_t)leaf_store0 * nc * P, a.nleaf, nc, P, part);
+        k_pair_flag<T><<<nb, kPairBlk, 0, s>>>(part, ngrp, P, a.screen_tau2, a.scr_norm, a.scr_inv, a.scr_bcount);
+        k_pair_scan<<<1, 1024, 0, s>>>(a.scr_bcount, nb, a.scr_count);
+        k_pair_compact<<<nb, kPairBlk, 0, s>>>(P, a.scr_bcount, a.scr_keep, a.scr_inv);
+        Ot = (T*)a.scr_o;
+        Mt = (T*)a.scr_m;
+        pcnt = a.scr_count;
+        k_pair_gather<T><<<gpair, 256, 0, s>>>(Ob + (size_t)leaf_store0 * nc * P, Ot + (size_t)leaf_store0 * nc * P,
+                                               P, a.scr_keep, a.scr_count);
+    }
     const int LMC = translate_chunk(nc);
     const int nchunk = (nc + LMC - 1) / LMC;
     const unsigned pblocks = (unsigned)((P + 128 * body::translate_ppt<T>() - 1) / (128 * body::translate_ppt<T>()));
@@ -243,8 +420,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         }
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 0, (int)P, nc, a.L, a.first_box, t0, a.child_ptr,
-                                             a.child_list, a.m2m_op, nullptr, a.parent, tops, Ob, Ob, 0,
-                                             (const int*)nullptr, (const T*)nullptr);
+                                             a.child_list, a.m2m_op, nullptr, a.parent, tops, Ot, Ot, 0,
+                                             (const int*)nullptr, (const T*)nullptr, pcnt);
     }
     // learned ranks: features from the multipoles of every box, FP16 MLP,
     // budgeted choice; M2L then reads the per-edge ranks
@@ -278,14 +455,14 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
             if (nt <= 0) continue;
             dim3 g(nt, pblocks, nchunk);
             launch_translate<T>(LMC, g, s, 3, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
-                                a.m2l_op, lmax_e, a.parent, tops, Ob, Mb, 0, a.l2l_op, (const T*)Mb);
+                                a.m2l_op, lmax_e, a.parent, tops, Ot, Mt, 0, a.l2l_op, (const T*)Mt, pcnt);
         }
     } else {
         int t0 = a.level_off[2], nt = a.nbox - t0;
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 1, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
                                              a.m2l_op, lmax_e, a.parent, tops, Ob, Mb, 0,
-                                             (const int*)nullptr, (const T*)nullptr);
+                                             (const int*)nullptr, (const T*)nullptr, (const int*)nullptr);
     }
     // (d) L2L: children at level lev accumulate their parent's expansion
     mark(4);
@@ -308,8 +485,13 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         dim3 g(nt, pblocks, nchunk);
         launch_translate<T>(LMC, g, s, 2, (int)P, nc, a.L, a.first_box, t0, nullptr, nullptr,
                                              a.l2l_op, nullptr, a.parent, tops, Mb, Mb, 1,
-                                             (const int*)nullptr, (const T*)nullptr);
+                                             (const int*)nullptr, (const T*)nullptr, (const int*)nullptr);
     }
+    // screened: the kept pairs' leaf local expansions back to their places,
+    // zero for the dropped pairs
+    if (a.screen)
+        k_pair_scatter<T><<<gpair, 256, 0, s>>>(Mt + (size_t)leaf_store0 * nc * P, Mb + (size_t)leaf_store0 * nc * P,
+                                                P, a.scr_inv);
     // (e) L2P
     mark(5);
     if (slots) {
@@ -455,19 +637,19 @@ cudaError_t run_farfield_J(const JArgs& a, cudaStream_t s) {
         const int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
         launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 0, 1, nc, a.L, a.first_box, t0, a.child_ptr,
                                  a.child_list, a.m2m_op, nullptr, a.parent, a.ops, Ob, Ob, 0,
-                                 (const int*)nullptr, (const double*)nullptr);
+                                 (const int*)nullptr, (const double*)nullptr, (const int*)nullptr);
     }
     {
         const int t0 = a.level_off[2], nt = a.nbox - t0;
         launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 1, 1, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
                                  a.m2l_op, nullptr, a.parent, a.ops, Ob, Mb, 0, (const int*)nullptr,
-                                 (const double*)nullptr);
+                                 (const double*)nullptr, (const int*)nullptr);
     }
     for (int lev = 3; lev <= D; ++lev) {
         const int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
         launch_translate<double>(LMC, dim3(nt, 1, nchunk), s, 2, 1, nc, a.L, a.first_box, t0, nullptr, nullptr,
                                  a.l2l_op, nullptr, a.parent, a.ops, Mb, Mb, 1, (const int*)nullptr,
-                                 (const double*)nullptr);
+                                 (const double*)nullptr, (const int*)nullptr);
     }
     k_j_l2p<<<a.nleaf, 256, 0, s>>>(a.leaf_rowoff, a.leaf_aos, a.row_ptr, a.ent_col, a.ent_val, a.vals, nc,
                                     Mb + (size_t)leaf_store0 * nc, a.D, a.ldd, a.J, a.ldj, a.part);

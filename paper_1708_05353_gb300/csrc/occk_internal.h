@@ -141,6 +141,10 @@ struct occk_ctx {
     int tr_engine = -1;                     // occk_set_translate_engine mask
     occk::DevBuf sob, smb;                  // slot storage of O~ and Mcal~ (slot pipeline)
     occk::DevBuf jbox;                      // far-field J: density multipoles, local expansions, partials
+    double screen_tau = 0.0;                // occupied-pair screening threshold (0: off)
+    int last_screen = 0;                    // the last occk_farfield_K screened
+    size_t last_screen_P = 0;               // its stored pair count (offset of the kept count)
+    occk::DevBuf scr_o, scr_m, scr_aux;     // compacted pair expansions; norms, keep/inverse maps, count
     int last_slot = 0;                      // last run used the slot pipeline
     int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
     // stage timers
@@ -203,6 +207,11 @@ struct FmmArgs {
     const float* mlp_prm; void* mlp_h; const float* mlp_norm;
     float* feat; float* pred; int* ranks; double* nrm; double tau; int nm2l;
     const int* m2l_tgt; const int* box_key; const int* box_level; const double* hlev;
+    // occupied-pair screening (screen != 0, FP64 and FP32): pairs with
+    // n^2 < screen_tau2 are dropped before M2M; the tree passes run on the
+    // kept pairs, compacted in scr_o / scr_m (same shape as obox / mbox)
+    int screen; double screen_tau2;
+    void* scr_o; void* scr_m; double* scr_norm; int* scr_keep; int* scr_inv; int* scr_count; int* scr_bcount;
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
 // Far-field Coulomb matrix (FP64; kernels_fmm.cu).

@@ -79,6 +79,8 @@ _SIGS = {
     "occk_set_translate_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "occk_set_l2p_split": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_set_pair_screen": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "occk_pair_screen_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "occk_farfield_J": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp,
                                        ctypes.POINTER(ctypes.c_double), _vp]),
     "occk_device_status": (ctypes.c_int, [_vp, _vp]),
@@ -186,6 +188,17 @@ class Context:
     def set_l2p_split(self, nsplit: int = 0):
         """K-range splits of the FP32 SIMT step (e); 0 chooses automatically."""
         self.check(lib().occk_set_l2p_split(self._h, int(nsplit)), "occk_set_l2p_split")
+
+    def set_pair_screen(self, tau: float = 0.0):
+        """Occupied-pair screening threshold for occk_farfield_K (0: off)."""
+        self.check(lib().occk_set_pair_screen(self._h, float(tau)), "occk_set_pair_screen")
+
+    def pair_screen_count(self, stream=None) -> int:
+        """Pairs i <= j kept by the last occk_farfield_K (-1 if it did not screen)."""
+        n = ctypes.c_longlong()
+        self.check(lib().occk_pair_screen_count(self._h, ctypes.byref(n), _stream_ptr(stream)),
+                   "occk_pair_screen_count")
+        return n.value
 
     def set_timing(self, on: bool):
         self.check(lib().occk_set_timing(self._h, 1 if on else 0), "occk_set_timing")

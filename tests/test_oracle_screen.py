@@ -13,6 +13,7 @@ import pytest
 from oracle import fmm
 from oracle import tree as otree
 from paper_1708_05353_gb300 import inputs
+from tests.helpers import tau_in_gap
 
 
 @pytest.fixture(scope="module")
@@ -21,18 +22,6 @@ def loc():
     tr = otree.build_tree(s.basis, s.depth, s.target_atoms_per_leaf)
     K0, E0, parts = fmm.farfield(s, L=3, tree=tr, return_parts=True)
     return s, tr, K0, E0, parts
-
-
-def tau_in_gap(norm2, q):
-    """A threshold between two consecutive distinct pair norms near the
-    q-quantile whose ratio exceeds 1 + 1e-6, so that no pair sits near it."""
-    n = np.unique(np.sqrt(norm2[np.triu_indices(norm2.shape[0], 0, norm2.shape[1])]))
-    k0 = int(q * (len(n) - 1))
-    for d in range(len(n)):
-        for k in (k0 + d, k0 - d):
-            if 0 <= k < len(n) - 1 and n[k + 1] > n[k] * (1 + 1e-6):
-                return float(np.sqrt(n[k] * n[k + 1]))
-    raise ValueError("no gap")
 
 
 def _pair_energies(tr, parts):
