@@ -406,7 +406,8 @@ __device__ __forceinline__ void l2p_body(int bx, int by, int bz, const int* __re
 // reduction), so that short grids still fill the GPU.
 __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit, const int* __restrict__ leaf_rowoff,
                                               const double* __restrict__ W, const double* __restrict__ Mbox,
-                                              int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+                                              int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
+                                              const unsigned char* __restrict__ tflag = nullptr) {
     constexpr int BR = 32, BI = 128, BK = 8, TR = 2, TI = 8;
     __shared__ double As[BK][BR + 1];
     __shared__ double Bs[BK][BI + 1];
@@ -425,6 +426,8 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit
     const int kt0 = (int)((long long)nkt * ks / nsplit), kt1 = (int)((long long)nkt * (ks + 1) / nsplit);
     for (int kt = kt0; kt < kt1; ++kt) {
         const int lm = kt / jt, k0 = (kt - lm * jt) * BK;
+        // screened pairs: skip K steps whose Mcal tile holds no kept pair
+        if (tflag && !tflag[(size_t)by * jt + k0 / 8]) continue;     // uniform across the block
         int l = 0;
         while ((l + 1) * (l + 1) <= lm) ++l;
         const double w = (lm == l * l) ? 2.0 : (((lm - l * l) & 1) ? 4.0 : -4.0);
@@ -486,7 +489,8 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit
 __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nsplit, const int* __restrict__ leaf_rowoff,
                                                 const float* __restrict__ W, const float* __restrict__ Mbox,
                                                 int nocc, int nrow, int nc, int leaf_store0,
-                                                double* __restrict__ KB) {
+                                                double* __restrict__ KB,
+                                                const unsigned char* __restrict__ tflag = nullptr) {
     constexpr int BR = 96, BI = 128, BK = 32, TR = 6, TI = 8;
     __shared__ __align__(16) float As[BK][BR + 4];
     __shared__ __align__(16) float Bs[BK][BI + 4];
@@ -507,8 +511,18 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nspl
     const bool warp_live = r0 + (threadIdx.x >> 5) * 2 * TR < nr;
     const int jt = (nocc + BK - 1) / BK, nkt = nc * jt;
     const int kt0 = (int)((long long)nkt * ks / nsplit), kt1 = (int)((long long)nkt * (ks + 1) / nsplit);
+    const int nj8 = (nocc + 7) / 8;
     for (int kt = kt0; kt < kt1; ++kt) {
         const int lm = kt / jt, k0 = (kt - lm * jt) * BK;
+        if (tflag) {
+            // screened pairs: skip K steps whose Mcal tile holds no kept pair
+            // (flags per 128 orbitals x 8 j; this step covers four)
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < BK / 8; ++u)
+                if (k0 / 8 + u < nj8) any |= tflag[(size_t)by * nj8 + k0 / 8 + u] != 0;
+            if (!any) continue;     // uniform across the block
+        }
         int l = 0;
         while ((l + 1) * (l + 1) <= lm) ++l;
         const float w = (lm == l * l) ? 2.f : (((lm - l * l) & 1) ? 4.f : -4.f);

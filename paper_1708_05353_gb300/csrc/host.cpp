@@ -837,7 +837,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         if (a.learned) return fail(ctx, OCCK_ERR_UNSUPPORTED, "occupied-pair screening with the learned selector");
         if ((e = ensure(ctx->scr_o, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
             (e = ensure(ctx->scr_m, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
-            (e = ensure(ctx->scr_aux, 16 * P + 16 + 4 * ((P + 255) / 256))) != cudaSuccess)
+            (e = ensure(ctx->scr_aux, 16 * P + 16 + 4 * ((P + 255) / 256) + 16 +
+                                          (size_t)((nocc + 127) / 128) * ((nocc + 7) / 8))) != cudaSuccess)
             return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "pair screening workspaces")
                                                   : cuda_fail(ctx, e, "pair screening workspaces");
         char* x = (char*)ctx->scr_aux.p;
@@ -850,6 +851,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.scr_inv = (int*)(x + 12 * P);
         a.scr_count = (int*)(x + 16 * P);
         a.scr_bcount = (int*)(x + 16 * P + 16);
+        a.scr_tiles = (unsigned char*)(x + 16 * P + 16 + 4 * ((P + 255) / 256) + 16);
         ctx->last_screen = 1;
         ctx->last_screen_P = P;
     }

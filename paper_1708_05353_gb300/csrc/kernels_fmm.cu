@@ -67,16 +67,18 @@ k_l2p(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const T* __r
 
 __global__ void __launch_bounds__(256)
 k_l2p_r32(int nsplit, const int* __restrict__ leaf_rowoff, const double* __restrict__ W,
-          const double* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+          const double* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
+          const unsigned char* __restrict__ tflag) {
     body::l2p_rect_body(blockIdx.x, blockIdx.y, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
-                        leaf_store0, KB);
+                        leaf_store0, KB, tflag);
 }
 
 __global__ void __launch_bounds__(256)
 k_l2p_r96f(int nsplit, const int* __restrict__ leaf_rowoff, const float* __restrict__ W,
-           const float* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB) {
+           const float* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
+           const unsigned char* __restrict__ tflag) {
     body::l2p_rect_body_f(blockIdx.x, blockIdx.y, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
-                          leaf_store0, KB);
+                          leaf_store0, KB, tflag);
 }
 
 __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
@@ -233,6 +235,31 @@ k_pair_compact(long long P, const int* __restrict__ boff, int* __restrict__ keep
     }
 }
 
+// Flags of the step (e) tiles that hold a kept pair: tf[i / 128][j / 8] for
+// both orderings of every kept pair (i <= j), so that L2P can skip K steps
+// whose Mcal tile is all dropped pairs.  tf is zeroed before.
+__global__ void k_pair_tiles(const int* __restrict__ keep, const int* __restrict__ count, int nocc,
+                             unsigned char* __restrict__ tf) {
+    const long long n = *count;
+    const int nj8 = (nocc + 7) / 8;
+    const double b = 2.0 * nocc + 1.0;
+    auto off = [&](long long r) { return r * (2LL * nocc - r + 1) / 2; };
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long p = keep[q];
+        // row i of the packed triangle: the largest i with off(i) <= p,
+        // off(i) = i (2 nocc - i + 1) / 2
+        long long i = (long long)((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
+        if (i < 0) i = 0;
+        if (i > nocc - 1) i = nocc - 1;
+        while (i > 0 && off(i) > p) --i;
+        while (i + 1 < nocc && off(i + 1) <= p) ++i;
+        const long long j = i + (p - off(i));
+        tf[(size_t)(i / 128) * nj8 + j / 8] = 1;
+        tf[(size_t)(j / 128) * nj8 + i / 8] = 1;
+    }
+}
+
 // dst[row][q] = src[row][keep[q]] for q < *count (rows of length P); a fixed
 // grid (the kept count is known on the device only) strides over q
 template <typename T>
@@ -367,6 +394,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         k_pair_flag<T><<<nb, kPairBlk, 0, s>>>(part, ngrp, P, a.screen_tau2, a.scr_norm, a.scr_inv, a.scr_bcount);
         k_pair_scan<<<1, 1024, 0, s>>>(a.scr_bcount, nb, a.scr_count);
         k_pair_compact<<<nb, kPairBlk, 0, s>>>(P, a.scr_bcount, a.scr_keep, a.scr_inv);
+        cudaMemsetAsync(a.scr_tiles, 0, (size_t)((nocc + 127) / 128) * ((nocc + 7) / 8), s);
+        k_pair_tiles<<<std::max(1, a.sm_count) * 4, 256, 0, s>>>(a.scr_keep, a.scr_count, nocc, a.scr_tiles);
         Ot = (T*)a.scr_o;
         Mt = (T*)a.scr_m;
         pcnt = a.scr_count;
@@ -509,12 +538,12 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         // 64-row tile would spend a third of the DFMA on padding
         dim3 g((a.max_rows + 31) / 32, (nocc + 127) / 128, a.nleaf * a.l2p_nsplit);
         k_l2p_r32<<<g, 256, 0, s>>>(a.l2p_nsplit, a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow,
-                                    nc, leaf_store0, a.kb);
+                                    nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr);
     } else {
         const int nsplit = a.l2p_nsplit;
         dim3 g((a.max_rows + 95) / 96, (nocc + 127) / 128, a.nleaf * nsplit);
         k_l2p_r96f<<<g, 256, 0, s>>>(nsplit, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
-                                     leaf_store0, a.kb);
+                                     leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr);
     }
     mark(6);
     constexpr int kRedBlocks = kFarfieldPartials;

@@ -212,6 +212,7 @@ struct FmmArgs {
     // kept pairs, compacted in scr_o / scr_m (same shape as obox / mbox)
     int screen; double screen_tau2;
     void* scr_o; void* scr_m; double* scr_norm; int* scr_keep; int* scr_inv; int* scr_count; int* scr_bcount;
+    unsigned char* scr_tiles;        // [nocc/128][nocc/8] step (e) tiles holding a kept pair
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
 // Far-field Coulomb matrix (FP64; kernels_fmm.cu).
