@@ -101,3 +101,16 @@ def test_tree_matches_oracle_chain_auto_depth():
 def test_tree_matches_oracle_full_chain():
     """The 150-carbon chain at full size: same boxes, lists and pair owners."""
     _compare(inputs.alkane(150, lmax=2), depth=0)
+
+
+def test_pair_screen_arguments():
+    """occk_set_pair_screen takes a finite tau >= 0; the kept count is -1 when
+    no screened build has run."""
+    ctx = occk.Context(-1)
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(occk.OcckError) as e:
+            ctx.set_pair_screen(bad)
+        assert e.value.code == -1
+    ctx.set_pair_screen(1e-4)
+    ctx.set_pair_screen(0.0)
+    assert ctx.pair_screen_count(stream=0) == -1
