@@ -519,15 +519,15 @@ def main():
                            "what": "far-field J^ff and E_J on the same tree, D = 2 C C^T"}
     # ---- occupied-pair screening: the same chain and tree with localised
     # occupied orbitals, unscreened and screened, in the main precision
-    if args.screen_tau > 0 and args.workload == "chain" and args.prec in ("fp64", "fp32"):
+    if args.screen_tau > 0 and args.workload == "chain":
         sl = inputs.alkane_localised(args.ncarbon, lmax=L)
         Cl = occk.fortran(torch.tensor(sl.C, dtype=torch.float64, device=dev))
 
-        def timed_loc(tau):
+        def timed_loc(tau, prec):
             ctx.set_pair_screen(tau)
             try:
                 for _ in range(3):
-                    occk.farfield_K(ctx, tree, Cl, prec=args.prec, K=K, Ex=Ex)
+                    occk.farfield_K(ctx, tree, Cl, prec=prec, K=K, Ex=Ex)
                 ev = []
                 nst = max(3, args.steps)
                 st = {k: 0.0 for k in occk.STAGES}
@@ -536,7 +536,7 @@ def main():
                     flush.fill_(float(k))
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     a.record(stream)
-                    occk.farfield_K(ctx, tree, Cl, prec=args.prec, K=K, Ex=Ex)
+                    occk.farfield_K(ctx, tree, Cl, prec=prec, K=K, Ex=Ex)
                     b.record(stream)
                     ev.append((a, b))
                     for n_, v_ in ctx.timings().items():
@@ -549,8 +549,8 @@ def main():
             return (sum(a.elapsed_time(b) for a, b in ev) / len(ev), float(Ex.item()), K.clone(), kept,
                     {k: round(v, 4) for k, v in st.items()})
 
-        ms0, E0, K0, _, st0 = timed_loc(0.0)
-        ms1, E1, K1, kept, st1 = timed_loc(args.screen_tau)
+        ms0, E0, K0, _, st0 = timed_loc(0.0, args.prec)
+        ms1, E1, K1, kept, st1 = timed_loc(args.screen_tau, args.prec)
         npair = system.nocc * (system.nocc + 1) // 2
         result["pair_screen"] = {
             "workload": sl.name + " (same geometry, basis and tree; localised occupied orbitals)",
@@ -562,6 +562,17 @@ def main():
             "abs_dE_Eh": abs(E1 - E0),
             "rel_dK": float((K1 - K0).abs().max().item()) / float(K0.abs().max().item()),
             "dtype": "f64" if args.prec == "fp64" else args.prec}
+        # the split-FP16 tensor-core form on the same localised orbitals,
+        # against the FP64 unscreened energy
+        if args.prec != "fp16x3":
+            E64l = timed_loc(0.0, "fp64")[1]
+            hs0, hE0, _, _, _ = timed_loc(0.0, "fp16x3")
+            hs1, hE1, _, hkept, hst1 = timed_loc(args.screen_tau, "fp16x3")
+            result["pair_screen"]["fp16x3"] = {
+                "ms_unscreened": round(hs0, 4), "ms_screened": round(hs1, 4), "speedup": round(hs0 / hs1, 3),
+                "kept_pairs": hkept, "stage_ms_screened": hst1,
+                "abs_dE_vs_fp64_unscreened_Eh": abs(hE1 - E64l),
+                "abs_dE_unscreened_vs_fp64_Eh": abs(hE0 - E64l)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(system, L, args.cpu_cols)
     if rank == 0:

@@ -331,8 +331,10 @@ occk_status occk_device_status(occk_ctx* ctx, void* stream);
  * norm of pair (i, j) is taken from the stored (min, max) ordering, so both
  * orderings share one decision.
  *   tau  absolute threshold, finite and >= 0; 0 turns screening off (default)
- * Screening runs with OCCK_FP64 and OCCK_FP32 and lmax_policy 0 or 1; other
- * precisions and the learned policy give OCCK_ERR_UNSUPPORTED while tau > 0.
+ * Screening runs with every precision and lmax_policy 0 or 1 (the learned
+ * policy gives OCCK_ERR_UNSUPPORTED while tau > 0); M2M, M2L and L2L then run
+ * on the SIMT translation kernel with unscaled storage, whatever
+ * occk_set_translate_engine selects.
  * With screening on, occk_debug_fetch returns current values for the leaf
  * boxes only.  OCCK_ERR_ARG for a negative, infinite or NaN tau. */
 occk_status occk_set_pair_screen(occk_ctx* ctx, double tau);

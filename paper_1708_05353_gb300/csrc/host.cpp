@@ -827,13 +827,13 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.hlev = d.hlev;
         ctx->ranks_valid = 1;
     }
-    // occupied-pair screening: FP64 and FP32 (unscaled storage, SIMT tree
-    // passes); not with the learned selector, whose features read every box
+    // occupied-pair screening: every precision, with the tree passes on the
+    // SIMT kernel over unscaled storage (the tensor-core translations are
+    // turned off below); not with the learned selector, whose features read
+    // every box
     a.screen = 0;
     ctx->last_screen = 0;
     if (ctx->screen_tau > 0) {
-        if (prec != OCCK_FP64 && prec != OCCK_FP32)
-            return fail(ctx, OCCK_ERR_UNSUPPORTED, "occupied-pair screening runs in FP64 and FP32 only");
         if (a.learned) return fail(ctx, OCCK_ERR_UNSUPPORTED, "occupied-pair screening with the learned selector");
         if ((e = ensure(ctx->scr_o, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
             (e = ensure(ctx->scr_m, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
@@ -1002,7 +1002,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     int max_m2l_edges = 0;
     for (int b = 0; b + 1 < (int)t->m2l_ptr.size(); ++b)
         max_m2l_edges = std::max(max_m2l_edges, t->m2l_ptr[b + 1] - t->m2l_ptr[b]);
-    a.tr_on = (a.tr_pan && a.m2l_lmax == nullptr && !a.learned && max_m2l_edges <= 256) ? 1 : 0;
+    a.tr_on = (a.tr_pan && a.m2l_lmax == nullptr && !a.learned && !a.screen && max_m2l_edges <= 256) ? 1 : 0;
     // which translations go to the tensor core, measured on GB300 (C150H302 at
     // ranks 2, 6, 8 and (H2O)100 at rank 4): from rank 4 on the slot pipeline
     // (all three translations on the tensor core, operands kept in its layout)

@@ -3,7 +3,8 @@ localised orbitals, Sec. IV) through the C ABI against the oracle with the
 same threshold: FP64 K and E within 1e-10 relative, the number of kept pairs
 equal (an integer decision; thresholds sit in a gap of the pair-norm
 distribution, 1e-6 relative wide in FP64 and 1e-4 in FP32, so both sides
-decide every pair the same way), FP32 within 1e-4.  A threshold of zero, or below every norm, is the unscreened method bit
+decide every pair the same way), FP32 within 1e-4, FP16X3 (whose translations
+then run on the SIMT kernel) within 1e-4.  A threshold of zero, or below every norm, is the unscreened method bit
 for bit; a threshold above every norm leaves no far field."""
 import numpy as np
 import pytest
@@ -99,8 +100,16 @@ def test_screen_chain_columns(ctx):
     assert rel_err(K[:, I], Kr) < 1e-10
 
 
-def test_screen_unsupported_precision(ctx, loc):
-    from paper_1708_05353_gb300 import occk
+@pytest.mark.parametrize("q", [0.3, 0.7])
+def test_screen_fp16x3(ctx, loc, q):
+    """The split-FP16 tensor-core form screens too (its tree passes then run on
+    the SIMT kernel): its norms carry the form's ~1e-6 relative error, so the
+    threshold keeps 1e-3 away from every pair; K and E follow the screened
+    oracle within the form's bounds."""
     s, tr, norm2 = loc
-    with pytest.raises(occk.OcckError):
-        _gpu(ctx, s, 3, prec="fp16x3", tau=1e-3)
+    tau = tau_in_gap(norm2, q, gap=1e-3)
+    Kr, Er, p = fmm.farfield(s, L=3, tree=tr, pair_tau=tau, return_parts=True)
+    _, K, E, kept = _gpu(ctx, s, 3, prec="fp16x3", tau=tau)
+    assert kept == int(np.triu(p["keep"]).sum())
+    assert rel_err(K, Kr) < 1e-4
+    assert abs(E - Er) <= 1e-5 * abs(Er)
