@@ -835,10 +835,18 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     ctx->last_screen = 0;
     if (ctx->screen_tau > 0) {
         if (a.learned) return fail(ctx, OCCK_ERR_UNSUPPORTED, "occupied-pair screening with the learned selector");
+        // layout of scr_aux: norms (8P), keep (4P), inverse (4P), count (16),
+        // block counts, step (e) tile flags, bound factors a2 and b2, step (a)
+        // tile flags (64-pair tiles, the finer of the two SIMT tilings)
+        const size_t o_bc = 16 * P + 16, n_bc = 4 * ((P + 255) / 256);
+        const size_t o_tf = o_bc + n_bc + 16, n_tf = (size_t)((nocc + 127) / 128) * ((nocc + 7) / 8);
+        const size_t o_ab = (o_tf + n_tf + 15) / 16 * 16, n_ab = 4 * (size_t)nleaf * nocc;
+        const size_t nt64 = (size_t)(nocc + 63) / 64;
+        const size_t o_ts = o_ab + (1 + (size_t)nc) * n_ab, n_ts = nt64 * (nt64 + 1) / 2;
+        const size_t scr_bytes = o_ts + n_ts + 16;
         if ((e = ensure(ctx->scr_o, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
             (e = ensure(ctx->scr_m, std::max<size_t>(bytes_box, 8))) != cudaSuccess ||
-            (e = ensure(ctx->scr_aux, 16 * P + 16 + 4 * ((P + 255) / 256) + 16 +
-                                          (size_t)((nocc + 127) / 128) * ((nocc + 7) / 8))) != cudaSuccess)
+            (e = ensure(ctx->scr_aux, scr_bytes)) != cudaSuccess)
             return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "pair screening workspaces")
                                                   : cuda_fail(ctx, e, "pair screening workspaces");
         char* x = (char*)ctx->scr_aux.p;
@@ -850,8 +858,11 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.scr_keep = (int*)(x + 8 * P);
         a.scr_inv = (int*)(x + 12 * P);
         a.scr_count = (int*)(x + 16 * P);
-        a.scr_bcount = (int*)(x + 16 * P + 16);
-        a.scr_tiles = (unsigned char*)(x + 16 * P + 16 + 4 * ((P + 255) / 256) + 16);
+        a.scr_bcount = (int*)(x + o_bc);
+        a.scr_tiles = (unsigned char*)(x + o_tf);
+        a.scr_a2 = (float*)(x + o_ab);
+        a.scr_b2 = (float*)(x + o_ab + n_ab);
+        a.scr_tskip = (unsigned char*)(x + o_ts);
         ctx->last_screen = 1;
         ctx->last_screen_P = P;
     }

@@ -38,7 +38,10 @@ __global__ void k_half(const int* __restrict__ row_ptr, const int* __restrict__ 
 template <typename T, int BM, int BK, int TM>
 __global__ void __launch_bounds__((BM / TM) * (BM / TM))
 k_full(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const T* __restrict__ Ct,
-       const T* __restrict__ W, int nocc, int nrow, int nc, int ntile, T* __restrict__ Obox, int leaf_store0) {
+       const T* __restrict__ W, int nocc, int nrow, int nc, int ntile, T* __restrict__ Obox, int leaf_store0,
+       const unsigned char* __restrict__ tskip) {
+    // screened: tiles whose every pair is dropped by the bound are not formed
+    if (tskip && tskip[blockIdx.x]) return;
     body::full_body<T, BM, BK, TM>(blockIdx.x, blockIdx.y, 0, leaf_rowoff, leaf_aos, Ct, W, nocc, nrow, nc, ntile,
                                    Obox, leaf_store0);
 }
@@ -116,6 +119,110 @@ __global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed) {
 // of sum over m = -l..l of |O_lm|^2).  The tree passes then run on the kept
 // pairs, compacted to the front of every [box][lm] row.
 // ---------------------------------------------------------------------------
+// Step (a) tiles that screening drops whole (Cauchy-Schwarz over the leaf's
+// AO rows):  sum_lm w_lm |O^{ij,X}_lm|^2 <= a2[X][i] b2[X][j] with
+// a2[X][i] = sum_{r in S_X} C_ri^2 and b2[X][j] = sum_lm w_lm sum_{r in S_X}
+// W_lm[r][j]^2, so n_ij^2 <= sum_X a2[X][i] b2[X][j].  A tile whose largest
+// bound is below tau^2 / 2 (the half covers the rounding of the bound) holds
+// only pairs that the exact criterion drops; it is not formed.
+// grid (leaf X, 128-orbital chunk, 1 + nc): z = 0 writes a2[X][i], z = 1 +
+// lm writes the component's part of b2, bp[lm][X][j] = w_lm sum_{r in S_X}
+// W_lm[r][j]^2 (summed over lm, in order, by k_bound_tiles).
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_bound_ab(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const T* __restrict__ Ct,
+           const T* __restrict__ W, int nocc, int nrow, int nleaf, float* __restrict__ a2, float* __restrict__ bp) {
+    const int X = blockIdx.x, i = blockIdx.y * blockDim.x + threadIdx.x, z = blockIdx.z;
+    if (i >= nocc) return;
+    const int r0 = leaf_rowoff[X], r1 = leaf_rowoff[X + 1];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (z == 0) {
+        int r = r0;
+        for (; r + 4 <= r1; r += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float c = (float)Ct[(size_t)leaf_aos[r + u] * nocc + i];
+                acc[u] += c * c;
+            }
+        }
+        for (; r < r1; ++r) {
+            const float c = (float)Ct[(size_t)leaf_aos[r] * nocc + i];
+            acc[0] += c * c;
+        }
+        a2[(size_t)X * nocc + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        return;
+    }
+    const int lm = z - 1;
+    int l = 0;
+    while ((l + 1) * (l + 1) <= lm) ++l;
+    const float w = lm == l * l ? 1.f : 2.f;
+    const T* Wl = W + (size_t)lm * nrow * nocc + i;
+    int r = r0;
+    for (; r + 4 <= r1; r += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float x = (float)Wl[(size_t)(r + u) * nocc];
+            acc[u] += x * x;
+        }
+    }
+    for (; r < r1; ++r) {
+        const float x = (float)Wl[(size_t)r * nocc];
+        acc[0] += x * x;
+    }
+    bp[((size_t)lm * nleaf + X) * nocc + i] = w * ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+}
+
+// One block per triangular tile (ti <= tj) of BM x BM pairs in the order of
+// k_full's grid; tskip[t] = 1 when every pair i <= j of the tile has
+// sum_X a2[X][i] b2[X][j] < half_tau2.
+__global__ void __launch_bounds__(256)
+k_bound_tiles(const float* __restrict__ a2, const float* __restrict__ bp, int nleaf, int nc, int nocc, int BM,
+              int ntile, float half_tau2, unsigned char* __restrict__ tskip) {
+    __shared__ float sa[32][128];
+    __shared__ float sb[32][128];
+    __shared__ int any;
+    int t = blockIdx.x, ti = 0;
+    while (t >= ntile - ti) {
+        t -= ntile - ti;
+        ++ti;
+    }
+    const int tj = ti + t;
+    const int i0 = ti * BM, j0 = tj * BM;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    // each thread owns (BM * BM) / 256 pairs of the tile
+    constexpr int kMaxPer = (128 * 128) / 256;
+    const int per = (BM * BM) / 256;
+    float u[kMaxPer];
+    for (int k = 0; k < kMaxPer; ++k) u[k] = 0.f;
+    for (int x0 = 0; x0 < nleaf; x0 += 32) {
+        const int nx = min(32, nleaf - x0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * BM; e += blockDim.x) {
+            const int x = e / BM, c = e % BM;
+            sa[x][c] = (x < nx && i0 + c < nocc) ? a2[(size_t)(x0 + x) * nocc + i0 + c] : 0.f;
+            float b = 0.f;
+            if (x < nx && j0 + c < nocc)
+                for (int lm = 0; lm < nc; ++lm) b += bp[((size_t)lm * nleaf + x0 + x) * nocc + j0 + c];
+            sb[x][c] = b;
+        }
+        __syncthreads();
+        for (int k = 0; k < per; ++k) {
+            const int e = threadIdx.x + 256 * k, ii = e / BM, jj = e % BM;
+            float acc = 0.f;
+            for (int x = 0; x < nx; ++x) acc += sa[x][ii] * sb[x][jj];
+            u[k] += acc;
+        }
+    }
+    for (int k = 0; k < per; ++k) {
+        const int e = threadIdx.x + 256 * k, ii = e / BM, jj = e % BM;
+        const int i = i0 + ii, j = j0 + jj;
+        if (i < nocc && j < nocc && i <= j && u[k] >= half_tau2) any = 1;   // benign race: all write 1
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) tskip[blockIdx.x] = any ? 0 : 1;
+}
+
 // Pass 1a: partial norms over groups of kPairLG leaves, part[g][p], in the
 // storage type.  A block takes 8 x 256 consecutive pairs of one group and
 // walks its leaf-component rows, reading 8 KB contiguous from each.
@@ -161,14 +268,31 @@ k_pair_part(const T* __restrict__ Oleaf, int nleaf, int nc, long long P, T* __re
 template <typename T>
 __global__ void __launch_bounds__(kPairBlk)
 k_pair_flag(const T* __restrict__ part, int ngrp, long long P, double tau2, double* __restrict__ n2,
-            int* __restrict__ inv, int* __restrict__ bcount) {
+            int* __restrict__ inv, int* __restrict__ bcount, const unsigned char* __restrict__ tskip, int nocc,
+            int BM) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int keep = 0;
     if (p < P) {
+        bool formed = true;
+        if (tskip) {
+            // pair (i, j) from its packed index; its step (a) tile (ti, tj)
+            const double b = 2.0 * nocc + 1.0;
+            long long i = (long long)((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
+            auto off = [&](long long r) { return r * (2LL * nocc - r + 1) / 2; };
+            if (i < 0) i = 0;
+            if (i > nocc - 1) i = nocc - 1;
+            while (i > 0 && off(i) > p) --i;
+            while (i + 1 < nocc && off(i + 1) <= p) ++i;
+            const long long j = i + (p - off(i));
+            const int nt = (nocc + BM - 1) / BM, ti = (int)(i / BM), tj = (int)(j / BM);
+            const int t = ti * nt - ti * (ti - 1) / 2 + (tj - ti);
+            formed = !tskip[t];
+        }
         double acc = 0.0;
-        for (int g = 0; g < ngrp; ++g) acc += (double)part[(size_t)g * P + p];
+        if (formed)
+            for (int g = 0; g < ngrp; ++g) acc += (double)part[(size_t)g * P + p];
         n2[p] = acc;
-        keep = acc >= tau2;
+        keep = formed && acc >= tau2;
         inv[p] = keep;
     }
     const int n = __syncthreads_count(keep);
@@ -363,15 +487,29 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     } else if constexpr (sizeof(T) == 8) {
         constexpr int BM = 64, BK = 8, TM = 4;
         int nt = (nocc + BM - 1) / BM;
+        if (a.screen) {
+            k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
+                a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
+            k_bound_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>(a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt,
+                                                             (float)(0.5 * a.screen_tau2), a.scr_tskip);
+        }
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
-                                                                 a.nrow, nc, nt, Ob, leaf_store0);
+                                                                 a.nrow, nc, nt, Ob, leaf_store0,
+                                                                 a.screen ? a.scr_tskip : nullptr);
     } else {
         constexpr int BM = 128, BK = 16, TM = 8;
         int nt = (nocc + BM - 1) / BM;
+        if (a.screen) {
+            k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
+                a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
+            k_bound_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>(a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt,
+                                                             (float)(0.5 * a.screen_tau2), a.scr_tskip);
+        }
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
-                                                                 a.nrow, nc, nt, Ob, leaf_store0);
+                                                                 a.nrow, nc, nt, Ob, leaf_store0,
+                                                                 a.screen ? a.scr_tskip : nullptr);
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -391,7 +529,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         T* part = (T*)a.scr_m;
         const dim3 gpart((unsigned)((P + kPairBlk * kPairPPT - 1) / (kPairBlk * kPairPPT)), (unsigned)ngrp);
         k_pair_part<T><<<gpart, kPairBlk, 0, s>>>(Ob + (size_t)leaf_store0 * nc * P, a.nleaf, nc, P, part);
-        k_pair_flag<T><<<nb, kPairBlk, 0, s>>>(part, ngrp, P, a.screen_tau2, a.scr_norm, a.scr_inv, a.scr_bcount);
+        k_pair_flag<T><<<nb, kPairBlk, 0, s>>>(part, ngrp, P, a.screen_tau2, a.scr_norm, a.scr_inv, a.scr_bcount,
+                                                tcm ? nullptr : a.scr_tskip, nocc, sizeof(T) == 8 ? 64 : 128);
         k_pair_scan<<<1, 1024, 0, s>>>(a.scr_bcount, nb, a.scr_count);
         k_pair_compact<<<nb, kPairBlk, 0, s>>>(P, a.scr_bcount, a.scr_keep, a.scr_inv);
         cudaMemsetAsync(a.scr_tiles, 0, (size_t)((nocc + 127) / 128) * ((nocc + 7) / 8), s);

@@ -213,6 +213,8 @@ struct FmmArgs {
     int screen; double screen_tau2;
     void* scr_o; void* scr_m; double* scr_norm; int* scr_keep; int* scr_inv; int* scr_count; int* scr_bcount;
     unsigned char* scr_tiles;        // [nocc/128][nocc/8] step (e) tiles holding a kept pair
+    float* scr_a2; float* scr_b2;    // bound factors of the SIMT step (a): a2 [nleaf][nocc], b2 parts [nc][nleaf][nocc]
+    unsigned char* scr_tskip;        // step (a) tiles (k_full's triangular order) dropped whole by the bound
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
 // Far-field Coulomb matrix (FP64; kernels_fmm.cu).

@@ -80,3 +80,19 @@ def test_localised_orbitals_screen_well(loc):
     K, E, p = fmm.farfield(s, L=3, tree=tr, pair_tau=1e-3, return_parts=True)
     assert p["keep"].mean() < 0.8
     assert abs(E - E0) < 1e-7
+
+
+def test_cauchy_schwarz_pair_bound(loc):
+    """The bound that lets step (a) skip whole tiles under screening:
+    n_ij^2 <= sum_X a_iX^2 b_jX^2, a_iX^2 = sum_{r in S_X} C_ri^2,
+    b_jX^2 = sum_{l, m} sum_{r in S_X} |O^{rj,X}_lm|^2 (Cauchy-Schwarz over
+    the leaf's AO rows), for every pair, with O^{ij} from the (min, max)
+    ordering as the screening uses it."""
+    s, tr, K0, E0, parts = loc
+    W = parts["W"]
+    _, _, p = fmm.farfield(s, L=3, tree=tr, pair_tau=1.0, return_parts=True)
+    a2 = np.array([np.sum(s.C[S] ** 2, axis=0) for S in tr["ao_sets"]])
+    b2 = np.array([np.sum(np.abs(Wb) ** 2, axis=(0, 1)) for Wb in W])
+    U = a2.T @ b2
+    iu = np.triu_indices(s.nocc)
+    assert np.all(p["norm2"][iu] <= U[iu] * (1 + 1e-12))
