@@ -434,9 +434,9 @@ def main():
             "stage_tflops": {k: round(flops[k] / max(stage_ms[k], 1e-9) / 1e9, 4) for k in flops}}
 
     # transpose, half, full, D-2 M2M, D-1 fused M2L+L2L, L2P, reduction,
-    # energy; screened builds add part, flag, scan, compact, tiles, gather and
-    # scatter
-    nlaunch = 7 + 2 * max(D - 2, 0) + (7 if args.workload == "chain-loc" else 0)
+    # energy; screened FP32/FP64 builds add the two step (a) bound kernels and
+    # part, flag, scan, compact, tiles, gather and scatter
+    nlaunch = 7 + 2 * max(D - 2, 0) + (9 if args.workload == "chain-loc" else 0)
     result = {
         "metric": METRIC,
         "value": job_seconds_per_build(ms_max, world),

@@ -172,55 +172,58 @@ k_bound_ab(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos
     bp[((size_t)lm * nleaf + X) * nocc + i] = w * ((acc[0] + acc[1]) + (acc[2] + acc[3]));
 }
 
-// One block per triangular tile (ti <= tj) of BM x BM pairs in the order of
-// k_full's grid; tskip[t] = 1 when every pair i <= j of the tile has
-// sum_X a2[X][i] b2[X][j] < half_tau2.
+// grid (triangular tile ti <= tj of BM x BM pairs in the order of k_full's
+// grid, slab of 8 rows of the tile): a slab holding a pair i <= j with
+// sum_X a2[X][i] b2[X][j] >= half_tau2 clears tskip[tile] (set to 1 before).
 __global__ void __launch_bounds__(256)
 k_bound_tiles(const float* __restrict__ a2, const float* __restrict__ bp, int nleaf, int nc, int nocc, int BM,
               int ntile, float half_tau2, unsigned char* __restrict__ tskip) {
-    __shared__ float sa[32][128];
+    constexpr int RS = 8;
+    __shared__ float sa[32][RS];
     __shared__ float sb[32][128];
-    __shared__ int any;
     int t = blockIdx.x, ti = 0;
     while (t >= ntile - ti) {
         t -= ntile - ti;
         ++ti;
     }
     const int tj = ti + t;
-    const int i0 = ti * BM, j0 = tj * BM;
-    if (threadIdx.x == 0) any = 0;
-    __syncthreads();
-    // each thread owns (BM * BM) / 256 pairs of the tile
-    constexpr int kMaxPer = (128 * 128) / 256;
-    const int per = (BM * BM) / 256;
-    float u[kMaxPer];
-    for (int k = 0; k < kMaxPer; ++k) u[k] = 0.f;
+    const int i0 = ti * BM + blockIdx.y * RS, j0 = tj * BM;
+    // each thread owns (RS * BM) / 256 pairs of the slab (4 or 2)
+    const int per = (RS * BM) / 256;
+    float u[4] = {0.f, 0.f, 0.f, 0.f};
     for (int x0 = 0; x0 < nleaf; x0 += 32) {
         const int nx = min(32, nleaf - x0);
         __syncthreads();
+        for (int e = threadIdx.x; e < 32 * RS; e += blockDim.x) {
+            const int x = e / RS, c = e % RS;
+            sa[x][c] = (x < nx && i0 + c < nocc) ? a2[(size_t)(x0 + x) * nocc + i0 + c] : 0.f;
+        }
         for (int e = threadIdx.x; e < 32 * BM; e += blockDim.x) {
             const int x = e / BM, c = e % BM;
-            sa[x][c] = (x < nx && i0 + c < nocc) ? a2[(size_t)(x0 + x) * nocc + i0 + c] : 0.f;
             float b = 0.f;
             if (x < nx && j0 + c < nocc)
                 for (int lm = 0; lm < nc; ++lm) b += bp[((size_t)lm * nleaf + x0 + x) * nocc + j0 + c];
             sb[x][c] = b;
         }
         __syncthreads();
-        for (int k = 0; k < per; ++k) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k >= per) break;
             const int e = threadIdx.x + 256 * k, ii = e / BM, jj = e % BM;
             float acc = 0.f;
             for (int x = 0; x < nx; ++x) acc += sa[x][ii] * sb[x][jj];
             u[k] += acc;
         }
     }
-    for (int k = 0; k < per; ++k) {
+    bool hit = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k >= per) break;
         const int e = threadIdx.x + 256 * k, ii = e / BM, jj = e % BM;
         const int i = i0 + ii, j = j0 + jj;
-        if (i < nocc && j < nocc && i <= j && u[k] >= half_tau2) any = 1;   // benign race: all write 1
+        hit |= i < nocc && j < nocc && i <= j && u[k] >= half_tau2;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) tskip[blockIdx.x] = any ? 0 : 1;
+    if (__syncthreads_or(hit) && threadIdx.x == 0) tskip[blockIdx.x] = 0;   // every writer stores 0
 }
 
 // Pass 1a: partial norms over groups of kPairLG leaves, part[g][p], in the
@@ -490,8 +493,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         if (a.screen) {
             k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
                 a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
-            k_bound_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>(a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt,
-                                                             (float)(0.5 * a.screen_tau2), a.scr_tskip);
+            cudaMemsetAsync(a.scr_tskip, 1, (size_t)nt * (nt + 1) / 2, s);
+            k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
+                a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
         }
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
@@ -503,8 +507,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         if (a.screen) {
             k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
                 a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
-            k_bound_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>(a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt,
-                                                             (float)(0.5 * a.screen_tau2), a.scr_tskip);
+            cudaMemsetAsync(a.scr_tskip, 1, (size_t)nt * (nt + 1) / 2, s);
+            k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
+                a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
         }
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
