@@ -60,14 +60,6 @@ k_translate(int mode, int P, int nc, int L, int first_box, int tgt0, const int* 
                                  opidx, lmax_e, parent, ops, in, out, accumulate, l2l_opidx, parent_in, pcount);
 }
 
-template <typename T, int BM, int BK, int TM>
-__global__ void __launch_bounds__((BM / TM) * (BM / TM))
-k_l2p(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const T* __restrict__ Mbox, int nocc, int nrow,
-      int nc, int leaf_store0, double* __restrict__ KB) {
-    body::l2p_body<T, BM, BK, TM>(blockIdx.x, blockIdx.y, blockIdx.z, leaf_rowoff, W, Mbox, nocc, nrow, nc,
-                                  leaf_store0, KB);
-}
-
 __global__ void __launch_bounds__(256)
 k_l2p_r32(int nsplit, const int* __restrict__ leaf_rowoff, const double* __restrict__ W,
           const double* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
