@@ -336,7 +336,10 @@ occk_status occk_device_status(occk_ctx* ctx, void* stream);
  * on the SIMT translation kernel with unscaled storage, whatever
  * occk_set_translate_engine selects.
  * With screening on, occk_debug_fetch returns current values for the leaf
- * boxes only.  OCCK_ERR_ARG for a negative, infinite or NaN tau. */
+ * boxes only: the leaf local expansions of every pair (zero for dropped
+ * pairs), and the leaf multipoles of every pair except, on the FP64 and FP32
+ * paths, those in step (a) tiles skipped because a bound placed every pair
+ * of the tile below tau.  OCCK_ERR_ARG for a negative, infinite or NaN tau. */
 occk_status occk_set_pair_screen(occk_ctx* ctx, double tau);
 
 /* Number of occupied pairs i <= j kept by the last occk_farfield_K call on
