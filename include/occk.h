@@ -192,10 +192,43 @@ occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tree, int nocc,
  * Real form of a rank-L expansion, nc = (L+1)^2 reals: for each l, Re m=0,
  * then (Re, Im) for m = 1..l (components with m < 0 follow from
  * X_{l,-m} = (-1)^m conj X_{lm}).  Levels 0-1 are zero (no M2L there).
- * FP32 runs are widened to double. */
-enum { OCCK_DBG_PAIR_MULT = 0, OCCK_DBG_OBOX = 1, OCCK_DBG_MBOX = 2 };
+ * FP32 runs are widened to double.
+ *   OCCK_DBG_SCREEN_TILES int32 [2]  of a screened call (occk_set_pair_screen):
+ *       {step (a) tiles skipped by the Cauchy-Schwarz bound, step (a) tiles
+ *       the bound examined} (SIMT forms only; {0, 0} for the tensor-core
+ *       forms, which form every tile) */
+enum { OCCK_DBG_PAIR_MULT = 0, OCCK_DBG_OBOX = 1, OCCK_DBG_MBOX = 2, OCCK_DBG_SCREEN_TILES = 3 };
 occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* tree, int what,
                              void* host_out, size_t bytes, void* stream);
+
+/* Occupied column block for sharding one far-field build over several GPUs
+ * (the data-parallel split of the occupied index that the paper's
+ * implementation makes over j batches, Sec. III B, here over blocks of i).
+ * With 0 <= i0 < i1 set, later occk_farfield_K calls on this context compute
+ * K^ff_{r,i} for i0 <= i < i1 only: steps (a)-(d) run on the occupied pairs
+ * (i, j) with i or j in the block (a pair's multipoles do not depend on the
+ * other pairs, so those columns come out bit for bit as in an unblocked
+ * call), step (e) and the K reduction cover the block's columns, the other
+ * columns of K_dev are not written, and Ex_dev / Ex_host receive the block's
+ * part -1/2 sum_{r, i in block} C_ri K_ri.  Gathering the blocks of all ranks
+ * gives the whole K; occk_exchange_energy on it gives E bit for bit as an
+ * unblocked call.  i0 = i1 = 0 turns the block off (default).  i1 > nocc
+ * fails in occk_farfield_K with OCCK_ERR_SHAPE; the learned selector
+ * (lmax_policy 2) is refused with a block (OCCK_ERR_UNSUPPORTED).  The block
+ * uses the workspaces and tree passes of occupied-pair screening (both may be
+ * on together: a pair is then kept if it touches the block and passes the
+ * threshold).  OCCK_ERR_ARG unless i0 = i1 = 0 or 0 <= i0 < i1. */
+occk_status occk_set_column_block(occk_ctx* ctx, int i0, int i1);
+
+/* Exchange energy E = -1/2 sum_ri C_ri K_ri of a stored K (FP64), with the
+ * same reduction order as the energy of occk_farfield_K, so that for the K an
+ * unblocked occk_farfield_K wrote it returns that call's E bit for bit (e.g.
+ * on K gathered from column blocks).  C_dev, K_dev [nao x nocc] column-major
+ * FP64 device (ldc, ldk >= nao); E_dev FP64 device scalar output, written on
+ * `stream`.  Uses the context's reduction workspace (allocated on first use):
+ * order it with the context's other calls (one stream). */
+occk_status occk_exchange_energy(occk_ctx* ctx, int nao, int nocc, const double* C_dev, int ldc,
+                                 const double* K_dev, int ldk, double* E_dev, void* stream);
 
 /* Exchange energy E = -1/2 sum_ri C_ri K_ri from caller buffers, allocating
  * no device memory.  The paper has no counterpart: this entry exists for
@@ -212,11 +245,15 @@ occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* tree, int what,
  *   E_dev FP64 device scalar output, written on `stream`
  * nocc > OCCK_NOALLOC_MAX_OCC fails with OCCK_ERR_SHAPE (and a message in
  * occk_last_error(ctx)); no cudaMalloc, cudaFree or allocating library call is
- * made.  The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the array and each
- * overwrites it: calls that overlap on the GPU race and must be ordered by
- * the caller (e.g. one stream). */
+ * made.  The device address of the array is looked up (cudaGetSymbolAddress,
+ * with the context's device current) on every call made outside stream
+ * capture -- the first such call on a device is its set-up, and a later
+ * device reset leaves no stale address behind; a call made during capture
+ * reuses the address of the last uncaptured call on that device, so make the
+ * first call on a device before any stream capture (OCCK_ERR_STATE
+ * otherwise).  All calls on a device share the array and each overwrites it:
+ * calls that overlap on the GPU race and must be ordered by the caller (e.g.
+ * one stream). */
 #define OCCK_NOALLOC_MAX_OCC 8192
 occk_status occk_exchange_energy_noalloc(occk_ctx* ctx, int nao, int nocc, const double* C_dev, int ldc,
                                          const double* K_dev, int ldk, double* E_dev, void* stream);
@@ -322,6 +359,19 @@ occk_status occk_batch_set_config(occk_batch* batch, const int* cfg);
  * a tensor-core kernel gave up (its results are then invalid), else OK. */
 occk_status occk_device_status(occk_ctx* ctx, void* stream);
 
+/* Test aid for the failure path of the bounded device waits (no paper
+ * counterpart).  Sets how many times the MMA-issuing thread of the
+ * tensor-core panel GEMMs of steps (a) and (e) polls for a stage's operands
+ * before it gives up (polls < 0 restores the default, 2^22; 0 gives up at the
+ * first wait).  A wait that gives up makes the kernel raise its abort flag,
+ * wait (with the default limit) for its own bulk copies and MMAs in flight,
+ * free its TMEM and return; occk_farfield_K then reports OCCK_ERR_TIMEOUT
+ * (when it synchronises) and occk_device_status does too, and the next call
+ * with the default limit is unaffected.  The setting belongs to the device,
+ * not the context: it applies to every context of the process on that device
+ * until changed.  Synchronous. */
+occk_status occk_debug_set_wait_limit(occk_ctx* ctx, long long polls);
+
 /* Occupied-pair screening for localised occupied orbitals (the extension the
  * paper proposes in Sec. IV).  With tau > 0, occk_farfield_K drops every
  * occupied pair (i, j) whose pair-density multipoles are negligible on all
@@ -395,9 +445,12 @@ occk_status occk_debug_tc_gemm(occk_ctx* ctx, int prec, int M, int N, int K, con
                                const float* B, float* D, void* stream);
 
 /* Sustained FMA throughput of this device for one arithmetic (prec =
- * OCCK_FP64 or OCCK_FP32), measured by a dependent-chain FMA kernel over all
- * SMs; *flops receives FLOP/s (2 per FMA).  Synchronises `stream`.  A
- * measurement aid for roofline reporting, not part of the exchange path. */
+ * OCCK_FP64 or OCCK_FP32), measured by a kernel in which every thread updates
+ * 8, 16 or 32 independent accumulators (four FMAs on each per loop trip), at
+ * 4 and 8 resident 256-thread blocks per SM; *flops receives the best rate
+ * seen, in FLOP/s (2 per FMA), at whatever SM clock the device runs.
+ * Synchronises `stream`.  A measurement aid for roofline reporting, not part
+ * of the exchange path. */
 occk_status occk_probe_fma_peak(occk_ctx* ctx, int prec, double* flops, void* stream);
 
 #ifdef __cplusplus

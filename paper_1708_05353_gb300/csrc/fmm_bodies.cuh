@@ -584,14 +584,18 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nspl
 // nsplit copies of KB when step (e) split its K range), in FP64, and the
 // per-block partial of E = -1/2 sum_ri C_ri K_ri.
 // ---------------------------------------------------------------------------
+// With a column block [col0, col1) only those columns are reduced and
+// written (elements x = i * nao + r from col0 * nao on, in the same order).
 static __device__ __forceinline__ void reduce_body(int bx, int by, int bz, const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
                            const double* __restrict__ KB, int nao, int nocc,
                            const double* __restrict__ C, int ldc, double* __restrict__ K, int ldk,
-                           double* __restrict__ part, int nsplit = 1, size_t split_stride = 0) {
+                           double* __restrict__ part, int nsplit = 1, size_t split_stride = 0, int col0 = 0,
+                           int col1 = -1) {
     __shared__ double red[256];
     double e = 0.0;
-    const long long n = (long long)nao * nocc;
-    for (long long x = (long long)bx * blockDim.x + threadIdx.x; x < n;
+    const long long x0 = (long long)nao * col0;
+    const long long n = (long long)nao * (col1 < 0 ? nocc : col1);
+    for (long long x = x0 + (long long)bx * blockDim.x + threadIdx.x; x < n;
          x += (long long)bz * blockDim.x) {
         int i = (int)(x / nao), r = (int)(x - (long long)i * nao);
         double s = 0.0;
@@ -620,6 +624,29 @@ static __global__ void k_final_energy(const double* __restrict__ part, int n, do
         __syncthreads();
     }
     if (threadIdx.x == 0) *E = -0.5 * red[0];
+}
+
+// Per-block partials of E = -1/2 sum_ri C_ri K_ri from a stored K, with the
+// element order, grid and per-thread accumulation of reduce_body (same grid),
+// so that k_final_energy then gives the energy of that K bit for bit as the
+// far-field call would have.
+static __global__ void k_energy_parts(int nao, int nocc, const double* __restrict__ C, int ldc,
+                                      const double* __restrict__ K, int ldk, double* __restrict__ part) {
+    __shared__ double red[256];
+    double e = 0.0;
+    const long long n = (long long)nao * nocc;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(x / nao), r = (int)(x - (long long)i * nao);
+        e += C[(size_t)i * ldc + r] * K[(size_t)i * ldk + r];
+    }
+    red[threadIdx.x] = e;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 static __global__ void k_zero_K(double* K, int ldk, int nao, int nocc, double* E) {

@@ -832,9 +832,21 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     // turned off below); not with the learned selector, whose features read
     // every box
     a.screen = 0;
+    a.col0 = a.col1 = 0;
     ctx->last_screen = 0;
-    if (ctx->screen_tau > 0) {
-        if (a.learned) return fail(ctx, OCCK_ERR_UNSUPPORTED, "occupied-pair screening with the learned selector");
+    const bool colblk = ctx->col_i1 > 0;
+    if (colblk) {
+        if (ctx->col_i1 > nocc)
+            return fail(ctx, OCCK_ERR_SHAPE, "column block [" + std::to_string(ctx->col_i0) + ", " +
+                                                 std::to_string(ctx->col_i1) + ") beyond nocc " +
+                                                 std::to_string(nocc));
+        a.col0 = ctx->col_i0;
+        a.col1 = ctx->col_i1;
+    }
+    if (ctx->screen_tau > 0 || colblk) {
+        if (a.learned)
+            return fail(ctx, OCCK_ERR_UNSUPPORTED,
+                        "occupied-pair screening or a column block with the learned selector");
         // layout of scr_aux: norms (8P), keep (4P), inverse (4P), count (16),
         // block counts, step (e) tile flags, bound factors a2 and b2, step (a)
         // tile flags (64-pair tiles, the finer of the two SIMT tilings)
@@ -851,7 +863,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
                                                   : cuda_fail(ctx, e, "pair screening workspaces");
         char* x = (char*)ctx->scr_aux.p;
         a.screen = 1;
-        a.screen_tau2 = ctx->screen_tau * ctx->screen_tau;
+        a.screen_tau2 = ctx->screen_tau > 0 ? ctx->screen_tau * ctx->screen_tau : 0.0;
         a.scr_o = ctx->scr_o.p;
         a.scr_m = ctx->scr_m.p;
         a.scr_norm = (double*)x;
@@ -865,6 +877,14 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.scr_tskip = (unsigned char*)(x + o_ts);
         ctx->last_screen = 1;
         ctx->last_screen_P = P;
+        // step (a) tiles of the SIMT forms (FP64: 64 x 64, FP32: 128 x 128)
+        // that the bound may skip; the tensor-core forms form every tile
+        ctx->last_tskip_n = 0;
+        ctx->last_tskip = a.scr_tskip;
+        if (prec == OCCK_FP64 || prec == OCCK_FP32) {
+            const size_t bm = prec == OCCK_FP64 ? 64 : 128, nt = (nocc + bm - 1) / bm;
+            ctx->last_tskip_n = nt * (nt + 1) / 2;
+        }
     }
     // panel plan of the tensor-core steps (a) and (e): panel counts per leaf
     if (occk::tc_mode(prec) >= 0) {
@@ -1078,6 +1098,32 @@ extern "C" occk_status occk_set_pair_screen(occk_ctx* ctx, double tau) {
     return OCCK_OK;
 }
 
+extern "C" occk_status occk_set_column_block(occk_ctx* ctx, int i0, int i1) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (i0 == 0 && i1 == 0) {
+        ctx->col_i0 = ctx->col_i1 = 0;
+        return OCCK_OK;
+    }
+    if (i0 < 0 || i1 <= i0) return fail(ctx, OCCK_ERR_ARG, "column block needs 0 <= i0 < i1 (or 0, 0 for off)");
+    ctx->col_i0 = i0;
+    ctx->col_i1 = i1;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_exchange_energy(occk_ctx* ctx, int nao, int nocc, const double* C_dev, int ldc,
+                                            const double* K_dev, int ldk, double* E_dev, void* stream) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device bound to this context");
+    if (!C_dev || !K_dev || !E_dev || nao <= 0 || nocc <= 0)
+        return fail(ctx, OCCK_ERR_ARG, "null buffer or non-positive size");
+    if (ldc < nao || ldk < nao) return fail(ctx, OCCK_ERR_SHAPE, "ldc/ldk < nao");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = ensure(ctx->part, 8 * (size_t)(4096 + 2));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_exchange_energy workspace");
+    e = occk::energy_from_K(nao, nocc, C_dev, ldc, K_dev, ldk, (double*)ctx->part.p, E_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "occk_exchange_energy launch");
+}
+
 extern "C" occk_status occk_pair_screen_count(occk_ctx* ctx, long long* kept, void* stream) {
     if (!ctx || !kept) return fail(ctx, OCCK_ERR_ARG, "null argument");
     *kept = -1;
@@ -1156,6 +1202,19 @@ extern "C" occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* t, int w
         if (bytes != n * 8) return fail(ctx, OCCK_ERR_SHAPE, "size mismatch");
         e = cudaMemcpy(out, t->dev.pair_vals, bytes, cudaMemcpyDeviceToHost);
         return e == cudaSuccess ? OCCK_OK : cuda_fail(ctx, e, "copy");
+    }
+    if (what == OCCK_DBG_SCREEN_TILES) {
+        if (bytes != 2 * sizeof(int)) return fail(ctx, OCCK_ERR_SHAPE, "size mismatch (2 ints)");
+        if (!ctx->last_screen) return fail(ctx, OCCK_ERR_STATE, "the last occk_farfield_K did not screen");
+        std::vector<unsigned char> f(ctx->last_tskip_n);
+        if (!f.empty()) {
+            e = cudaMemcpy(f.data(), ctx->last_tskip, f.size(), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "copy");
+        }
+        int* o = (int*)out;
+        o[0] = (int)std::count(f.begin(), f.end(), (unsigned char)0);
+        o[1] = (int)f.size();
+        return OCCK_OK;
     }
     if (what != OCCK_DBG_OBOX && what != OCCK_DBG_MBOX) return fail(ctx, OCCK_ERR_ARG, "bad what");
     if (ctx->last_tree != t) return fail(ctx, OCCK_ERR_STATE, "last run used another tree");
@@ -1257,6 +1316,15 @@ extern "C" occk_status occk_device_status(occk_ctx* ctx, void* stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_device_status");
     if (werr) return fail(ctx, OCCK_ERR_TIMEOUT, "a tensor-core wait gave up in the last call");
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_debug_set_wait_limit(occk_ctx* ctx, long long polls) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device bound to this context");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = occk::set_mma_wait_limit(polls);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_debug_set_wait_limit");
     return OCCK_OK;
 }
 

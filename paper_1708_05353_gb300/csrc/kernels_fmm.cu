@@ -60,46 +60,52 @@ k_translate(int mode, int P, int nc, int L, int first_box, int tgt0, const int* 
                                  opidx, lmax_e, parent, ops, in, out, accumulate, l2l_opidx, parent_in, pcount);
 }
 
+// grid.y runs over the 128-orbital tiles tile0, tile0 + 1, ... (all of them
+// unless a column block restricts the output columns)
 __global__ void __launch_bounds__(256)
 k_l2p_r32(int nsplit, const int* __restrict__ leaf_rowoff, const double* __restrict__ W,
           const double* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
-          const unsigned char* __restrict__ tflag) {
-    body::l2p_rect_body(blockIdx.x, blockIdx.y, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
+          const unsigned char* __restrict__ tflag, int tile0) {
+    body::l2p_rect_body(blockIdx.x, blockIdx.y + tile0, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
                         leaf_store0, KB, tflag);
 }
 
 __global__ void __launch_bounds__(256)
 k_l2p_r96f(int nsplit, const int* __restrict__ leaf_rowoff, const float* __restrict__ W,
            const float* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
-           const unsigned char* __restrict__ tflag) {
-    body::l2p_rect_body_f(blockIdx.x, blockIdx.y, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
+           const unsigned char* __restrict__ tflag, int tile0) {
+    body::l2p_rect_body_f(blockIdx.x, blockIdx.y + tile0, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
                           leaf_store0, KB, tflag);
 }
 
 __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
                            const double* __restrict__ KB, int nao, int nocc, const double* __restrict__ C, int ldc,
                            double* __restrict__ K, int ldk, double* __restrict__ part, int nsplit,
-                           size_t split_stride) {
+                           size_t split_stride, int col0, int col1) {
     body::reduce_body(blockIdx.x, 0, gridDim.x, ao_row_ptr, ao_rows, KB, nao, nocc, C, ldc, K, ldk, part, nsplit,
-                      split_stride);
+                      split_stride, col0, col1);
 }
 
 // ---------------------------------------------------------------------------
-// FMA throughput probe: 8 independent dependent chains per thread.
-// ---------------------------------------------------------------------------
-template <typename T>
+// FMA throughput probe: NACC independent accumulators per thread, four FMAs
+// on each per loop trip, so neither latency nor loop overhead limits the
+// issue rate; the result is consumed so that nothing is removed.
+template <typename T, int NACC>
 __global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed) {
-    T a[16];
+    T a[NACC];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) a[q] = seed + T(threadIdx.x + q);
+    for (int q = 0; q < NACC; ++q) a[q] = seed + T(threadIdx.x + q) * T(1e-3);
     const T m = T(0.999999), c = T(1e-7);
     for (int k = 0; k < iters; ++k) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) a[q] = a[q] * m + c;
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int q = 0; q < NACC; ++q) a[q] = fma(a[q], m, c);
+        }
     }
     T s = T(0);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) s += a[q];
+    for (int q = 0; q < NACC; ++q) s += a[q];
     if (s == T(-1.2345)) out[threadIdx.x] = s;
 }
 
@@ -218,6 +224,23 @@ k_bound_tiles(const float* __restrict__ a2, const float* __restrict__ bp, int nl
     if (__syncthreads_or(hit) && threadIdx.x == 0) tskip[blockIdx.x] = 0;   // every writer stores 0
 }
 
+// Column block [col0, col1): clears tskip[t] of every step (a) tile (ti <= tj,
+// k_full's triangular order) none of whose rows or columns lies in the block
+// (its pairs touch no column of the block and are dropped anyway).
+__global__ void k_col_tiles(int ntile, int BM, int col0, int col1, unsigned char* __restrict__ tskip) {
+    const int n = ntile * (ntile + 1) / 2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int r = t, ti = 0;
+        while (r >= ntile - ti) {
+            r -= ntile - ti;
+            ++ti;
+        }
+        const int tj = ti + r;
+        auto hits = [&](int tt) { return tt * BM < col1 && (tt + 1) * BM > col0; };
+        if (!hits(ti) && !hits(tj)) tskip[t] = 0;
+    }
+}
+
 // Pass 1a: partial norms over groups of kPairLG leaves, part[g][p], in the
 // storage type.  A block takes 8 x 256 consecutive pairs of one group and
 // walks its leaf-component rows, reading 8 KB contiguous from each.
@@ -260,16 +283,20 @@ k_pair_part(const T* __restrict__ Oleaf, int nleaf, int nc, long long P, T* __re
 // Pass 1b (kPairBlk pairs per block): each pair's norm (the groups summed in
 // order, in FP64) and keep flag (stored in inv as 1 / 0), and the block's
 // count of kept pairs.
+// With a column block [col0, col1) (col1 > col0) a pair is kept only if it
+// touches the block (i or j in it); with ngrp = 0 no norm is read and the
+// threshold tau2 must be 0.
 template <typename T>
 __global__ void __launch_bounds__(kPairBlk)
 k_pair_flag(const T* __restrict__ part, int ngrp, long long P, double tau2, double* __restrict__ n2,
             int* __restrict__ inv, int* __restrict__ bcount, const unsigned char* __restrict__ tskip, int nocc,
-            int BM) {
+            int BM, int col0, int col1) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int keep = 0;
     if (p < P) {
         bool formed = true;
-        if (tskip) {
+        const bool colblk = col1 > col0;
+        if (tskip || colblk) {
             // pair (i, j) from its packed index; its step (a) tile (ti, tj)
             const double b = 2.0 * nocc + 1.0;
             long long i = (long long)((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
@@ -279,9 +306,12 @@ k_pair_flag(const T* __restrict__ part, int ngrp, long long P, double tau2, doub
             while (i > 0 && off(i) > p) --i;
             while (i + 1 < nocc && off(i + 1) <= p) ++i;
             const long long j = i + (p - off(i));
-            const int nt = (nocc + BM - 1) / BM, ti = (int)(i / BM), tj = (int)(j / BM);
-            const int t = ti * nt - ti * (ti - 1) / 2 + (tj - ti);
-            formed = !tskip[t];
+            if (tskip) {
+                const int nt = (nocc + BM - 1) / BM, ti = (int)(i / BM), tj = (int)(j / BM);
+                const int t = ti * nt - ti * (ti - 1) / 2 + (tj - ti);
+                formed = !tskip[t];
+            }
+            if (colblk) formed = formed && ((i >= col0 && i < col1) || (j >= col0 && j < col1));
         }
         double acc = 0.0;
         if (formed)
@@ -430,6 +460,12 @@ void launch_translate(int lmc, dim3 g, cudaStream_t s, Args... args) {
 }
 
 // ---------------------------------------------------------------------------
+// The step (a) tile bound is accumulated in FP32; below about 1e-30 the
+// squares it sums reach FP32's subnormal range, where the 2x margin of the
+// comparison no longer covers the rounding.  Such thresholds form every tile
+// (the exact FP64 criterion then decides every pair alone).
+inline bool bound_usable(double tau2) { return 0.5 * tau2 >= 1e-30; }
+
 template <typename T>
 cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     const int nocc = a.nocc, nc = a.nc, D = a.depth;
@@ -483,11 +519,16 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         constexpr int BM = 64, BK = 8, TM = 4;
         int nt = (nocc + BM - 1) / BM;
         if (a.screen) {
-            k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
-                a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
             cudaMemsetAsync(a.scr_tskip, 1, (size_t)nt * (nt + 1) / 2, s);
-            k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
-                a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
+            if (a.screen_tau2 > 0 && bound_usable(a.screen_tau2)) {
+                k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
+                    a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
+                k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
+                    a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
+            }
+            if (a.col1 > a.col0)
+                k_col_tiles<<<std::max(1, (nt * (nt + 1) / 2 + 255) / 256), 256, 0, s>>>(nt, BM, a.col0, a.col1,
+                                                                                         a.scr_tskip);
         }
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
@@ -497,11 +538,16 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         constexpr int BM = 128, BK = 16, TM = 8;
         int nt = (nocc + BM - 1) / BM;
         if (a.screen) {
-            k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
-                a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
             cudaMemsetAsync(a.scr_tskip, 1, (size_t)nt * (nt + 1) / 2, s);
-            k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
-                a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
+            if (a.screen_tau2 > 0 && bound_usable(a.screen_tau2)) {
+                k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
+                    a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
+                k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
+                    a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
+            }
+            if (a.col1 > a.col0)
+                k_col_tiles<<<std::max(1, (nt * (nt + 1) / 2 + 255) / 256), 256, 0, s>>>(nt, BM, a.col0, a.col1,
+                                                                                         a.scr_tskip);
         }
         dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
         k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
@@ -525,9 +571,13 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         // holds at least nleaf x nc rows of P)
         T* part = (T*)a.scr_m;
         const dim3 gpart((unsigned)((P + kPairBlk * kPairPPT - 1) / (kPairBlk * kPairPPT)), (unsigned)ngrp);
-        k_pair_part<T><<<gpart, kPairBlk, 0, s>>>(Ob + (size_t)leaf_store0 * nc * P, a.nleaf, nc, P, part);
-        k_pair_flag<T><<<nb, kPairBlk, 0, s>>>(part, ngrp, P, a.screen_tau2, a.scr_norm, a.scr_inv, a.scr_bcount,
-                                                tcm ? nullptr : a.scr_tskip, nocc, sizeof(T) == 8 ? 64 : 128);
+        // a column block alone (no threshold) reads no norm
+        const bool norms = a.screen_tau2 > 0;
+        if (norms)
+            k_pair_part<T><<<gpart, kPairBlk, 0, s>>>(Ob + (size_t)leaf_store0 * nc * P, a.nleaf, nc, P, part);
+        k_pair_flag<T><<<nb, kPairBlk, 0, s>>>(part, norms ? ngrp : 0, P, a.screen_tau2, a.scr_norm, a.scr_inv,
+                                                a.scr_bcount, tcm ? nullptr : a.scr_tskip, nocc,
+                                                sizeof(T) == 8 ? 64 : 128, a.col0, a.col1);
         k_pair_scan<<<1, 1024, 0, s>>>(a.scr_bcount, nb, a.scr_count);
         k_pair_compact<<<nb, kPairBlk, 0, s>>>(P, a.scr_bcount, a.scr_keep, a.scr_inv);
         cudaMemsetAsync(a.scr_tiles, 0, (size_t)((nocc + 127) / 128) * ((nocc + 7) / 8), s);
@@ -657,7 +707,10 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     if (a.screen)
         k_pair_scatter<T><<<gpair, 256, 0, s>>>(Mt + (size_t)leaf_store0 * nc * P, Mb + (size_t)leaf_store0 * nc * P,
                                                 P, a.scr_inv);
-    // (e) L2P
+    // (e) L2P: with a column block only the 128-orbital tiles of its columns
+    const bool colblk = a.col1 > a.col0;
+    const int itile0 = colblk ? a.col0 / 128 : 0;
+    const int itile1 = colblk ? (a.col1 + 127) / 128 : (nocc + 127) / 128;
     mark(5);
     if (slots) {
         cudaError_t e2 = tr_slots_unpack(a.prec, nc, a.slot_m, (int)P, ntile, leaf_store0, a.nbox - a.leaf0,
@@ -672,20 +725,21 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     } else if constexpr (sizeof(T) == 8) {
         // 32 AO rows x 128 orbitals per block: leaves hold ~70-600 AOs, and a
         // 64-row tile would spend a third of the DFMA on padding
-        dim3 g((a.max_rows + 31) / 32, (nocc + 127) / 128, a.nleaf * a.l2p_nsplit);
+        dim3 g((a.max_rows + 31) / 32, itile1 - itile0, a.nleaf * a.l2p_nsplit);
         k_l2p_r32<<<g, 256, 0, s>>>(a.l2p_nsplit, a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow,
-                                    nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr);
+                                    nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr, itile0);
     } else {
         const int nsplit = a.l2p_nsplit;
-        dim3 g((a.max_rows + 95) / 96, (nocc + 127) / 128, a.nleaf * nsplit);
+        dim3 g((a.max_rows + 95) / 96, itile1 - itile0, a.nleaf * nsplit);
         k_l2p_r96f<<<g, 256, 0, s>>>(nsplit, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
-                                     leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr);
+                                     leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr, itile0);
     }
     mark(6);
     constexpr int kRedBlocks = kFarfieldPartials;
     const int nsplit = a.l2p_nsplit;
     k_reduce_K<<<kRedBlocks, 256, 0, s>>>(a.ao_row_ptr, a.ao_rows, a.kb, a.nao, nocc, a.C, a.ldc, a.K,
-                                          a.ldk, a.part, nsplit, (size_t)a.nrow * nocc);
+                                          a.ldk, a.part, nsplit, (size_t)a.nrow * nocc, colblk ? a.col0 : 0,
+                                          colblk ? a.col1 : -1);
     k_final_energy<<<1, 256, 0, s>>>(a.part, kRedBlocks, a.Ex_dev);
     mark(OCCK_NSTAGE);
     return cudaGetLastError();
@@ -822,36 +876,56 @@ cudaError_t run_farfield_J(const JArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t energy_from_K(int nao, int nocc, const double* C, int ldc, const double* K, int ldk, double* part,
+                          double* E, cudaStream_t s) {
+    body::k_energy_parts<<<kFarfieldPartials, 256, 0, s>>>(nao, nocc, C, ldc, K, ldk, part);
+    k_final_energy<<<1, 256, 0, s>>>(part, kFarfieldPartials, E);
+    return cudaGetLastError();
+}
+
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s) {
     if (a.prec == OCCK_FP64) return run_typed<double>(a, s);
     return run_typed<float>(a, s);
 }
 
 cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s) {
-    const int iters = 1 << 13;
-    const int blocks = sm_count * 8, threads = 256;
+    // best rate over occupancies (4, 8 blocks of 256 threads per SM) and
+    // accumulator counts (8, 16, 32), each timed three times after one warm-up
     void* buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, 1024 * 8);
     if (e != cudaSuccess) return e;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
-        cudaEventRecord(e0, s);
-        if (prec == OCCK_FP64)
-            k_fma_probe<double><<<blocks, threads, 0, s>>>((double*)buf, iters, 1.0);
-        else
-            k_fma_probe<float><<<blocks, threads, 0, s>>>((float*)buf, iters * 8, 1.0f);
-        cudaEventRecord(e1, s);
-        e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) break;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) best = std::min(best, ms);
+    const int threads = 256;
+    double best_rate = 0.0;
+    for (int bps : {4, 8}) {
+        const int blocks = sm_count * bps;
+        for (int nacc : {8, 16, 32}) {
+            // about 2^27 FMAs per thread-block wave for FP32, 2^21 for FP64
+            const int iters = prec == OCCK_FP64 ? (1 << 12) / (nacc / 8) : (1 << 16) / (nacc / 8);
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                cudaEventRecord(e0, s);
+                if (prec == OCCK_FP64) {
+                    if (nacc == 8) k_fma_probe<double, 8><<<blocks, threads, 0, s>>>((double*)buf, iters, 1.0);
+                    if (nacc == 16) k_fma_probe<double, 16><<<blocks, threads, 0, s>>>((double*)buf, iters, 1.0);
+                    if (nacc == 32) k_fma_probe<double, 32><<<blocks, threads, 0, s>>>((double*)buf, iters, 1.0);
+                } else {
+                    if (nacc == 8) k_fma_probe<float, 8><<<blocks, threads, 0, s>>>((float*)buf, iters, 1.0f);
+                    if (nacc == 16) k_fma_probe<float, 16><<<blocks, threads, 0, s>>>((float*)buf, iters, 1.0f);
+                    if (nacc == 32) k_fma_probe<float, 32><<<blocks, threads, 0, s>>>((float*)buf, iters, 1.0f);
+                }
+                cudaEventRecord(e1, s);
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) break;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double nfma = (double)blocks * threads * nacc * 4.0 * iters;
+                if (rep > 0 && ms > 0) best_rate = std::max(best_rate, 2.0 * nfma / (ms * 1e-3));
+            }
+        }
     }
-    const double nfma = (double)blocks * threads * 16.0 * (prec == OCCK_FP64 ? iters : iters * 8.0);
-    *flops = 2.0 * nfma / (best * 1e-3);
+    *flops = best_rate;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(buf);

@@ -39,6 +39,25 @@ using namespace tc;
 constexpr uint32_t kLBO = 128, kSBO = 1024;
 constexpr int kPart = 128 * 128;                 // bytes of one panel part
 constexpr uint32_t kWait = 1u << 22;
+
+// Polls allowed to the MMA thread's wait for a stage's operands.  kWait in
+// normal use; occk_debug_set_wait_limit lowers it so that a test can make
+// that wait give up and exercise the abort path (the waits of the drain keep
+// kWait).  One value per device, shared by every context in the process.
+__device__ uint32_t g_mma_full_wait = kWait;
+
+// Bounded wait that also gives up as soon as another role has raised *flag
+// (a producer or epilogue waiting for a stage that an aborted MMA thread
+// will never release).
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                                    const int* flag) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(const volatile int*)flag) return false;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
 template <int P>
 struct Q : Fmt<P> {
     static constexpr int BK = 128 / Fmt<P>::esz;
@@ -193,6 +212,7 @@ struct PState {
     uint64_t full[4], empty[4], accf[2], acce[2];
     uint32_t tmem;
     int abort;
+    uint32_t gp, gm;   // stages issued by the producer, consumed by the MMA thread
 };
 
 template <int P>
@@ -242,6 +262,8 @@ __device__ __forceinline__ bool pgemm_tile(const uint8_t* Apanels, const uint8_t
             mbar_init(&st.acce[b], 128);
         }
         st.abort = 0;
+        st.gp = 0;
+        st.gm = 0;
         mbar_fence_init();
     }
     fence_before_sync();
@@ -255,25 +277,27 @@ __device__ __forceinline__ bool pgemm_tile(const uint8_t* Apanels, const uint8_t
         if (lane == 0) {
             for (int kc = 0; kc < nk && !*(volatile int*)&st.abort; ++kc) {
                 const int s = kc % S;
-                if (kc >= S && !mbar_wait_bounded(&st.empty[s], ((kc / S) - 1) & 1, kWait)) {
+                if (kc >= S && !mbar_wait_abortable(&st.empty[s], ((kc / S) - 1) & 1, kWait, &st.abort)) {
                     st.abort = 1;
                     break;
                 }
                 mbar_expect_tx(&st.full[s], 2u * Q<P>::pbytes);
                 bulk_g2s(stageA(s), Apanels + (size_t)kc * Q<P>::pbytes, Q<P>::pbytes, &st.full[s]);
                 bulk_g2s(stageB(s), Bpanels + (size_t)kc * Q<P>::pbytes, Q<P>::pbytes, &st.full[s]);
+                st.gp = (uint32_t)kc + 1;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = instr_desc(128, 128, Q<P>::fmt);
+            const uint32_t full_wait = g_mma_full_wait;
             for (int kc = 0; kc < nk && !*(volatile int*)&st.abort; ++kc) {
                 const int s = kc % S, b = kc & 1;
-                if (!mbar_wait_bounded(&st.full[s], (kc / S) & 1, kWait)) {
+                if (!mbar_wait_bounded(&st.full[s], (kc / S) & 1, full_wait)) {
                     st.abort = 1;
                     break;
                 }
-                if (kc >= 2 && !mbar_wait_bounded(&st.acce[b], ((kc >> 1) - 1) & 1, kWait)) {
+                if (kc >= 2 && !mbar_wait_abortable(&st.acce[b], ((kc >> 1) - 1) & 1, kWait, &st.abort)) {
                     st.abort = 1;
                     break;
                 }
@@ -281,13 +305,18 @@ __device__ __forceinline__ bool pgemm_tile(const uint8_t* Apanels, const uint8_t
                 issue_panel_mmas<P>(stageA(s), stageB(s), tmem + (uint32_t)b * kBuf, idesc);
                 mma_commit(&st.empty[s]);
                 mma_commit(&st.accf[b]);
+                st.gm = (uint32_t)kc + 1;
             }
+            // the last MMAs finish before TMEM is given back
+            const uint32_t gl = st.gm;
+            if (gl > 0) mbar_wait_bounded(&st.accf[(gl - 1) & 1], ((gl - 1) >> 1) & 1, kWait);
         }
     } else {
         const int q4 = warp & 3;   // TMEM lane quarter of this warp
         for (int kc = 0; kc < nk; ++kc) {
             const int b = kc & 1;
-            if (*(volatile int*)&st.abort || !mbar_wait_bounded(&st.accf[b], (kc >> 1) & 1, kWait)) {
+            if (*(volatile int*)&st.abort ||
+                !mbar_wait_abortable(&st.accf[b], (kc >> 1) & 1, kWait, &st.abort)) {
                 st.abort = 1;
                 break;
             }
@@ -313,7 +342,13 @@ __device__ __forceinline__ bool pgemm_tile(const uint8_t* Apanels, const uint8_t
     fence_before_sync();
     __syncthreads();
     const bool ok = !*(volatile int*)&st.abort;
-    if (!ok && t == 0) atomicExch(err_word, 1);
+    if (!ok && t == 0) {
+        atomicExch(err_word, 1);
+        // copies issued but never consumed: wait (bounded) until they land
+        for (uint32_t g = st.gm; g < st.gp; ++g) mbar_wait_bounded(&st.full[g % S], (g / S) & 1, kWait);
+    }
+    __syncthreads();
+    fence_after_sync();
     if (warp == 2) tmem_dealloc(tmem, 2 * kBuf);
     return ok;
 }
@@ -374,7 +409,8 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
                 src(it, A, B, nk);
                 for (int kc = 0; kc < nk; ++kc, ++g) {
                     const int r = (int)(g % S);
-                    if (g >= (uint32_t)S && !mbar_wait_bounded(&st.empty[r], ((g / S) - 1) & 1, kWait)) {
+                    if (g >= (uint32_t)S &&
+                        !mbar_wait_abortable(&st.empty[r], ((g / S) - 1) & 1, kWait, &st.abort)) {
                         st.abort = 1;
                         break;
                     }
@@ -388,6 +424,7 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = instr_desc(128, 128, Q<P>::fmt);
+            const uint32_t full_wait = g_mma_full_wait;
             uint32_t g = 0;
             for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
                 const uint8_t *A, *B;
@@ -395,8 +432,8 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
                 src(it, A, B, nk);
                 for (int kc = 0; kc < nk; ++kc, ++g) {
                     const int r = (int)(g % S), b = (int)(g & 1);
-                    if (!mbar_wait_bounded(&st.full[r], (g / S) & 1, kWait) ||
-                        (g >= 2 && !mbar_wait_bounded(&st.acce[b], ((g >> 1) - 1) & 1, kWait))) {
+                    if (!mbar_wait_bounded(&st.full[r], (g / S) & 1, full_wait) ||
+                        (g >= 2 && !mbar_wait_abortable(&st.acce[b], ((g >> 1) - 1) & 1, kWait, &st.abort))) {
                         st.abort = 1;
                         break;
                     }
@@ -424,7 +461,8 @@ __device__ __forceinline__ void pgemm_persistent(long long nitems, Src src, Epi 
             bool ok = true;
             for (int kc = 0; kc < nk; ++kc, ++g) {
                 const int b = (int)(g & 1);
-                if (*(volatile int*)&st.abort || !mbar_wait_bounded(&st.accf[b], (g >> 1) & 1, kWait)) {
+                if (*(volatile int*)&st.abort ||
+                    !mbar_wait_abortable(&st.accf[b], (g >> 1) & 1, kWait, &st.abort)) {
                     st.abort = 1;
                     ok = false;
                     break;
@@ -716,6 +754,11 @@ int panel_bytes(int prec) {
         case Q_FP16X3: { constexpr int P = Q_FP16X3; return call; }   \
         default: return cudaErrorInvalidValue;                        \
     }
+
+cudaError_t set_mma_wait_limit(long long polls) {
+    const uint32_t v = polls < 0 ? kWait : (uint32_t)std::min<long long>(polls, 0xffffffffLL);
+    return cudaMemcpyToSymbol(g_mma_full_wait, &v, sizeof(v));
+}
 
 cudaError_t panel_l2p(int prec, const PanelArgs& a, cudaStream_t s) { OCCK_Q_DISPATCH(prec, l2p_typed<P>(a, s)); }
 cudaError_t panel_a2(int prec, const PanelArgs& a, cudaStream_t s) { OCCK_Q_DISPATCH(prec, a2_typed<P>(a, s)); }

@@ -82,12 +82,23 @@ extern "C" occk_status occk_exchange_energy_noalloc(occk_ctx* ctx, int nao, int 
         ctx->err = std::string("occk_exchange_energy_noalloc: cudaSetDevice: ") + cudaGetErrorString(e);
         return OCCK_ERR_CUDA;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    // Device address of the static array (the host-side symbol is only a
+    // stand-in, not a device address).  Outside stream capture it is looked up
+    // on every call, with this device current, so a device reset or a new
+    // primary context never leaves a stale address behind; during capture the
+    // address of the last uncaptured call on this device is used, so the first
+    // call on a device must come before any capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("occk_exchange_energy_noalloc: cudaStreamIsCapturing: ") + cudaGetErrorString(e);
+        return OCCK_ERR_CUDA;
+    }
     double* col = nullptr;
     {
-        // First call on this device: resolve the device address of the static
-        // array (the host-side symbol is only a stand-in, not a device address).
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[ctx->device]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_col_energy);
             if (e != cudaSuccess) {
@@ -96,10 +107,13 @@ extern "C" occk_status occk_exchange_energy_noalloc(occk_ctx* ctx, int nao, int 
                 return OCCK_ERR_CUDA;
             }
             g_addr[ctx->device] = static_cast<double*>(p);
+        } else if (!g_addr[ctx->device]) {
+            ctx->err = "occk_exchange_energy_noalloc: first call on this device made during stream capture; "
+                       "call it once outside capture first";
+            return OCCK_ERR_STATE;
         }
         col = g_addr[ctx->device];
     }
-    cudaStream_t s = (cudaStream_t)stream;
     k_col_energy<<<nocc, 256, 0, s>>>(C_dev, ldc, K_dev, ldk, nao, nocc, col);
     k_sum_cols<<<1, 256, 0, s>>>(col, nocc, E_dev);
     e = cudaGetLastError();

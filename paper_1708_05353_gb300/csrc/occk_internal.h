@@ -142,8 +142,11 @@ struct occk_ctx {
     occk::DevBuf sob, smb;                  // slot storage of O~ and Mcal~ (slot pipeline)
     occk::DevBuf jbox;                      // far-field J: density multipoles, local expansions, partials
     double screen_tau = 0.0;                // occupied-pair screening threshold (0: off)
+    int col_i0 = 0, col_i1 = 0;             // occk_set_column_block (col_i1 == 0: off)
     int last_screen = 0;                    // the last occk_farfield_K screened
     size_t last_screen_P = 0;               // its stored pair count (offset of the kept count)
+    size_t last_tskip_n = 0;                // its step (a) bound tiles (SIMT forms; 0 otherwise)
+    const unsigned char* last_tskip = nullptr;   // their flags (0 = tile skipped)
     occk::DevBuf scr_o, scr_m, scr_aux;     // compacted pair expansions; norms, keep/inverse maps, count
     int last_slot = 0;                      // last run used the slot pipeline
     int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
@@ -215,8 +218,16 @@ struct FmmArgs {
     unsigned char* scr_tiles;        // [nocc/128][nocc/8] step (e) tiles holding a kept pair
     float* scr_a2; float* scr_b2;    // bound factors of the SIMT step (a): a2 [nleaf][nocc], b2 parts [nc][nleaf][nocc]
     unsigned char* scr_tskip;        // step (a) tiles (k_full's triangular order) dropped whole by the bound
+    // occupied column block [col0, col1) (col1 > col0; both 0 when unused):
+    // only pairs touching the block are kept (screen != 0), step (e) and the
+    // K reduction cover only the block's columns, Ex_dev gets their part of E
+    int col0, col1;
 };
 cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s);
+// E = -1/2 sum C K from a stored K with the far-field reduction's order
+// (kFarfieldPartials partials in `part`, then one final block).
+cudaError_t energy_from_K(int nao, int nocc, const double* C, int ldc, const double* K, int ldk, double* part,
+                          double* E, cudaStream_t s);
 // Far-field Coulomb matrix (FP64; kernels_fmm.cu).
 struct JArgs {
     int nao, nc, L, depth, nbox, first_box, nleaf, leaf0;
@@ -281,6 +292,9 @@ int panel_elem_bytes(int prec);
 int panel_bytes(int prec);
 cudaError_t panel_l2p(int prec, const PanelArgs& a, cudaStream_t s);
 cudaError_t panel_a2(int prec, const PanelArgs& a, cudaStream_t s);
+// Polls allowed to the MMA thread's operand wait in the panel GEMMs of steps
+// (a) and (e) on the current device (< 0 restores the default 2^22).
+cudaError_t set_mma_wait_limit(long long polls);
 
 // ----- tensor-core translations, steps (b)-(d) (kernels_tc_translate.cu) --------
 struct TrArgs {

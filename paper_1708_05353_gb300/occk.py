@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": OCCK_FP64, "fp32": OCCK_FP32, "tf32": OCCK_TF32, "bf16": O
               "fp16": OCCK_FP16, "bf16x3": OCCK_BF16X3, "fp16x3": OCCK_FP16X3}
 TREE_ARRAYS = {"level_off": 0, "box_key": 1, "parent": 2, "centre": 3, "m2l": 4, "pairs": 5,
                "pair_centre": 6, "leaf_aos": 7, "leaf_rowoff": 8}
-DBG = {"pair_mult": 0, "obox": 1, "mbox": 2}
+DBG = {"pair_mult": 0, "obox": 1, "mbox": 2, "screen_tiles": 3}
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_SHAPE", -3: "ERR_CUDA", -4: "ERR_OOM",
           -5: "ERR_TIMEOUT", -6: "ERR_UNSUPPORTED", -7: "ERR_STATE"}
 
@@ -107,6 +107,10 @@ _SIGS = {
     "occk_exchange_energy_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
                                                     ctypes.c_int, _vp, _vp]),
     "occk_get_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "occk_debug_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+    "occk_set_column_block": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "occk_exchange_energy": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                            ctypes.c_int, _vp, _vp]),
 }
 NSTAGE = 7
 MLP_NIN, MLP_HIDDEN, MLP_NOUT = 16, 64, 8
@@ -193,12 +197,21 @@ class Context:
         """Occupied-pair screening threshold for occk_farfield_K (0: off)."""
         self.check(lib().occk_set_pair_screen(self._h, float(tau)), "occk_set_pair_screen")
 
+    def set_column_block(self, i0: int = 0, i1: int = 0):
+        """Occupied column block [i0, i1) of later far-field calls (0, 0: off)."""
+        self.check(lib().occk_set_column_block(self._h, int(i0), int(i1)), "occk_set_column_block")
+
     def pair_screen_count(self, stream=None) -> int:
         """Pairs i <= j kept by the last occk_farfield_K (-1 if it did not screen)."""
         n = ctypes.c_longlong()
         self.check(lib().occk_pair_screen_count(self._h, ctypes.byref(n), _stream_ptr(stream)),
                    "occk_pair_screen_count")
         return n.value
+
+    def debug_set_wait_limit(self, polls: int = -1):
+        """Polls of the tensor-core GEMMs' operand wait before it gives up
+        (test aid; -1 restores the default).  Applies to the whole device."""
+        self.check(lib().occk_debug_set_wait_limit(self._h, int(polls)), "occk_debug_set_wait_limit")
 
     def set_timing(self, on: bool):
         self.check(lib().occk_set_timing(self._h, 1 if on else 0), "occk_set_timing")
@@ -234,6 +247,7 @@ class Tree:
         self._h = _vp()
         ctx.check(lib().occk_build_tree(ctx._h, ctypes.byref(b), ctypes.byref(p), ctypes.byref(self._h)),
                   "occk_build_tree")
+        self.nao = int(basis.nao)
 
     def close(self):
         if self._h:
@@ -293,6 +307,37 @@ def empty_fortran(nrow, ncol, dtype=None, device=None):
     return torch.empty((ncol, nrow), dtype=dtype or torch.float64, device=device).t()
 
 
+def _is_fortran(t):
+    return t.dim() == 2 and (t.stride(0) == 1 or t.shape[0] == 1) and ld(t) >= max(1, t.shape[0])
+
+
+def _on_ctx_device(ctx, t):
+    return bool(getattr(t, "is_cuda", False)) and ctx.device >= 0 and t.device.index == ctx.device
+
+
+def _check_matrix(ctx, name, t, shape=None, nrow=None, device=True):
+    """Raise OcckError before any library call unless t is a 2-D float64
+    tensor of the expected shape on the context's device (the C ABI receives
+    bare pointers and cannot check any of this)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64:
+        raise OcckError(-1, f"{name} must be a float64 torch tensor, got {getattr(t, 'dtype', type(t))}")
+    if t.dim() != 2 or (shape is not None and tuple(t.shape) != tuple(shape)) or \
+            (nrow is not None and t.shape[0] != nrow) or t.shape[0] < 1 or t.shape[1] < 1:
+        want = shape if shape is not None else (f"[{nrow}, n]" if nrow is not None else "2-D, non-empty")
+        raise OcckError(-2, f"{name} has shape {tuple(t.shape)}, expected {want}")
+    if device and not _on_ctx_device(ctx, t):
+        raise OcckError(-1, f"{name} is on {t.device}, the context is bound to cuda:{ctx.device}")
+
+
+def _check_scalar(ctx, name, t, device=True):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.dim() != 0:
+        raise OcckError(-1, f"{name} must be a 0-d float64 tensor")
+    if device and not _on_ctx_device(ctx, t):
+        raise OcckError(-1, f"{name} is on {t.device}, the context is bound to cuda:{ctx.device}")
+
+
 def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K=None, Ex=None,
                want_energy_host: bool = False, stream=None):
     """occk_farfield_K on torch CUDA tensors.  C: [nao, nocc] float64 (any
@@ -300,10 +345,19 @@ def farfield_K(ctx: Context, tree: Tree, C, prec="fp64", lmax_policy: int = 0, K
     column-major [nao, nocc] and Ex a 0-d device tensor (or a float when
     want_energy_host)."""
     import torch
+    nao = tree.nao
+    for dev in (False, True):          # dtypes and shapes first, then devices
+        _check_matrix(ctx, "C", C, nrow=nao, device=dev)
+        if K is not None:
+            _check_matrix(ctx, "K", K, shape=tuple(C.shape), device=dev)
+        if Ex is not None:
+            _check_scalar(ctx, "Ex", Ex, device=dev)
     C = fortran(C)
-    nao, nocc = C.shape
+    nocc = C.shape[1]
     if K is None:
         K = empty_fortran(nao, nocc, torch.float64, C.device)
+    elif not _is_fortran(K):
+        raise OcckError(-2, "K must be a column-major [nao, nocc] view (see empty_fortran)")
     if Ex is None:
         Ex = torch.empty((), dtype=torch.float64, device=C.device)
     eh = ctypes.c_double()
@@ -321,8 +375,16 @@ def farfield_J(ctx: Context, tree: Tree, D, J=None, Ej=None, want_energy_host: b
     column-major [nao, nao] and Ej a 0-d device tensor (or a float when
     want_energy_host)."""
     import torch
+    nao = tree.nao
+    for dev in (False, True):
+        _check_matrix(ctx, "D", D, shape=(nao, nao), device=dev)
+        if J is not None:
+            _check_matrix(ctx, "J", J, shape=(nao, nao), device=dev)
+        if Ej is not None:
+            _check_scalar(ctx, "Ej", Ej, device=dev)
+    if J is not None and not _is_fortran(J):
+        raise OcckError(-2, "J must be a column-major [nao, nao] view (see empty_fortran)")
     D = fortran(D)
-    nao = D.shape[0]
     if J is None:
         J = empty_fortran(nao, nao, torch.float64, D.device)
     if Ej is None:
@@ -490,12 +552,37 @@ def device_status(ctx: Context, stream=None):
     ctx.check(lib().occk_device_status(ctx._h, _stream_ptr(stream)), "occk_device_status")
 
 
+def exchange_energy(ctx: Context, C, K, E=None, stream=None):
+    """occk_exchange_energy on column-major torch CUDA tensors: -1/2 sum C*K
+    with the reduction order of occk_farfield_K's energy.  Returns E (0-d
+    device tensor)."""
+    import torch
+    for dev in (False, True):
+        _check_matrix(ctx, "C", C, device=dev)
+        _check_matrix(ctx, "K", K, shape=tuple(C.shape), device=dev)
+        if E is not None:
+            _check_scalar(ctx, "E", E, device=dev)
+    C = fortran(C)
+    K = fortran(K)
+    nao, nocc = C.shape
+    if E is None:
+        E = torch.empty((), dtype=torch.float64, device=C.device)
+    ctx.check(lib().occk_exchange_energy(ctx._h, nao, nocc, _vp(C.data_ptr()), ld(C), _vp(K.data_ptr()), ld(K),
+                                         _vp(E.data_ptr()), _stream_ptr(stream)), "occk_exchange_energy")
+    return E
+
+
 def exchange_energy_noalloc(ctx: Context, C, K, E=None, stream=None):
     """occk_exchange_energy_noalloc on column-major torch CUDA tensors: the
     energy -1/2 sum C*K with its scratch in a static device array (the
     library allocates no device memory in this call).  Returns E (0-d device
     tensor; allocate it yourself and pass it in to avoid torch allocating)."""
     import torch
+    for dev in (False, True):
+        _check_matrix(ctx, "C", C, device=dev)
+        _check_matrix(ctx, "K", K, shape=tuple(C.shape), device=dev)
+        if E is not None:
+            _check_scalar(ctx, "E", E, device=dev)
     C = fortran(C)
     K = fortran(K)
     nao, nocc = C.shape
@@ -510,6 +597,11 @@ def exchange_energy_noalloc(ctx: Context, C, K, E=None, stream=None):
 def debug_fetch(ctx: Context, tree: Tree, what: str, nocc: int = 0, stream=None) -> np.ndarray:
     inf = tree.info()
     nc = (inf["lmax"] + 1) ** 2
+    if what == "screen_tiles":
+        out = np.zeros(2, dtype=np.int32)
+        ctx.check(lib().occk_debug_fetch(ctx._h, tree._h, DBG[what], out.ctypes.data_as(_vp), out.nbytes,
+                                         _stream_ptr(stream)), "occk_debug_fetch")
+        return out
     if what == "pair_mult":
         n = None
         # number of value rows: sum over kept pairs of na*nb

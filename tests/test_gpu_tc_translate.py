@@ -1,6 +1,7 @@
 """Tensor-core translations of the mixed forms: M2M, M2L and L2L on tcgen05
-(Eqs. fmm1-3), checked against the FP64 path on the same tree, which the
-parity tests tie to the FP64 oracle.
+(Eqs. fmm1-3), checked against the FP64 path on the same tree and against
+exact K columns of the FP64 oracle (tests/golden/oracle_columns.npz, written
+by tests/golden/make_columns.py from the oracle alone).
 
 Every expansion order that selects a different GEMM width (L = 2, 4, 6, 10:
 N = 16, 32, 64, 128) runs on an alkane chain deep enough for M2M and L2L, with
@@ -11,11 +12,15 @@ same allowance for accumulation over a few hundred terms as for steps (a) and
 (e).  The local expansions of every box are compared too, so an error in one
 translation kind cannot hide behind the others.
 """
+import os
+
 import numpy as np
 import pytest
 
 from paper_1708_05353_gb300 import inputs
 from tests.helpers import rel_err
+
+GOLD = np.load(os.path.join(os.path.dirname(__file__), "golden", "oracle_columns.npz"))
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +77,15 @@ def test_tc_translate_chain(ctx, chain, L, prec, engine):
         ctx.set_translate_engine(7)
     errK = rel_err(K, K64)
     errM = max(rel_err(M[b], M64[b]) for b in range(M.shape[0]) if np.abs(M64[b]).max() > 0)
-    print(f"L={L} {prec} engine {engine}: K {errK:.2e}, Mcal {errM:.2e}, |dE| {abs(E - E64):.2e} (E = {E64:.6f})")
+    cols = GOLD["chain20/cols"]
+    fp = GOLD["chain20/fingerprint"]
+    assert [s.basis.nao, s.nocc, tree.info()["nm2l"]] == [int(fp[0]), int(fp[1]), int(fp[4])]
+    errO = rel_err(K[:, cols], GOLD[f"chain20/L{L}/K"])
+    err64 = rel_err(K64[:, cols], GOLD[f"chain20/L{L}/K"])
+    print(f"L={L} {prec} engine {engine}: K {errK:.2e} (oracle columns {errO:.2e}; FP64 path {err64:.2e}), "
+          f"Mcal {errM:.2e}, |dE| {abs(E - E64):.2e} (E = {E64:.6f})")
+    assert err64 < 1e-10
+    assert errO < K_BOUND[prec]
     assert errK < K_BOUND[prec]
     assert errM < 4 * K_BOUND[prec]
     assert abs(E - E64) <= K_BOUND[prec] * abs(E64)

@@ -1,0 +1,69 @@
+"""The failure path of the bounded device waits, made to run on purpose.
+
+Every wait of the tensor-core kernels on an mbarrier is bounded.  Here the
+MMA-issuing thread of the panel GEMMs (steps (a) and (e) of the mixed forms)
+is allowed zero polls for its operands, so its first wait gives up: the
+kernel raises its abort flag, waits with the normal limit for the bulk copies
+and MMAs it has in flight, frees its TMEM and returns, and the host reads the
+device error word.  Nothing faults, traps or hangs: the wait that gives up is
+one whose copies do land, only later.  The call must report OCCK_ERR_TIMEOUT,
+and the next call with the default limit must give the same K and E as a
+clean run (the context stays usable).
+"""
+import numpy as np
+import pytest
+
+from paper_1708_05353_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_1708_05353_gb300 import occk
+    ctx = occk.Context(0)
+    s = inputs.water(nmol=12, lmax=4)
+    tree = occk.Tree(ctx, s.basis, depth=2)
+    tree.pair_multipoles(4)
+    C = torch.tensor(s.C, dtype=torch.float64, device="cuda:0")
+    yield occk, ctx, tree, s, C
+    ctx.debug_set_wait_limit(-1)
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "tf32"])
+def test_wait_gives_up_then_context_recovers(setup, prec):
+    occk, ctx, tree, s, C = setup
+    K0, E0 = occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
+    K0 = K0.cpu().numpy()
+    ctx.debug_set_wait_limit(0)
+    try:
+        with pytest.raises(occk.OcckError) as e:
+            occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
+        assert e.value.code == -5, str(e.value)
+        with pytest.raises(occk.OcckError) as e2:
+            occk.device_status(ctx)
+        assert e2.value.code == -5
+    finally:
+        ctx.debug_set_wait_limit(-1)
+    K1, E1 = occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
+    occk.device_status(ctx)                     # clean again
+    assert np.array_equal(K1.cpu().numpy(), K0) and E1 == E0
+
+
+def test_debug_gemm_wait_gives_up(setup):
+    occk, ctx, tree, s, C = setup
+    g = torch.Generator(device="cpu").manual_seed(3)
+    A = torch.randn(200, 300, generator=g).float().cuda()
+    B = torch.randn(150, 300, generator=g).float().cuda()
+    ctx.debug_set_wait_limit(0)
+    try:
+        with pytest.raises(occk.OcckError) as e:
+            occk.debug_tc_gemm(ctx, "fp16x3", A, B)
+        assert e.value.code == -5
+    finally:
+        ctx.debug_set_wait_limit(-1)
+    D = occk.debug_tc_gemm(ctx, "fp16x3", A, B)
+    ref = (A.double() @ B.double().T)
+    assert float((D.double() - ref).abs().max() / ref.abs().max()) < 2e-6

@@ -1,8 +1,7 @@
 """The multi-rank host logic of bench.py on CPU with the gloo backend,
-world size 2 (the runs here have one GPU, so N > 1 is replicas only): the
-step time is the maximum over ranks, the whole-job time per K build divides
-it by the number of replicas, and the reference arm does its work on rank 0
-alone."""
+world size 2: the step time is the maximum over ranks, the ranks share one
+K build (column blocks), so the whole-job time per build is the slowest
+rank's step time, and the reference arm does its work on rank 0 alone."""
 import importlib.util
 import io
 import os
@@ -58,7 +57,7 @@ def test_max_over_ranks_gloo_world2():
     got = sorted(q.get() for _ in range(2))
     for rank, m, v in got:
         assert m == 5.0                       # the slower rank's step time
-        assert v == pytest.approx(5.0e-3 / 2)  # two replicas per step
+        assert v == pytest.approx(5.0e-3)     # one shared build per step
 
 
 def test_single_rank_passthrough():
@@ -74,7 +73,6 @@ def test_reference_arm_runs_on_rank0_only():
         lmax = 2
         steps = 1
         warmup = 0
-        cpu_cols = 1
         gpus = 2
         workload = "chain"
         ncarbon = 10
