@@ -451,28 +451,42 @@ def learned_object(args, ctx, dev, system, tm):
     import torch
     from paper_1708_05353_gb300 import learn, occk
     Lr = args.learned_rank
-    tree = occk.Tree(ctx, system.basis, depth=system.depth, target_atoms_per_leaf=system.target_atoms_per_leaf)
-    tree.pair_multipoles(Lr)
-    learn.load(ctx)
-    occk.set_learned_tau(ctx, args.learned_tau)
     C = occk.fortran(torch.tensor(system.C, dtype=torch.float64, device=dev))
     K = occk.empty_fortran(system.basis.nao, system.nocc, torch.float64, dev)
     Ex = torch.empty((), dtype=torch.float64, device=dev)
     out = {"lref": Lr, "tau_Eh": args.learned_tau, "what": (
-        "one build each after one untimed call of the same form; M2L FLOP ratio from the chosen ranks, "
-        "sum_e (L_e+1)^4 vs fixed rank")}
+        "FP64: one build each; split-FP16: one build each after one untimed call; every form on a context "
+        "of its own (the rank-10 workspaces of one form are freed before the next); M2L FLOP ratio from the "
+        "chosen ranks, sum_e (L_e+1)^4 vs fixed rank")}
     res = {}
+    state = {}
 
     def one(prec, policy, warm):
-        ms, st = tm.run(lambda: occk.farfield_K(ctx, tree, C, prec=prec, lmax_policy=policy, K=K, Ex=Ex), 1,
-                        warm=warm, stages=True)
-        torch.cuda.synchronize()
+        # a fresh context and tree per form: FP64 at rank 10 holds ~90 GB of
+        # multipoles and local expansions, the tensor-core form its slots and
+        # panels; one context with both would not fit
+        c2 = occk.Context(ctx.device)
+        tree = occk.Tree(c2, system.basis, depth=system.depth, target_atoms_per_leaf=system.target_atoms_per_leaf)
+        tree.pair_multipoles(Lr)
+        learn.load(c2)
+        occk.set_learned_tau(c2, args.learned_tau)
+        tm2 = Timer(c2, dev)
+        try:
+            ms, st = tm2.run(lambda: occk.farfield_K(c2, tree, C, prec=prec, lmax_policy=policy, K=K, Ex=Ex), 1,
+                             warm=warm, stages=True)
+            torch.cuda.synchronize()
+            state["ranks"] = occk.edge_ranks(c2, tree) if policy == 2 else None
+        finally:
+            del tm2
+            tree.close()
+            c2.close()
+            torch.cuda.empty_cache()
         return ms, float(Ex.item()), st
 
     ms_f, E_f, st_f = one("fp64", 0, 0)
     res["fp64_fixed"] = {"ms": round(ms_f, 2), "E": E_f, "stage_ms": st_f}
     ms_l, E_l, st_l = one("fp64", 2, 0)
-    ranks = occk.edge_ranks(ctx, tree)
+    ranks = state["ranks"]
     nedge = len(ranks)
     cost_l = float(((ranks.astype("float64") + 1) ** 4).sum())
     cost_f = float(nedge * (Lr + 1) ** 4)
@@ -489,7 +503,6 @@ def learned_object(args, ctx, dev, system, tm):
     res["fp16x3_learned"] = {"ms": round(ms_hl, 2), "abs_dE_vs_fixed_fp64_Eh": abs(E_hl - E_f),
                              "speedup_vs_fixed_fp64": round(ms_f / ms_hl, 3), "stage_ms": st_hl}
     out.update(res)
-    tree.close()
     return out
 
 
@@ -621,6 +634,8 @@ def main(argv=None):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    # FMA peak of this GPU, measured now and again after the timed region
+    probe0 = ctx.probe_fma_peak("fp64" if args.prec == "fp64" else "fp32")
 
     # ---- timed region: K steps, L2 flushed before each, events around each
     ctx.set_timing(True)
@@ -686,7 +701,7 @@ def main(argv=None):
         fl["d_l2l"] = 0.0
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     peak_prec = "fp64" if args.prec == "fp64" else "fp32"
-    probe = ctx.probe_fma_peak(peak_prec)
+    probe = max(probe0, ctx.probe_fma_peak(peak_prec))
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     nominal = (1.25e12 * sm_count / 152.0 if peak_prec == "fp64" else sm_count * 128 * 2 * 2.07e9) * sm_mhz / 2070.0
     kernel_names = {"a_half": "k_half", "a_full": "k_full", "b_m2m": "k_translate(M2M)",

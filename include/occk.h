@@ -446,9 +446,10 @@ occk_status occk_debug_tc_gemm(occk_ctx* ctx, int prec, int M, int N, int K, con
 
 /* Sustained FMA throughput of this device for one arithmetic (prec =
  * OCCK_FP64 or OCCK_FP32), measured by a kernel in which every thread updates
- * 8, 16 or 32 independent accumulators (four FMAs on each per loop trip), at
- * 4 and 8 resident 256-thread blocks per SM; *flops receives the best rate
- * seen, in FLOP/s (2 per FMA), at whatever SM clock the device runs.
+ * 8, 16 or 32 independent accumulators (four FMAs on each per loop trip; two
+ * operand patterns: a = a m + c and a = b m + a), at 4 and 8 resident
+ * 256-thread blocks per SM; *flops receives the best rate seen, in FLOP/s (2
+ * per FMA), at whatever SM clock the device runs.
  * Synchronises `stream`.  A measurement aid for roofline reporting, not part
  * of the exchange path. */
 occk_status occk_probe_fma_peak(occk_ctx* ctx, int prec, double* flops, void* stream);

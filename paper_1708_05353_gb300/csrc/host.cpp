@@ -1212,7 +1212,7 @@ extern "C" occk_status occk_debug_fetch(occk_ctx* ctx, const occk_tree* t, int w
             if (e != cudaSuccess) return cuda_fail(ctx, e, "copy");
         }
         int* o = (int*)out;
-        o[0] = (int)std::count(f.begin(), f.end(), (unsigned char)0);
+        o[0] = (int)std::count_if(f.begin(), f.end(), [](unsigned char v) { return v != 0; });
         o[1] = (int)f.size();
         return OCCK_OK;
     }

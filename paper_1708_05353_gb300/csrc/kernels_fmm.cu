@@ -89,24 +89,43 @@ __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __rest
 // ---------------------------------------------------------------------------
 // FMA throughput probe: NACC independent accumulators per thread, four FMAs
 // on each per loop trip, so neither latency nor loop overhead limits the
-// issue rate; the result is consumed so that nothing is removed.
-template <typename T, int NACC>
+// issue rate; the result is consumed so that nothing is removed.  Form 0
+// updates a = a m + c (one shared multiplier and addend), form 1 a = b m + a
+// with a different multiplicand b per accumulator (the operand pattern of a
+// GEMM's inner loop).
+template <typename T, int NACC, int FORM>
 __global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed) {
-    T a[NACC];
+    T a[NACC], b[NACC];
 #pragma unroll
-    for (int q = 0; q < NACC; ++q) a[q] = seed + T(threadIdx.x + q) * T(1e-3);
+    for (int q = 0; q < NACC; ++q) {
+        a[q] = seed + T(threadIdx.x + q) * T(1e-3);
+        b[q] = T(1e-9) * T(q + 1);
+    }
     const T m = T(0.999999), c = T(1e-7);
     for (int k = 0; k < iters; ++k) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
 #pragma unroll
-            for (int q = 0; q < NACC; ++q) a[q] = fma(a[q], m, c);
+            for (int q = 0; q < NACC; ++q) {
+                if constexpr (FORM == 0)
+                    a[q] = fma(a[q], m, c);
+                else
+                    a[q] = fma(b[q], m, a[q]);
+            }
         }
     }
     T s = T(0);
 #pragma unroll
     for (int q = 0; q < NACC; ++q) s += a[q];
     if (s == T(-1.2345)) out[threadIdx.x] = s;
+}
+
+template <typename T, int NACC>
+void launch_probe(int form, int blocks, T* buf, int iters, cudaStream_t s) {
+    if (form == 0)
+        k_fma_probe<T, NACC, 0><<<blocks, 256, 0, s>>>(buf, iters, T(1));
+    else
+        k_fma_probe<T, NACC, 1><<<blocks, 256, 0, s>>>(buf, iters, T(1));
 }
 
 // ---------------------------------------------------------------------------
@@ -224,9 +243,10 @@ k_bound_tiles(const float* __restrict__ a2, const float* __restrict__ bp, int nl
     if (__syncthreads_or(hit) && threadIdx.x == 0) tskip[blockIdx.x] = 0;   // every writer stores 0
 }
 
-// Column block [col0, col1): clears tskip[t] of every step (a) tile (ti <= tj,
-// k_full's triangular order) none of whose rows or columns lies in the block
-// (its pairs touch no column of the block and are dropped anyway).
+// Column block [col0, col1): sets tskip[t] (tile not formed) for every step
+// (a) tile (ti <= tj, k_full's triangular order) none of whose rows or
+// columns lies in the block (its pairs touch no column of the block and are
+// dropped anyway).
 __global__ void k_col_tiles(int ntile, int BM, int col0, int col1, unsigned char* __restrict__ tskip) {
     const int n = ntile * (ntile + 1) / 2;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -237,7 +257,7 @@ __global__ void k_col_tiles(int ntile, int BM, int col0, int col1, unsigned char
         }
         const int tj = ti + r;
         auto hits = [&](int tt) { return tt * BM < col1 && (tt + 1) * BM > col0; };
-        if (!hits(ti) && !hits(tj)) tskip[t] = 0;
+        if (!hits(ti) && !hits(tj)) tskip[t] = 1;
     }
 }
 
@@ -519,8 +539,12 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         constexpr int BM = 64, BK = 8, TM = 4;
         int nt = (nocc + BM - 1) / BM;
         if (a.screen) {
-            cudaMemsetAsync(a.scr_tskip, 1, (size_t)nt * (nt + 1) / 2, s);
-            if (a.screen_tau2 > 0 && bound_usable(a.screen_tau2)) {
+            // tskip[t] = 1: tile t is not formed.  With a usable bound every
+            // tile starts skipped and the bound clears the ones that may hold
+            // a kept pair; otherwise every tile starts formed.
+            const bool bound = a.screen_tau2 > 0 && bound_usable(a.screen_tau2);
+            cudaMemsetAsync(a.scr_tskip, bound ? 1 : 0, (size_t)nt * (nt + 1) / 2, s);
+            if (bound) {
                 k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
                     a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
                 k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
@@ -538,8 +562,12 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         constexpr int BM = 128, BK = 16, TM = 8;
         int nt = (nocc + BM - 1) / BM;
         if (a.screen) {
-            cudaMemsetAsync(a.scr_tskip, 1, (size_t)nt * (nt + 1) / 2, s);
-            if (a.screen_tau2 > 0 && bound_usable(a.screen_tau2)) {
+            // tskip[t] = 1: tile t is not formed.  With a usable bound every
+            // tile starts skipped and the bound clears the ones that may hold
+            // a kept pair; otherwise every tile starts formed.
+            const bool bound = a.screen_tau2 > 0 && bound_usable(a.screen_tau2);
+            cudaMemsetAsync(a.scr_tskip, bound ? 1 : 0, (size_t)nt * (nt + 1) / 2, s);
+            if (bound) {
                 k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
                     a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
                 k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
@@ -889,8 +917,9 @@ cudaError_t run_farfield(const FmmArgs& a, cudaStream_t s) {
 }
 
 cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s) {
-    // best rate over occupancies (4, 8 blocks of 256 threads per SM) and
-    // accumulator counts (8, 16, 32), each timed three times after one warm-up
+    // best rate over the two operand forms, occupancies of 4 and 8 blocks of
+    // 256 threads per SM and 8, 16 or 32 accumulators, each timed three
+    // times after one warm-up
     void* buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, 1024 * 8);
     if (e != cudaSuccess) return e;
@@ -899,29 +928,33 @@ cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s) {
     cudaEventCreate(&e1);
     const int threads = 256;
     double best_rate = 0.0;
-    for (int bps : {4, 8}) {
-        const int blocks = sm_count * bps;
-        for (int nacc : {8, 16, 32}) {
-            // about 2^27 FMAs per thread-block wave for FP32, 2^21 for FP64
-            const int iters = prec == OCCK_FP64 ? (1 << 12) / (nacc / 8) : (1 << 16) / (nacc / 8);
-            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-                cudaEventRecord(e0, s);
-                if (prec == OCCK_FP64) {
-                    if (nacc == 8) k_fma_probe<double, 8><<<blocks, threads, 0, s>>>((double*)buf, iters, 1.0);
-                    if (nacc == 16) k_fma_probe<double, 16><<<blocks, threads, 0, s>>>((double*)buf, iters, 1.0);
-                    if (nacc == 32) k_fma_probe<double, 32><<<blocks, threads, 0, s>>>((double*)buf, iters, 1.0);
-                } else {
-                    if (nacc == 8) k_fma_probe<float, 8><<<blocks, threads, 0, s>>>((float*)buf, iters, 1.0f);
-                    if (nacc == 16) k_fma_probe<float, 16><<<blocks, threads, 0, s>>>((float*)buf, iters, 1.0f);
-                    if (nacc == 32) k_fma_probe<float, 32><<<blocks, threads, 0, s>>>((float*)buf, iters, 1.0f);
+    for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
+        for (int bps : {4, 8}) {
+            const int blocks = sm_count * bps;
+            for (int nacc : {8, 16, 32}) {
+                // about 2^27 FMAs per thread-block wave for FP32, 2^21 for FP64
+                const int iters = prec == OCCK_FP64 ? (1 << 12) / (nacc / 8) : (1 << 16) / (nacc / 8);
+                for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                    cudaEventRecord(e0, s);
+                    if (prec == OCCK_FP64) {
+                        double* b = (double*)buf;
+                        if (nacc == 8) launch_probe<double, 8>(form, blocks, b, iters, s);
+                        if (nacc == 16) launch_probe<double, 16>(form, blocks, b, iters, s);
+                        if (nacc == 32) launch_probe<double, 32>(form, blocks, b, iters, s);
+                    } else {
+                        float* b = (float*)buf;
+                        if (nacc == 8) launch_probe<float, 8>(form, blocks, b, iters, s);
+                        if (nacc == 16) launch_probe<float, 16>(form, blocks, b, iters, s);
+                        if (nacc == 32) launch_probe<float, 32>(form, blocks, b, iters, s);
+                    }
+                    cudaEventRecord(e1, s);
+                    e = cudaEventSynchronize(e1);
+                    if (e != cudaSuccess) break;
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    const double nfma = (double)blocks * threads * nacc * 4.0 * iters;
+                    if (rep > 0 && ms > 0) best_rate = std::max(best_rate, 2.0 * nfma / (ms * 1e-3));
                 }
-                cudaEventRecord(e1, s);
-                e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) break;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                const double nfma = (double)blocks * threads * nacc * 4.0 * iters;
-                if (rep > 0 && ms > 0) best_rate = std::max(best_rate, 2.0 * nfma / (ms * 1e-3));
             }
         }
     }
