@@ -9,6 +9,8 @@
 namespace occk {
 namespace body {
 
+
+
 // Occupied pairs are stored once: p = (i, j) with i <= j, row-major upper
 // triangle (O^{ij} = O^{ji} and Mcal^{ij} = Mcal^{ji}).
 __host__ __device__ __forceinline__ size_t tri_index(int i, int j, int n) {
@@ -131,7 +133,13 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
     const int tj = ti + t;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
     const int i0 = ti * BM, j0 = tj * BM;
-    const int tx = threadIdx.x % (BM / TM), ty = threadIdx.x / (BM / TM);
+    // FP64 (DFMA-bound): a warp owns a stripe of 2 * TM columns over all rows,
+    // so that in a tile whose columns run past nocc the warps holding only
+    // such columns skip their FMAs; FP32 keeps row stripes and 16-byte loads
+    constexpr bool kColWarps = sizeof(T) == 8;
+    const int tx = kColWarps ? threadIdx.x / (BM / TM) : threadIdx.x % (BM / TM);
+    const int ty = kColWarps ? threadIdx.x % (BM / TM) : threadIdx.x / (BM / TM);
+    const bool warp_live = !kColWarps || j0 + ((threadIdx.x >> 5) * 32 / (BM / TM)) * TM < nocc;
     const T* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
     T acc[TM][TM];
 #pragma unroll
@@ -170,6 +178,7 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
     for (int ks = 0; ks < nk; ++ks) {
         const int buf = ks & 1;
         if (ks + 1 < nk) gload((ks + 1) * BK);
+        if (warp_live) {
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             T a[TM], b[TM];
@@ -192,6 +201,7 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
             for (int x = 0; x < TM; ++x)
 #pragma unroll
                 for (int y = 0; y < TM; ++y) acc[x][y] += a[x] * b[y];
+        }
         }
         if (ks + 1 < nk) sstore(buf ^ 1);
         __syncthreads();
@@ -399,21 +409,26 @@ __device__ __forceinline__ void l2p_body(int bx, int by, int bz, const int* __re
     }
 }
 
-// FP64 step (e) with a 32-row x 128-column block tile (thread tile 2 x 8):
-// same sum as l2p_body, less padding on leaves with a few dozen AOs.  Block
-// z = leaf * nsplit + split: the split covers its share of the flattened
-// (lm, j-chunk) range and writes its own copy of KB (summed by the K
-// reduction), so that short grids still fill the GPU.
+// FP64 step (e) with a 32-row x 16 TI-column block tile (thread tile 2 x TI)
+// over the orbitals i0 = 128 by .. i0 + 16 TI - 1: TI = 8 covers a whole
+// 128-orbital tile; TI = 2 covers only the first 32 columns of one, for the
+// last tile when it holds 32 orbitals or fewer (the other 96 columns would
+// be padding that costs DFMAs).  Same sum as l2p_body, less padding on
+// leaves with a few dozen AOs.  Block z = leaf * nsplit + split: the split
+// covers its share of the flattened (lm, j-chunk) range and writes its own
+// copy of KB (summed by the K reduction), so that short grids still fill the
+// GPU.
+template <int TI = 8>
 __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit, const int* __restrict__ leaf_rowoff,
                                               const double* __restrict__ W, const double* __restrict__ Mbox,
                                               int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
                                               const unsigned char* __restrict__ tflag = nullptr) {
-    constexpr int BR = 32, BI = 128, BK = 8, TR = 2, TI = 8;
+    constexpr int BR = 32, BI = 16 * TI, BK = 8, TR = 2;
     __shared__ double As[BK][BR + 1];
     __shared__ double Bs[BK][BI + 1];
     const int B = bz / nsplit, ks = bz % nsplit;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
-    const int r0 = bx * BR, i0 = by * BI;
+    const int r0 = bx * BR, i0 = by * 128;
     if (r0 >= nr) return;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const size_t P = npairs(nocc);

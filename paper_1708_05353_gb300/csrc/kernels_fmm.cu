@@ -62,12 +62,13 @@ k_translate(int mode, int P, int nc, int L, int first_box, int tgt0, const int* 
 
 // grid.y runs over the 128-orbital tiles tile0, tile0 + 1, ... (all of them
 // unless a column block restricts the output columns)
+template <int TI>
 __global__ void __launch_bounds__(256)
 k_l2p_r32(int nsplit, const int* __restrict__ leaf_rowoff, const double* __restrict__ W,
           const double* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
           const unsigned char* __restrict__ tflag, int tile0) {
-    body::l2p_rect_body(blockIdx.x, blockIdx.y + tile0, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
-                        leaf_store0, KB, tflag);
+    body::l2p_rect_body<TI>(blockIdx.x, blockIdx.y + tile0, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow,
+                            nc, leaf_store0, KB, tflag);
 }
 
 __global__ void __launch_bounds__(256)
@@ -93,15 +94,17 @@ __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __rest
 // updates a = a m + c (one shared multiplier and addend), form 1 a = b m + a
 // with a different multiplicand b per accumulator (the operand pattern of a
 // GEMM's inner loop).
+// The multiplier and addend come from device memory (mc[0], mc[1]) so that
+// they sit in registers like a GEMM's operands, not in the constant bank.
 template <typename T, int NACC, int FORM>
-__global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed) {
+__global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed, const T* __restrict__ mc) {
     T a[NACC], b[NACC];
+    const T m = mc[0], c = mc[1];
 #pragma unroll
     for (int q = 0; q < NACC; ++q) {
-        a[q] = seed + T(threadIdx.x + q) * T(1e-3);
-        b[q] = T(1e-9) * T(q + 1);
+        a[q] = seed + T(threadIdx.x + q) * c;
+        b[q] = c * T(q + 1);
     }
-    const T m = T(0.999999), c = T(1e-7);
     for (int k = 0; k < iters; ++k) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -122,10 +125,11 @@ __global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T seed) {
 
 template <typename T, int NACC>
 void launch_probe(int form, int blocks, T* buf, int iters, cudaStream_t s) {
+    const T* mc = buf + 512;
     if (form == 0)
-        k_fma_probe<T, NACC, 0><<<blocks, 256, 0, s>>>(buf, iters, T(1));
+        k_fma_probe<T, NACC, 0><<<blocks, 256, 0, s>>>(buf, iters, T(1), mc);
     else
-        k_fma_probe<T, NACC, 1><<<blocks, 256, 0, s>>>(buf, iters, T(1));
+        k_fma_probe<T, NACC, 1><<<blocks, 256, 0, s>>>(buf, iters, T(1), mc);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,6 +457,36 @@ __global__ void k_pair_scatter(const T* __restrict__ src, T* __restrict__ dst, l
     }
 }
 
+// Components per block of k_half: the instantiated width that leaves the
+// fewest padded components (ties: the wider one, fewer blocks).
+int half_chunk(int nc) {
+    const int cand[] = {25, 16, 9, 4};
+    int best = 16, waste = 1 << 30;
+    for (int c : cand) {
+        const int w = ((nc + c - 1) / c) * c - nc;
+        if (w < waste) {
+            waste = w;
+            best = c;
+        }
+    }
+    return best;
+}
+
+// Threads per block of k_half (a multiple of 32, 64..256): each pass covers
+// threads x jpt orbitals, so the width with the fewest orbitals past nocc in
+// the last pass is chosen (ties: the widest, fewest passes).
+int half_threads(int nocc, int jpt) {
+    int best = 128, waste = 1 << 30;
+    for (int t = 256; t >= 64; t -= 32) {
+        const int per = t * jpt, w = ((nocc + per - 1) / per) * per - nocc;
+        if (w < waste) {
+            waste = w;
+            best = t;
+        }
+    }
+    return best;
+}
+
 // Output components per block of k_translate: the instantiated width that
 // wastes the fewest lanes of the last chunk (rows past nc still cost FMAs).
 int translate_chunk(int nc) {
@@ -511,9 +545,18 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         k_transpose_C<T><<<g, b, 0, s>>>(a.C, a.ldc, a.nao, nocc, Ct);
     }
     {
-        constexpr int LMC = 16;
+        // components per block and threads per block chosen to waste the
+        // fewest FMAs (padded components and orbitals past nocc cost as much
+        // as real ones)
+        const int LMC = half_chunk(nc);
+        const int nth = half_threads(nocc, sizeof(T) == 4 ? 4 : 1);
         dim3 g(a.nrow, (nc + LMC - 1) / LMC);
-        k_half<T, LMC><<<g, 128, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W);
+        switch (LMC) {
+            case 4: k_half<T, 4><<<g, nth, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W); break;
+            case 9: k_half<T, 9><<<g, nth, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W); break;
+            case 25: k_half<T, 25><<<g, nth, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W); break;
+            default: k_half<T, 16><<<g, nth, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W); break;
+        }
     }
     const int leaf_store0 = a.leaf0 - a.first_box;
     const bool tcm = sizeof(T) == 4 && tc_mode(a.prec) >= 0;
@@ -753,9 +796,19 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     } else if constexpr (sizeof(T) == 8) {
         // 32 AO rows x 128 orbitals per block: leaves hold ~70-600 AOs, and a
         // 64-row tile would spend a third of the DFMA on padding
-        dim3 g((a.max_rows + 31) / 32, itile1 - itile0, a.nleaf * a.l2p_nsplit);
-        k_l2p_r32<<<g, 256, 0, s>>>(a.l2p_nsplit, a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc, a.nrow,
-                                    nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr, itile0);
+        // the last 128-orbital tile, when it holds 32 orbitals or fewer, runs
+        // as a 32-column launch of its own (no DFMAs on padded columns)
+        const bool tail = nocc - (itile1 - 1) * 128 <= 32;
+        dim3 g((a.max_rows + 31) / 32, itile1 - itile0 - (tail ? 1 : 0), a.nleaf * a.l2p_nsplit);
+        if (g.y > 0)
+            k_l2p_r32<8><<<g, 256, 0, s>>>(a.l2p_nsplit, a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc,
+                                           a.nrow, nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr, itile0);
+        if (tail) {
+            g.y = 1;
+            k_l2p_r32<2><<<g, 256, 0, s>>>(a.l2p_nsplit, a.leaf_rowoff, (const double*)W, (const double*)Mb, nocc,
+                                           a.nrow, nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr,
+                                           itile1 - 1);
+        }
     } else {
         const int nsplit = a.l2p_nsplit;
         dim3 g((a.max_rows + 95) / 96, itile1 - itile0, a.nleaf * nsplit);
@@ -923,6 +976,17 @@ cudaError_t probe_fma(int prec, int sm_count, double* flops, cudaStream_t s) {
     void* buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, 1024 * 8);
     if (e != cudaSuccess) return e;
+    {
+        // multiplier 0.999999 and addend 1e-7 at element 512 of the buffer
+        const double md[2] = {0.999999, 1e-7};
+        const float mf[2] = {0.999999f, 1e-7f};
+        e = prec == OCCK_FP64 ? cudaMemcpy((double*)buf + 512, md, sizeof(md), cudaMemcpyHostToDevice)
+                              : cudaMemcpy((float*)buf + 512, mf, sizeof(mf), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(buf);
+            return e;
+        }
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
