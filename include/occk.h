@@ -429,6 +429,18 @@ occk_status occk_farfield_J(occk_ctx* ctx, const occk_tree* tree, const double* 
  * 15.  No paper counterpart: an implementation choice. */
 occk_status occk_set_translate_engine(occk_ctx* ctx, int mask);
 
+/* M2L pass of the FP32 SIMT translations (occk_farfield_K with any precision
+ * other than OCCK_FP64 whose translations run on SIMT; ranks 1-3):
+ * mode = 1 runs every level with the sibling-grouped kernel (one block per
+ * parent's children, the union of their interaction lists walked once, so a
+ * source shared by several siblings is read once); 0 runs the per-target
+ * kernel; -1 (default) groups a level when its M2L edges number at least
+ * twice its union sources (3-D clusters).  Both give the same sums in the
+ * same order (bit-identical K).  Ignored with per-edge ranks (lmax_policy 1,
+ * 2).  OCCK_ERR_ARG outside -1..1.  No paper counterpart: an implementation
+ * choice. */
+occk_status occk_set_m2l_group(occk_ctx* ctx, int mode);
+
 /* K-range splits of step (e): each of nsplit blocks of a tile sums a share of
  * the (lm, j) range into its own copy of the per-leaf K rows, which the K
  * reduction adds up (in a fixed order).  nsplit = 0 (default) chooses enough

@@ -68,6 +68,7 @@ void free_tree_device(occk_tree* t) {
     dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.opdesc);
     dfree(d.l2l_op); dfree(d.lscale); dfree(d.box_scale);
     dfree(d.box_key); dfree(d.box_level); dfree(d.hlev); dfree(d.m2l_tgt);
+    dfree(d.grp_child); dfree(d.grp_parent); dfree(d.grp_ptr); dfree(d.grp_src); dfree(d.grp_op);
 }
 
 inline long long ifloor_clamp(double v, long long n) {
@@ -477,6 +478,47 @@ extern "C" occk_status occk_build_tree(occk_ctx* ctx, const occk_basis* bs,
         t->m2l_ptr[a + 1]++;
     }
     for (int b = 0; b < nbox; ++b) t->m2l_ptr[b + 1] += t->m2l_ptr[b];
+    // sibling groups of the M2L pass (levels 2..D): one group per parent
+    t->grp_level_off.assign(D + 2, 0);
+    t->grp_gain.assign(D + 1, 0.0);
+    t->grp_ptr.assign(1, 0);
+    {
+        int ng = 0;
+        for (int lev = 0; lev <= D; ++lev) {
+            if (lev >= 2) t->grp_level_off[lev] = ng;
+            if (lev < 2) continue;
+            std::map<int, std::vector<int>> kids;      // parent -> children, both ascending
+            for (int c = t->level_off[lev]; c < t->level_off[lev + 1]; ++c) kids[t->parent[c]].push_back(c);
+            long long nedge = 0, nunion = 0;
+            for (auto& pk : kids) {
+                std::vector<int> slots(8, -1);
+                std::map<int, std::vector<int>> srcop;   // source -> op per slot
+                const int nk = std::min<int>(8, (int)pk.second.size());
+                for (int k = 0; k < nk; ++k) {
+                    const int c = pk.second[k];
+                    slots[k] = c;
+                    for (int e = t->m2l_ptr[c]; e < t->m2l_ptr[c + 1]; ++e) {
+                        auto& v = srcop[t->m2l_src[e]];
+                        if (v.empty()) v.assign(8, -1);
+                        v[k] = t->m2l_op[e];
+                        ++nedge;
+                    }
+                }
+                for (int k = 0; k < 8; ++k) t->grp_child.push_back(slots[k]);
+                t->grp_parent.push_back(pk.first);
+                for (auto& so : srcop) {
+                    t->grp_src.push_back(so.first);
+                    for (int k = 0; k < 8; ++k) t->grp_op.push_back(so.second[k]);
+                }
+                nunion += (long long)srcop.size();
+                t->grp_ptr.push_back((int)t->grp_src.size());
+                ++ng;
+            }
+            t->grp_gain[lev] = nunion > 0 ? (double)nedge / (double)nunion : 0.0;
+        }
+        t->grp_level_off[D + 1] = ng;
+        if (D < 2) t->grp_level_off.assign(D + 2, 0);
+    }
 
     // ---- device upload
     if (ctx->device >= 0) {
@@ -526,6 +568,13 @@ extern "C" occk_status occk_build_tree(occk_ctx* ctx, const occk_basis* bs,
         if (e == cudaSuccess) e = upload(&d.box_level, level);
         if (e == cudaSuccess) e = upload(&d.hlev, t->h);
         if (e == cudaSuccess) e = upload(&d.m2l_tgt, t->m2l_tgt);
+        if (!t->grp_parent.empty()) {
+            if (e == cudaSuccess) e = upload(&d.grp_child, t->grp_child);
+            if (e == cudaSuccess) e = upload(&d.grp_parent, t->grp_parent);
+            if (e == cudaSuccess) e = upload(&d.grp_ptr, t->grp_ptr);
+            if (e == cudaSuccess && !t->grp_src.empty()) e = upload(&d.grp_src, t->grp_src);
+            if (e == cudaSuccess && !t->grp_op.empty()) e = upload(&d.grp_op, t->grp_op);
+        }
         if (e != cudaSuccess) {
             free_tree_device(t);
             delete t;
@@ -1047,6 +1096,18 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.tr_mask = ctx->tr_engine >= 0 ? ctx->tr_engine : (L >= (split_form ? 6 : 4) ? 15 : 0);
     if (!a.tr_mask) a.tr_on = 0;
     a.ops_scaled = (const float*)ctx->tops.p;
+    // sibling-grouped M2L for the FP32 SIMT translations: a level is grouped
+    // when its children share enough of their interaction lists (M2L edges
+    // per distinct source >= 2, e.g. 3-D clusters; chains share few), or
+    // always / never as occk_set_m2l_group asks
+    a.grp_use = 0;
+    a.grp_level_off = t->grp_level_off.data();
+    a.grp_child = d.grp_child; a.grp_parent = d.grp_parent; a.grp_ptr = d.grp_ptr;
+    a.grp_src = d.grp_src; a.grp_op = d.grp_op;
+    if (prec != OCCK_FP64 && (nc == 4 || nc == 9 || nc == 16) && d.grp_parent && ctx->m2l_group != 0) {
+        for (int lev = 2; lev <= D && lev < 32; ++lev)
+            if (ctx->m2l_group == 1 || t->grp_gain[lev] >= 2.0) a.grp_use |= 1u << lev;
+    }
     // slot pipeline (mask 15): O~ and Mcal~ of every stored box in the tensor
     // core's operand layout between the steps
     a.slot_o = a.slot_m = nullptr;
@@ -1325,6 +1386,13 @@ extern "C" occk_status occk_debug_set_wait_limit(occk_ctx* ctx, long long polls)
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = occk::set_mma_wait_limit(polls);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_debug_set_wait_limit");
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_m2l_group(occk_ctx* ctx, int mode) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (mode < -1 || mode > 1) return fail(ctx, OCCK_ERR_ARG, "m2l group mode must be -1, 0 or 1");
+    ctx->m2l_group = mode;
     return OCCK_OK;
 }
 

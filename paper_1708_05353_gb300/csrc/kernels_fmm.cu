@@ -457,6 +457,115 @@ __global__ void k_pair_scatter(const T* __restrict__ src, T* __restrict__ dst, l
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sibling-grouped M2L fused with L2L (FP32), one level: the same sums as
+// k_translate's mode 3, in the same order.  A block takes one sibling group
+// (the <= 8 children of one parent, one warp each) and 32 * PPW consecutive
+// pairs.  It walks the ascending union of the children's interaction lists:
+// every source's multipoles for the block's pairs are loaded once into
+// shared memory (the next source's prefetched into registers meanwhile) and
+// applied by each warp whose child has that source in its list,
+//   Mcal^{ij}(child) += T(child, src) O^{ij}(src)    (Eqs. fmmex, fmm2),
+// the operator entries read through the read-only cache (the same address
+// for all lanes).  Then, at levels >= 3, the parent's finished local
+// expansion is translated down (Eq. fmm3) and each child is written once.
+// A source shared by several siblings is read once instead of once per
+// edge, which is what limits the per-target pass in 3-D clusters.
+// ---------------------------------------------------------------------------
+template <int NC, int PPW>
+__global__ void __launch_bounds__(256)
+k_m2l_group(int P, const int* __restrict__ pcount, int first_box, int g0, const int* __restrict__ grp_child,
+            const int* __restrict__ grp_parent, const int* __restrict__ grp_ptr, const int* __restrict__ grp_src,
+            const int* __restrict__ grp_op, const int* __restrict__ l2l_op, int do_l2l, const float* __restrict__ ops,
+            const float* __restrict__ in, const float* parent_in, float* out) {
+    constexpr int TP = 32 * PPW;                      // pairs of the block
+    constexpr int PER = (NC * TP + 255) / 256;        // tile elements each thread moves
+    __shared__ float tile[2][NC][TP];
+    const int g = g0 + blockIdx.y;
+    const int pb = blockIdx.x * TP;
+    const int Pl = pcount ? min(P, *pcount) : P;
+    if (pb >= Pl) return;                              // uniform across the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int child = grp_child[g * 8 + warp];
+    float acc[NC][PPW];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int p = 0; p < PPW; ++p) acc[c][p] = 0.f;
+    float pre[PER];
+    auto gload = [&](const float* base, int box) {
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int e = threadIdx.x + 256 * m;
+            const int c = e / TP, p = e - c * TP;
+            pre[m] = (e < NC * TP && pb + p < Pl) ? base[((size_t)(box - first_box) * NC + c) * P + pb + p] : 0.f;
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int e = threadIdx.x + 256 * m;
+            const int c = e / TP, p = e - c * TP;
+            if (e < NC * TP) tile[buf][c][p] = pre[m];
+        }
+    };
+    auto apply = [&](int buf, int op) {                // warp-uniform op >= 0
+        const float* T = ops + (size_t)op * NC * NC;
+#pragma unroll
+        for (int ci = 0; ci < NC; ++ci) {
+            float v[PPW];
+#pragma unroll
+            for (int p = 0; p < PPW; ++p) v[p] = tile[buf][ci][lane + 32 * p];
+#pragma unroll
+            for (int co = 0; co < NC; ++co) {
+                const float w = __ldg(T + co * NC + ci);
+#pragma unroll
+                for (int p = 0; p < PPW; ++p) acc[co][p] += w * v[p];
+            }
+        }
+    };
+    const int s0 = grp_ptr[g], s1 = grp_ptr[g + 1];
+    if (s0 < s1) {
+        gload(in, grp_src[s0]);
+        sstore(0);
+    }
+    __syncthreads();
+    for (int x = s0; x < s1; ++x) {
+        const int buf = (x - s0) & 1;
+        if (x + 1 < s1) gload(in, grp_src[x + 1]);
+        const int op = child >= 0 ? grp_op[(size_t)x * 8 + warp] : -1;
+        if (op >= 0) apply(buf, op);
+        if (x + 1 < s1) sstore(buf ^ 1);
+        __syncthreads();
+    }
+    if (do_l2l) {
+        const int buf = (s1 - s0) & 1;
+        gload(parent_in, grp_parent[g]);
+        sstore(buf);
+        __syncthreads();
+        if (child >= 0) apply(buf, l2l_op[child]);
+    }
+    if (child < 0) return;
+#pragma unroll
+    for (int co = 0; co < NC; ++co)
+#pragma unroll
+        for (int p = 0; p < PPW; ++p) {
+            const int q = pb + lane + 32 * p;
+            if (q < Pl) out[((size_t)(child - first_box) * NC + co) * P + q] = acc[co][p];
+        }
+}
+
+template <int NC, int PPW>
+void launch_m2l_group(const FmmArgs& a, int lev, int P, const int* pcount, const float* ops, const float* in,
+                      float* out, cudaStream_t s) {
+    constexpr int TP = 32 * PPW;
+    const int g0 = a.grp_level_off[lev], ng = a.grp_level_off[lev + 1] - g0;
+    if (ng <= 0) return;
+    dim3 g((P + TP - 1) / TP, ng);
+    k_m2l_group<NC, PPW><<<g, 256, 0, s>>>(P, pcount, a.first_box, g0, a.grp_child, a.grp_parent, a.grp_ptr,
+                                          a.grp_src, a.grp_op, a.l2l_op, lev >= 3 ? 1 : 0, ops, in, out, out);
+}
+
 // Components per block of k_half: the instantiated width that leaves the
 // fewest padded components (ties: the wider one, fewer blocks).
 int half_chunk(int nc) {
@@ -739,6 +848,18 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         for (int lev = 2; lev <= D; ++lev) {
             int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
             if (nt <= 0) continue;
+            if constexpr (sizeof(T) == 4) {
+                if (((a.grp_use >> lev) & 1u) && lmax_e == nullptr) {
+                    const float* fo = (const float*)tops;
+                    if (nc == 9)
+                        launch_m2l_group<9, 4>(a, lev, (int)P, pcnt, fo, (const float*)Ot, (float*)Mt, s);
+                    else if (nc == 16)
+                        launch_m2l_group<16, 2>(a, lev, (int)P, pcnt, fo, (const float*)Ot, (float*)Mt, s);
+                    else
+                        launch_m2l_group<4, 4>(a, lev, (int)P, pcnt, fo, (const float*)Ot, (float*)Mt, s);
+                    continue;
+                }
+            }
             dim3 g(nt, pblocks, nchunk);
             launch_translate<T>(LMC, g, s, 3, (int)P, nc, a.L, a.first_box, t0, a.m2l_ptr, a.m2l_src,
                                 a.m2l_op, lmax_e, a.parent, tops, Ot, Mt, 0, a.l2l_op, (const T*)Mt, pcnt);

@@ -82,6 +82,18 @@ struct occk_tree {
     std::vector<int> m2l_ptr;               // [nbox+1]
     std::vector<int> edge_lmax;             // per M2L edge (policy 1), empty if unset
     int lmax = -1;
+    // sibling groups of the M2L pass: the boxes of each level 2..D grouped by
+    // parent (groups in parent order, children in box order, at most 8); per
+    // group the ascending union of its children's interaction lists with the
+    // operator of each (child slot, source) edge, -1 where the source is not
+    // in that child's list
+    std::vector<int> grp_level_off;         // [depth+2]: first group of level l (l = 2..D+1)
+    std::vector<int> grp_child;             // [ngroup*8], -1 for unused slots
+    std::vector<int> grp_parent;            // [ngroup]
+    std::vector<int> grp_ptr;               // [ngroup+1] into grp_src
+    std::vector<int> grp_src;               // union sources
+    std::vector<int> grp_op;                // [nsrc*8]
+    std::vector<double> grp_gain;           // [depth+1]: M2L edges / union sources of the level
 
     // ---- device copy -----------------------------------------------------
     struct {
@@ -107,6 +119,8 @@ struct occk_tree {
         int* box_level = nullptr;      // [nbox]
         double* hlev = nullptr;        // [depth+1]
         int* m2l_tgt = nullptr;        // [nm2l]
+        int* grp_child = nullptr; int* grp_parent = nullptr; int* grp_ptr = nullptr;
+        int* grp_src = nullptr; int* grp_op = nullptr;
     } dev;
     int nops_alloc_lmax = -1;
     long long gen = 0;                      // changes whenever the operators are regenerated
@@ -139,6 +153,7 @@ struct occk_ctx {
     std::vector<double> tp_scd;             // [2][nlev][nc] scales of the last panel build (host)
     int last_scaled = 0;                    // last run kept O and Mcal in scaled form
     int tr_engine = -1;                     // occk_set_translate_engine mask
+    int m2l_group = -1;                     // occk_set_m2l_group: -1 auto, 0 off, 1 on
     occk::DevBuf sob, smb;                  // slot storage of O~ and Mcal~ (slot pipeline)
     occk::DevBuf jbox;                      // far-field J: density multipoles, local expansions, partials
     double screen_tau = 0.0;                // occupied-pair screening threshold (0: off)
@@ -218,6 +233,11 @@ struct FmmArgs {
     unsigned char* scr_tiles;        // [nocc/128][nocc/8] step (e) tiles holding a kept pair
     float* scr_a2; float* scr_b2;    // bound factors of the SIMT step (a): a2 [nleaf][nocc], b2 parts [nc][nleaf][nocc]
     unsigned char* scr_tskip;        // step (a) tiles (k_full's triangular order) dropped whole by the bound
+    // sibling-grouped FP32 M2L (fused with L2L) per level: grp_use[lev] != 0
+    // runs level lev with k_m2l_group instead of the per-target pass
+    const int* grp_level_off;        // host [depth+2]
+    const int* grp_child; const int* grp_parent; const int* grp_ptr; const int* grp_src; const int* grp_op;
+    unsigned grp_use;                // bit lev set: level lev grouped
     // occupied column block [col0, col1) (col1 > col0; both 0 when unused):
     // only pairs touching the block are kept (screen != 0), step (e) and the
     // K reduction cover only the block's columns, Ex_dev gets their part of E

@@ -109,6 +109,7 @@ _SIGS = {
     "occk_get_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "occk_debug_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_longlong]),
     "occk_set_column_block": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "occk_set_m2l_group": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_exchange_energy": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
                                             ctypes.c_int, _vp, _vp]),
 }
@@ -188,6 +189,11 @@ class Context:
         M2L, bit 2 L2L; 15: all three with the expansions kept in the tensor
         core's operand layout; -1 chooses by expansion rank."""
         self.check(lib().occk_set_translate_engine(self._h, int(mask)), "occk_set_translate_engine")
+
+    def set_m2l_group(self, mode: int = -1):
+        """Sibling-grouped FP32 M2L: 1 always, 0 never, -1 by the level's
+        sharing of interaction-list sources."""
+        self.check(lib().occk_set_m2l_group(self._h, int(mode)), "occk_set_m2l_group")
 
     def set_l2p_split(self, nsplit: int = 0):
         """K-range splits of the FP32 SIMT step (e); 0 chooses automatically."""
