@@ -64,6 +64,7 @@ def parse(argv=None):
                    help="reference rank of the learned-selector comparison on the protein workload (0: skip)")
     p.add_argument("--learned-tau", type=float, default=1e-6, help="error budget (Eh) of the learned selector")
     p.add_argument("--no-chain", action="store_true", help="skip the C150H302 FP32/FP16X3 object")
+    p.add_argument("--no-batch", action="store_true", help="skip the uneven-batch object")
     p.add_argument("--screen-tau", type=float, default=1e-4,
                    help="occupied-pair screening threshold timed on localised orbitals of C150H302 (0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -379,44 +380,41 @@ class Timer:
         return ms, {k: round(v, 4) for k, v in st.items()}
 
 
-def run_batch(args, rank, world, local):
+def batch_object(args, dev, steps, prec="fp32", clocks_dev=None):
     """The uneven batch: graphene-like flake, chains of 50/100/200 carbons and
-    16 water clusters of 10-60 molecules, lmax 4, FP32 contractions, in one
-    graph-captured launch sequence with autotuned tiles; timed against the
-    same systems run one call after another."""
+    16 water clusters of 10-60 molecules, lmax 4, in one graph-captured launch
+    sequence whose mode and tiles the autotuner picks (level-synchronous
+    persistent kernels over all systems, or every system's own pipeline on
+    forked streams); timed against the same systems run one call after
+    another, and checked against per-system FP64 runs."""
     import numpy as np
     import torch
     from paper_1708_05353_gb300 import inputs, occk
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     L = 4
+    t0 = time.perf_counter()
     systems = inputs.batch_workload(lmax=L)
-    ctx = occk.Context(local)
+    ctx = occk.Context(dev.index or 0)
     trees = []
     for s_ in systems:
         t = occk.Tree(ctx, s_.basis, depth=s_.depth, target_atoms_per_leaf=s_.target_atoms_per_leaf)
         t.pair_multipoles(L)
         trees.append(t)
-    prec = "fp64" if args.prec == "fp64" and args.batch_fp64 else "fp32"
     b = occk.Batch(ctx, trees, [s_.nocc for s_ in systems], prec=prec)
     for k, s_ in enumerate(systems):
         c, _, _, ld = b.buffers(k)
         occk.device_view(c, (s_.nocc, ld), torch.float64, dev).copy_(torch.tensor(s_.C.T, dtype=torch.float64))
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
     cfg = b.tune(args.tune_cache)
+    t_tune = time.perf_counter() - t0
     tm = Timer(ctx, dev)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(3):
         b.run(use_graph=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local)
-    ms_graph, _ = tm.run(lambda: b.run(use_graph=True), args.steps, warm=0)
-    clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-    ms_graph = max_over_ranks(ms_graph, world, dev)
-    ms_nograph, _ = tm.run(lambda: b.run(use_graph=False), args.steps)
+    clocks = Clocks(clocks_dev) if clocks_dev is not None else None
+    ms_graph, _ = tm.run(lambda: b.run(use_graph=True), steps, warm=0)
+    clk = clocks.stop() if clocks is not None else None
+    ms_nograph, _ = tm.run(lambda: b.run(use_graph=False), steps)
     Cs = [occk.fortran(torch.tensor(s_.C, dtype=torch.float64, device=dev)) for s_ in systems]
     Ks = [occk.empty_fortran(s_.basis.nao, s_.nocc, torch.float64, dev) for s_ in systems]
     Es = torch.empty(len(systems), dtype=torch.float64, device=dev)
@@ -424,21 +422,41 @@ def run_batch(args, rank, world, local):
     def seq():
         for k in range(len(systems)):
             occk.farfield_K(ctx, trees[k], Cs[k], prec=prec, K=Ks[k], Ex=Es[k])
-    ms_seq, _ = tm.run(seq, args.steps)
+    ms_seq, _ = tm.run(seq, steps)
     Eb = occk.device_view(b.buffers(0)[2], (len(systems),), torch.float64, dev).cpu().numpy()
     for k in range(len(systems)):
         occk.farfield_K(ctx, trees[k], Cs[k], prec="fp64", K=Ks[k], Ex=Es[k])
     torch.cuda.synchronize()
     errs = np.abs(Eb - Es.cpu().numpy())
-    line = {"metric": METRIC, "value": ms_graph * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": "batch: flake C150H30, chains C50/C100/C200, 16 water clusters 10-60",
-                       "nsys": len(systems), "lmax": L, "tuned": cfg, "parallelism": f"replicas x{world}",
+    out = {"workload": "batch: flake C150H30, chains C50/C100/C200, 16 water clusters 10-60 molecules",
+           "nsys": len(systems), "lmax": L, "dtype": "f32" if prec == "fp32" else "f64",
+           "tuned": cfg, "tune_s": round(t_tune, 2), "setup_s": round(t_setup, 2),
+           "batch_graph_ms": round(ms_graph, 3), "batch_no_graph_ms": round(ms_nograph, 3),
+           "sequential_calls_ms": round(ms_seq, 3), "speedup_vs_sequential": round(ms_seq / ms_graph, 3),
+           "max_abs_dE_vs_fp64_Eh": float(errs.max()), "clocks": clk}
+    del tm
+    b.close()
+    for t in trees:
+        t.close()
+    ctx.close()
+    return out
+
+
+def run_batch(args, rank, world, local):
+    """`--workload batch`: the batch object as the headline line."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = "fp64" if args.prec == "fp64" and args.batch_fp64 else "fp32"
+    o = batch_object(args, dev, args.steps, prec=prec, clocks_dev=local)
+    ms = max_over_ranks(o["batch_graph_ms"], world, dev)
+    line = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": o["dtype"], "data": "synthetic",
+            "config": {"workload": o["workload"], "nsys": o["nsys"], "lmax": o["lmax"], "tuned": o["tuned"],
+                       "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MB write) before every timed step"},
-            "batch_graph_ms": ms_graph, "batch_no_graph_ms": ms_nograph, "sequential_calls_ms": ms_seq,
-            "speedup_vs_sequential": ms_seq / ms_graph, "max_abs_dE_vs_fp64_Eh": float(errs.max()),
-            "clocks": clk}
+            "clocks": o.pop("clocks"), "batch": o}
     if rank == 0:
         print(json.dumps(line, default=float), flush=True)
 
@@ -811,6 +829,11 @@ def main(argv=None):
             del Dm, J
         except Exception as ex:
             result["coulomb_j"] = {"error": repr(ex)}
+        if args.workload == "protein" and not args.no_batch:
+            try:
+                result["batch"] = batch_object(args, dev, max(5, args.steps // 2))
+            except Exception as ex:
+                result["batch"] = {"error": repr(ex)}
         if args.screen_tau > 0 and args.workload in ("protein", "chain"):
             try:
                 result["pair_screen"] = screen_object(args, ctx, dev, tm)

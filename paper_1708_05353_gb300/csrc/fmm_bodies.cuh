@@ -448,10 +448,12 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit
         const double w = (lm == l * l) ? 2.0 : (((lm - l * l) & 1) ? 4.0 : -4.0);
         const double* Wl = W + ((size_t)lm * nrow + rb0) * nocc;
         const double* Ml = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
-        {   // A: 32 rows x 8 columns, one element per thread
+        {   // A: 32 rows x 8 columns, one element per thread, times the
+            // real-form weight w (a power of two, so w a b is rounded exactly
+            // as a (w b); 256 multiplies per step instead of 1024 on B)
             const int row = threadIdx.x / BK, kk = threadIdx.x % BK;
             const int r = r0 + row, j = k0 + kk;
-            As[kk][row] = (r < nr && j < nocc) ? Wl[(size_t)r * nocc + j] : 0.0;
+            As[kk][row] = (r < nr && j < nocc) ? w * Wl[(size_t)r * nocc + j] : 0.0;
         }
         // B: 128 rows (i) x 8 columns (j) of the symmetric Mcal, read from
         // the packed upper triangle; thread order follows the stored rows
@@ -459,9 +461,7 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit
         for (int e = threadIdx.x; e < BK * BI; e += 256) {
             const int row = below ? e % BI : e / BK, kk = below ? e / BI : e % BK;
             const int i = i0 + row, j = k0 + kk;
-            Bs[kk][row] = (i < nocc && j < nocc)
-                              ? w * Ml[i <= j ? tri_index(i, j, nocc) : tri_index(j, i, nocc)]
-                              : 0.0;
+            Bs[kk][row] = (i < nocc && j < nocc) ? Ml[i <= j ? tri_index(i, j, nocc) : tri_index(j, i, nocc)] : 0.0;
         }
         __syncthreads();
         // a warp covers rows r0 + 4w .. r0 + 4w + 3: skip warps past the leaf's rows
