@@ -415,6 +415,14 @@ def batch_object(args, dev, steps, prec="fp32", clocks_dev=None):
     ms_graph, _ = tm.run(lambda: b.run(use_graph=True), steps, warm=0)
     clk = clocks.stop() if clocks is not None else None
     ms_nograph, _ = tm.run(lambda: b.run(use_graph=False), steps)
+    # both modes at the tuned tile shapes: the level-synchronous persistent
+    # kernels over all systems (mode 0) and every system's own pipeline on
+    # forked streams (mode 1), each as a captured graph
+    modes = {}
+    for mode in (0, 1):
+        b.set_config(chunk=cfg["chunk"], blocks_per_sm=cfg["blocks_per_sm"], tile=cfg["tile"], mode=mode)
+        modes[f"mode{mode}_graph_ms"] = round(tm.run(lambda: b.run(use_graph=True), steps, warm=2)[0], 3)
+    b.set_config(**cfg)
     Cs = [occk.fortran(torch.tensor(s_.C, dtype=torch.float64, device=dev)) for s_ in systems]
     Ks = [occk.empty_fortran(s_.basis.nao, s_.nocc, torch.float64, dev) for s_ in systems]
     Es = torch.empty(len(systems), dtype=torch.float64, device=dev)
@@ -433,6 +441,7 @@ def batch_object(args, dev, steps, prec="fp32", clocks_dev=None):
            "tuned": cfg, "tune_s": round(t_tune, 2), "setup_s": round(t_setup, 2),
            "batch_graph_ms": round(ms_graph, 3), "batch_no_graph_ms": round(ms_nograph, 3),
            "sequential_calls_ms": round(ms_seq, 3), "speedup_vs_sequential": round(ms_seq / ms_graph, 3),
+           **modes,
            "max_abs_dE_vs_fp64_Eh": float(errs.max()), "clocks": clk}
     del tm
     b.close()

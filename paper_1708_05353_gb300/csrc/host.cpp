@@ -65,7 +65,7 @@ void free_tree_device(occk_tree* t) {
     dfree(d.m2l_ptr); dfree(d.m2l_src); dfree(d.m2l_op);
     dfree(d.m2l_lmax_full); dfree(d.m2l_lmax_edge); dfree(d.parent);
     dfree(d.pairs); dfree(d.prim_exp); dfree(d.prim_coef);
-    dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.ops_ft); dfree(d.opdesc);
+    dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.opdesc);
     dfree(d.l2l_op); dfree(d.lscale); dfree(d.box_scale);
     dfree(d.box_key); dfree(d.box_level); dfree(d.hlev); dfree(d.m2l_tgt);
     dfree(d.grp_child); dfree(d.grp_parent); dfree(d.grp_ptr); dfree(d.grp_src); dfree(d.grp_op);
@@ -659,17 +659,15 @@ extern "C" occk_status occk_pair_multipoles(occk_ctx* ctx, occk_tree* t, int lma
     auto& d = t->dev;
     const int nc = occk::ncomp(lmax);
     const int nops = (int)t->ops.size();
-    dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.ops_ft);
-    const int nc4 = (nc + 3) / 4 * 4;
+    dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d.pair_vals, sizeof(double) * (size_t)t->nvals * nc);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d.pair_vals_f, sizeof(float) * (size_t)t->nvals * nc);
     if (nops > 0) {
         if (e == cudaSuccess) e = cudaMalloc((void**)&d.ops, sizeof(double) * (size_t)nops * nc * nc);
         if (e == cudaSuccess) e = cudaMalloc((void**)&d.ops_f, sizeof(float) * (size_t)nops * nc * nc);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&d.ops_ft, sizeof(float) * (size_t)nops * nc * nc4);
     }
     if (e != cudaSuccess) {
-        dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f); dfree(d.ops_ft);
+        dfree(d.pair_vals); dfree(d.pair_vals_f); dfree(d.ops); dfree(d.ops_f);
         return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "pair multipole storage")
                                               : cuda_fail(ctx, e, "occk_pair_multipoles alloc");
     }
@@ -699,7 +697,6 @@ extern "C" occk_status occk_pair_multipoles(occk_ctx* ctx, occk_tree* t, int lma
     e = occk::launch_pair_multipoles(d.pairs, (int)t->pair_a.size(), d.prim_exp, d.prim_coef, lmax,
                                      d.pair_vals, d.pair_vals_f, t->nvals, s);
     if (e == cudaSuccess && nops > 0) e = occk::launch_gen_ops(d.opdesc, nops, lmax, d.ops, d.ops_f, s);
-    if (e == cudaSuccess && nops > 0) e = occk::transpose_ops(d.ops_f, nops, nc, d.ops_ft, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_pair_multipoles launch");
     t->lmax = lmax;
     static std::atomic<long long> gen_counter{0};
@@ -1106,12 +1103,11 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.grp_use = 0;
     a.grp_level_off = t->grp_level_off.data();
     a.grp_child = d.grp_child; a.grp_parent = d.grp_parent; a.grp_ptr = d.grp_ptr;
-    a.grp_src = d.grp_src; a.grp_op = d.grp_op; a.ops_ft = d.ops_ft;
+    a.grp_src = d.grp_src; a.grp_op = d.grp_op;
     // measured on GB300 (protein-sized cluster, (H2O)100): grouped M2L at
     // rank 2 1.36-1.42x faster than per target; at rank 3 (16 components,
     // half the pairs per block) slower, so the default groups rank <= 2 only
-    if (prec != OCCK_FP64 && (nc == 4 || nc == 9 || nc == 16) && d.grp_parent && d.ops_ft &&
-        ctx->m2l_group != 0) {
+    if (prec != OCCK_FP64 && (nc == 4 || nc == 9 || nc == 16) && d.grp_parent && ctx->m2l_group != 0) {
         for (int lev = 2; lev <= D && lev < 32; ++lev)
             if (ctx->m2l_group == 1 || (nc <= 9 && t->grp_gain[lev] >= 2.0)) a.grp_use |= 1u << lev;
     }

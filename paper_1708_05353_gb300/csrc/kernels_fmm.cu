@@ -509,26 +509,19 @@ k_m2l_group(int P, const int* __restrict__ pcount, int first_box, int g0, const 
             if (e < NC * TP) tile[buf][c][p] = pre[m];
         }
     };
-    // operators transposed, [op][input][output padded to NC4]: one input's
-    // column is NC4 / 4 sixteen-byte loads (the same address in every lane)
-    constexpr int NC4 = (NC + 3) / 4 * 4;
     auto apply = [&](int buf, int op) {                // warp-uniform op >= 0
-        const float4* T = reinterpret_cast<const float4*>(ops + (size_t)op * NC * NC4);
+        const float* T = ops + (size_t)op * NC * NC;
 #pragma unroll
         for (int ci = 0; ci < NC; ++ci) {
             float v[PPW];
 #pragma unroll
             for (int p = 0; p < PPW; ++p) v[p] = tile[buf][ci][lane + 32 * p];
-            float w[NC4];
 #pragma unroll
-            for (int q = 0; q < NC4 / 4; ++q) {
-                const float4 t4 = __ldg(T + ci * (NC4 / 4) + q);
-                w[4 * q] = t4.x; w[4 * q + 1] = t4.y; w[4 * q + 2] = t4.z; w[4 * q + 3] = t4.w;
+            for (int co = 0; co < NC; ++co) {
+                const float w = __ldg(T + co * NC + ci);
+#pragma unroll
+                for (int p = 0; p < PPW; ++p) acc[co][p] += w * v[p];
             }
-#pragma unroll
-            for (int co = 0; co < NC; ++co)
-#pragma unroll
-                for (int p = 0; p < PPW; ++p) acc[co][p] += w[co] * v[p];
         }
     };
     const int s0 = grp_ptr[g], s1 = grp_ptr[g + 1];
@@ -571,18 +564,6 @@ void launch_m2l_group(const FmmArgs& a, int lev, int P, const int* pcount, const
     dim3 g((P + TP - 1) / TP, ng);
     k_m2l_group<NC, PPW><<<g, 256, 0, s>>>(P, pcount, a.first_box, g0, a.grp_child, a.grp_parent, a.grp_ptr,
                                           a.grp_src, a.grp_op, a.l2l_op, lev >= 3 ? 1 : 0, ops, in, out, out);
-}
-
-__global__ void k_ops_transpose(const float* __restrict__ ops, int nops, int nc, int nc4, float* __restrict__ opst) {
-    const long long n = (long long)nops * nc * nc4;
-    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (long long)gridDim.x * blockDim.x) {
-        const int co = (int)(x % nc4);
-        const long long r = x / nc4;
-        const int ci = (int)(r % nc);
-        const long long op = r / nc;
-        opst[x] = co < nc ? ops[(op * nc + co) * nc + ci] : 0.f;
-    }
 }
 
 // Components per block of k_half: the instantiated width that leaves the
@@ -868,8 +849,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
             int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
             if (nt <= 0) continue;
             if constexpr (sizeof(T) == 4) {
-                if (((a.grp_use >> lev) & 1u) && lmax_e == nullptr && !trc) {
-                    const float* fo = a.ops_ft;
+                if (((a.grp_use >> lev) & 1u) && lmax_e == nullptr) {
+                    const float* fo = (const float*)tops;
                     if (nc == 9)
                         launch_m2l_group<9, 4>(a, lev, (int)P, pcnt, fo, (const float*)Ot, (float*)Mt, s);
                     else if (nc == 16)
@@ -1101,14 +1082,6 @@ cudaError_t energy_from_K(int nao, int nocc, const double* C, int ldc, const dou
                           double* E, cudaStream_t s) {
     body::k_energy_parts<<<kFarfieldPartials, 256, 0, s>>>(nao, nocc, C, ldc, K, ldk, part);
     k_final_energy<<<1, 256, 0, s>>>(part, kFarfieldPartials, E);
-    return cudaGetLastError();
-}
-
-cudaError_t transpose_ops(const float* ops_f, int nops, int nc, float* ops_ft, cudaStream_t s) {
-    const int nc4 = (nc + 3) / 4 * 4;
-    const long long n = (long long)nops * nc * nc4;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
-    k_ops_transpose<<<std::max(blocks, 1), 256, 0, s>>>(ops_f, nops, nc, nc4, ops_ft);
     return cudaGetLastError();
 }
 

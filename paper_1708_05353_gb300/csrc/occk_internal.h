@@ -112,7 +112,6 @@ struct occk_tree {
         float* pair_vals_f = nullptr;
         double* ops = nullptr;         // [nops][nc][nc]
         float* ops_f = nullptr;
-        float* ops_ft = nullptr;       // [nops][nc][nc4] FP32 transposed (input-major), rows padded to nc4 = 4k
         occk::OpDesc* opdesc = nullptr;
         float* lscale = nullptr;       // [nc] sqrt((l+m)!(l-m)!) / h_leaf^l
         float* box_scale = nullptr;    // [nbox]
@@ -175,9 +174,6 @@ struct occk_ctx {
 namespace occk {
 
 // ----- kernel launchers (kernels_*.cu) ------------------------------------
-// FP32 operators transposed to [op][input][output], output rows padded to
-// a multiple of 4 floats (zeros), for 16-byte loads of one input's column.
-cudaError_t transpose_ops(const float* ops_f, int nops, int nc, float* ops_ft, cudaStream_t s);
 cudaError_t launch_gen_ops(const OpDesc* d_desc, int nops, int L, double* d_out, float* d_out_f,
                            cudaStream_t s);
 cudaError_t launch_pair_multipoles(const PairDesc* d_pairs, int npair, const double* d_exp,
@@ -242,7 +238,6 @@ struct FmmArgs {
     const int* grp_level_off;        // host [depth+2]
     const int* grp_child; const int* grp_parent; const int* grp_ptr; const int* grp_src; const int* grp_op;
     unsigned grp_use;                // bit lev set: level lev grouped
-    const float* ops_ft;             // transposed FP32 operators (unscaled), see transpose_ops
     // occupied column block [col0, col1) (col1 > col0; both 0 when unused):
     // only pairs touching the block are kept (screen != 0), step (e) and the
     // K reduction cover only the block's columns, Ex_dev gets their part of E
