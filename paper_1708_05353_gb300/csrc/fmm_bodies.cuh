@@ -190,6 +190,14 @@ __device__ __forceinline__ void full_body(int bx, int by, int bz, const int* __r
                     a[q] = av.x; a[q + 1] = av.y; a[q + 2] = av.z; a[q + 3] = av.w;
                     b[q] = bv.x; b[q + 1] = bv.y; b[q + 2] = bv.z; b[q + 3] = bv.w;
                 }
+            } else if constexpr (sizeof(T) == 4 && TM % 2 == 0) {   // float2 shared loads (conflict-free for TM = 6)
+#pragma unroll
+                for (int q = 0; q < TM; q += 2) {
+                    const float2 av = *reinterpret_cast<const float2*>(&As[buf][kk][ty * TM + q]);
+                    const float2 bv = *reinterpret_cast<const float2*>(&Bs[buf][kk][tx * TM + q]);
+                    a[q] = av.x; a[q + 1] = av.y;
+                    b[q] = bv.x; b[q + 1] = bv.y;
+                }
             } else {
 #pragma unroll
                 for (int q = 0; q < TM; ++q) {
@@ -501,19 +509,23 @@ __device__ __forceinline__ void l2p_rect_body(int bx, int by, int bz, int nsplit
 // in several waves instead of one and a sliver.  A leaf of up to 96 AOs is
 // one row tile, so each element of the packed Mcal is read once per leaf;
 // shared-memory operands are read as float2/float4 (5 loads per 48 FMAs).
+//
+// TI = 2 covers only the first 32 orbitals of the 128-orbital tile `by`
+// (columns tx + 16 y), for the last tile when it holds 32 or fewer.
+template <int TI = 8>
 __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nsplit, const int* __restrict__ leaf_rowoff,
                                                 const float* __restrict__ W, const float* __restrict__ Mbox,
                                                 int nocc, int nrow, int nc, int leaf_store0,
                                                 double* __restrict__ KB,
                                                 const unsigned char* __restrict__ tflag = nullptr) {
-    constexpr int BR = 96, BI = 128, BK = 32, TR = 6, TI = 8;
+    constexpr int BR = 96, BI = 16 * TI, BK = 32, TR = 6;
     __shared__ __align__(16) float As[BK][BR + 4];
     __shared__ __align__(16) float Bs[BK][BI + 4];
     // block z = leaf * nsplit + split: the split covers its share of the
     // flattened (lm, j-chunk) range and writes its own copy of KB
     const int B = bz / nsplit, ks = bz % nsplit;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
-    const int r0 = bx * BR, i0 = by * BI;
+    const int r0 = bx * BR, i0 = by * 128;
     if (r0 >= nr) return;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const size_t P = npairs(nocc);
@@ -568,12 +580,19 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nspl
                 const float2 a0 = *reinterpret_cast<const float2*>(&As[kk][ty * TR]);
                 const float2 a1 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 2]);
                 const float2 a2 = *reinterpret_cast<const float2*>(&As[kk][ty * TR + 4]);
-                // columns tx*4.. and 64 + tx*4..: each quarter warp reads
-                // 128 contiguous bytes (no bank conflict)
-                const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-                const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
                 const float av[6] = {a0.x, a0.y, a1.x, a1.y, a2.x, a2.y};
-                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                float bv[TI];
+                if constexpr (TI == 8) {
+                    // columns tx*4.. and 64 + tx*4..: each quarter warp reads
+                    // 128 contiguous bytes (no bank conflict)
+                    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+                    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+                    bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
+                    bv[4] = b1.x; bv[5] = b1.y; bv[6] = b1.z; bv[7] = b1.w;
+                } else {
+#pragma unroll
+                    for (int y = 0; y < TI; ++y) bv[y] = Bs[kk][tx + 16 * y];
+                }
 #pragma unroll
                 for (int x = 0; x < TR; ++x)
 #pragma unroll
@@ -588,7 +607,7 @@ __device__ __forceinline__ void l2p_rect_body_f(int bx, int by, int bz, int nspl
         if (r >= nr) continue;
 #pragma unroll
         for (int y = 0; y < TI; ++y) {
-            const int i = i0 + (y >> 2) * 64 + tx * 4 + (y & 3);
+            const int i = i0 + (TI == 8 ? (y >> 2) * 64 + tx * 4 + (y & 3) : tx + 16 * y);
             if (i < nocc) KB[(size_t)ks * nrow * nocc + (size_t)(rb0 + r) * nocc + i] = (double)acc[x][y];
         }
     }

@@ -931,7 +931,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         ctx->last_tskip_n = 0;
         ctx->last_tskip = a.scr_tskip;
         if (prec == OCCK_FP64 || prec == OCCK_FP32) {
-            const size_t bm = prec == OCCK_FP64 ? 64 : 128, nt = (nocc + bm - 1) / bm;
+            const size_t bm = prec == OCCK_FP64 ? occk::kFullTileFP64 : occk::full_tile_fp32(nocc);
+            const size_t nt = (nocc + bm - 1) / bm;
             ctx->last_tskip_n = nt * (nt + 1) / 2;
         }
     }

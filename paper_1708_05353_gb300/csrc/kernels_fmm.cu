@@ -11,6 +11,7 @@
 //   KB   [nrow][nocc]           per-leaf partial K rows (FP64)
 // Every pair-indexed access is coalesced along p (or along j).
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 
 #include "fmm_bodies.cuh"
@@ -71,12 +72,13 @@ k_l2p_r32(int nsplit, const int* __restrict__ leaf_rowoff, const double* __restr
                             nc, leaf_store0, KB, tflag);
 }
 
+template <int TI>
 __global__ void __launch_bounds__(256)
 k_l2p_r96f(int nsplit, const int* __restrict__ leaf_rowoff, const float* __restrict__ W,
            const float* __restrict__ Mbox, int nocc, int nrow, int nc, int leaf_store0, double* __restrict__ KB,
            const unsigned char* __restrict__ tflag, int tile0) {
-    body::l2p_rect_body_f(blockIdx.x, blockIdx.y + tile0, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow, nc,
-                          leaf_store0, KB, tflag);
+    body::l2p_rect_body_f<TI>(blockIdx.x, blockIdx.y + tile0, blockIdx.z, nsplit, leaf_rowoff, W, Mbox, nocc, nrow,
+                              nc, leaf_store0, KB, tflag);
 }
 
 __global__ void k_reduce_K(const int* __restrict__ ao_row_ptr, const int* __restrict__ ao_rows,
@@ -688,7 +690,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         cudaError_t e2 = panel_a2(a.prec, pa, s);
         if (e2 != cudaSuccess) return e2;
     } else if constexpr (sizeof(T) == 8) {
-        constexpr int BM = 64, BK = 8, TM = 4;
+        constexpr int BM = kFullTileFP64, BK = 8, TM = 4;
         int nt = (nocc + BM - 1) / BM;
         if (a.screen) {
             // tskip[t] = 1: tile t is not formed.  With a usable bound every
@@ -711,28 +713,34 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
                                                                  a.nrow, nc, nt, Ob, leaf_store0,
                                                                  a.screen ? a.scr_tskip : nullptr);
     } else {
-        constexpr int BM = 128, BK = 16, TM = 8;
-        int nt = (nocc + BM - 1) / BM;
-        if (a.screen) {
-            // tskip[t] = 1: tile t is not formed.  With a usable bound every
-            // tile starts skipped and the bound clears the ones that may hold
-            // a kept pair; otherwise every tile starts formed.
-            const bool bound = a.screen_tau2 > 0 && bound_usable(a.screen_tau2);
-            cudaMemsetAsync(a.scr_tskip, bound ? 1 : 0, (size_t)nt * (nt + 1) / 2, s);
-            if (bound) {
-                k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
-                    a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
-                k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
-                    a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
+        // 128 x 128 tiles (8 x 8 per thread) or 96 x 96 (6 x 6), whichever
+        // wastes fewer FMAs on padding and on the lower halves of diagonal
+        // tiles (full_tile_fp32)
+        auto launch = [&](auto tile) {
+            constexpr int BM = decltype(tile)::value, BK = 16, TM = BM == 96 ? 6 : 8;
+            const int nt = (nocc + BM - 1) / BM;
+            if (a.screen) {
+                const bool bound = a.screen_tau2 > 0 && bound_usable(a.screen_tau2);
+                cudaMemsetAsync(a.scr_tskip, bound ? 1 : 0, (size_t)nt * (nt + 1) / 2, s);
+                if (bound) {
+                    k_bound_ab<T><<<dim3(a.nleaf, (nocc + 127) / 128, nc + 1), 128, 0, s>>>(
+                        a.leaf_rowoff, a.leaf_aos, Ct, W, nocc, a.nrow, a.nleaf, a.scr_a2, a.scr_b2);
+                    k_bound_tiles<<<dim3(nt * (nt + 1) / 2, BM / 8), 256, 0, s>>>(
+                        a.scr_a2, a.scr_b2, a.nleaf, nc, nocc, BM, nt, (float)(0.5 * a.screen_tau2), a.scr_tskip);
+                }
+                if (a.col1 > a.col0)
+                    k_col_tiles<<<std::max(1, (nt * (nt + 1) / 2 + 255) / 256), 256, 0, s>>>(nt, BM, a.col0,
+                                                                                             a.col1, a.scr_tskip);
             }
-            if (a.col1 > a.col0)
-                k_col_tiles<<<std::max(1, (nt * (nt + 1) / 2 + 255) / 256), 256, 0, s>>>(nt, BM, a.col0, a.col1,
-                                                                                         a.scr_tskip);
-        }
-        dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
-        k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
-                                                                 a.nrow, nc, nt, Ob, leaf_store0,
-                                                                 a.screen ? a.scr_tskip : nullptr);
+            dim3 g(nt * (nt + 1) / 2, a.nleaf * nc);
+            k_full<T, BM, BK, TM><<<g, (BM / TM) * (BM / TM), 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, W, nocc,
+                                                                     a.nrow, nc, nt, Ob, leaf_store0,
+                                                                     a.screen ? a.scr_tskip : nullptr);
+        };
+        if (full_tile_fp32(nocc) == 96)
+            launch(std::integral_constant<int, 96>{});
+        else
+            launch(std::integral_constant<int, 128>{});
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -757,7 +765,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
             k_pair_part<T><<<gpart, kPairBlk, 0, s>>>(Ob + (size_t)leaf_store0 * nc * P, a.nleaf, nc, P, part);
         k_pair_flag<T><<<nb, kPairBlk, 0, s>>>(part, norms ? ngrp : 0, P, a.screen_tau2, a.scr_norm, a.scr_inv,
                                                 a.scr_bcount, tcm ? nullptr : a.scr_tskip, nocc,
-                                                sizeof(T) == 8 ? 64 : 128, a.col0, a.col1);
+                                                sizeof(T) == 8 ? kFullTileFP64 : full_tile_fp32(nocc), a.col0,
+                                                a.col1);
         k_pair_scan<<<1, 1024, 0, s>>>(a.scr_bcount, nb, a.scr_count);
         k_pair_compact<<<nb, kPairBlk, 0, s>>>(P, a.scr_bcount, a.scr_keep, a.scr_inv);
         cudaMemsetAsync(a.scr_tiles, 0, (size_t)((nocc + 127) / 128) * ((nocc + 7) / 8), s);
@@ -932,9 +941,17 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         }
     } else {
         const int nsplit = a.l2p_nsplit;
-        dim3 g((a.max_rows + 95) / 96, itile1 - itile0, a.nleaf * nsplit);
-        k_l2p_r96f<<<g, 256, 0, s>>>(nsplit, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow, nc,
-                                     leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr, itile0);
+        // the last orbital tile with 32 orbitals or fewer as a 32-column launch
+        const bool tail = nocc - (itile1 - 1) * 128 <= 32;
+        dim3 g((a.max_rows + 95) / 96, itile1 - itile0 - (tail ? 1 : 0), a.nleaf * nsplit);
+        if (g.y > 0)
+            k_l2p_r96f<8><<<g, 256, 0, s>>>(nsplit, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow,
+                                            nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr, itile0);
+        if (tail) {
+            g.y = 1;
+            k_l2p_r96f<2><<<g, 256, 0, s>>>(nsplit, a.leaf_rowoff, (const float*)W, (const float*)Mb, nocc, a.nrow,
+                                            nc, leaf_store0, a.kb, a.screen ? a.scr_tiles : nullptr, itile1 - 1);
+        }
     }
     mark(6);
     constexpr int kRedBlocks = kFarfieldPartials;

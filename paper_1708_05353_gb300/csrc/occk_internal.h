@@ -265,6 +265,20 @@ struct JArgs {
 cudaError_t run_farfield_J(const JArgs& a, cudaStream_t s);
 // partial energies run_farfield writes to FmmArgs::part (its K reduction blocks)
 constexpr int kFarfieldPartials = 1024;
+// orbital tile of the SIMT step (a) O^{ij} kernel (k_full): 64 x 64 in FP64;
+// in FP32 128 x 128 (8 x 8 per thread) unless 96 x 96 (6 x 6 per thread)
+// covers a third more useful pairs i <= j with its triangle of tiles
+// (measured on GB300: 660 orbitals 18.1 -> 15.3 ms with 96; 601 orbitals
+// 0.75 -> 0.95 ms, so 128 there).  The screening's step (a) tile flags use
+// the same tiles.
+constexpr int kFullTileFP64 = 64;
+inline int full_tile_fp32(int nocc) {
+    auto useful = [nocc](int bm) {
+        const double nt = (nocc + bm - 1) / bm;
+        return (double)nocc * (nocc + 1) / 2 / (nt * (nt + 1) / 2 * (double)bm * bm);
+    };
+    return useful(96) > 1.15 * useful(128) ? 96 : 128;
+}
 // Arguments of the SIMT FP64/FP32 path for one tree with caller-provided
 // workspaces (the batch's per-system pipelines; host.cpp).
 FmmArgs simt_args(const occk_ctx* ctx, const occk_tree* t, int nocc, int prec, const double* C, int ldc, double* K,
