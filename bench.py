@@ -470,6 +470,31 @@ def run_batch(args, rank, world, local):
         print(json.dumps(line, default=float), flush=True)
 
 
+def tc_gemm_object(ctx, dev, tm, n=8192):
+    """Throughput of the project's tcgen05 GEMM engine (the one steps (a) and
+    (e) of the mixed forms use) on a plain n x n x n product D = A B^T from
+    FP32 inputs, panel conversion included, per form: the engine's own peak,
+    beside cuBLAS's measured BF16 rate (MEASURED_PEAKS.json).  The split forms
+    issue three MMAs per product; their rate counts 2 n^3 FLOP once."""
+    import torch
+    from paper_1708_05353_gb300 import occk
+    g = torch.Generator(device="cpu").manual_seed(5)
+    A = torch.randn(n, n, generator=g, dtype=torch.float32).to(dev)
+    B = torch.randn(n, n, generator=g, dtype=torch.float32).to(dev)
+    out = {"shape": [n, n, n], "what": "D = A B^T, FP32 in and out, tcgen05 panel GEMM incl. operand conversion"}
+    for prec in ("tf32", "bf16", "fp16", "bf16x3", "fp16x3"):
+        ms, _ = tm.run(lambda: occk.debug_tc_gemm(ctx, prec, A, B), 3, warm=1)
+        out[prec] = {"ms": round(ms, 3), "tflops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 1)}
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks):
+        bf = json.load(open(peaks)).get("bf16_tflops")
+        if bf:
+            out["cublas_bf16_tflops_measured"] = bf
+            out["bf16_frac_of_cublas"] = round(out["bf16"]["tflops"] / bf, 3)
+    del A, B
+    return out
+
+
 def learned_object(args, ctx, dev, system, tm):
     """The learned per-edge rank selector against fixed rank L_ref (one build
     each; at L_ref = 10 a plain FP64 build of this workload takes about a
@@ -838,6 +863,11 @@ def main(argv=None):
             del Dm, J
         except Exception as ex:
             result["coulomb_j"] = {"error": repr(ex)}
+        if args.workload == "protein":
+            try:
+                result["tc_gemm"] = tc_gemm_object(ctx, dev, tm)
+            except Exception as ex:
+                result["tc_gemm"] = {"error": repr(ex)}
         if args.workload == "protein" and not args.no_batch:
             try:
                 result["batch"] = batch_object(args, dev, max(5, args.steps // 2))

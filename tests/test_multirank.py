@@ -81,3 +81,41 @@ def test_reference_arm_runs_on_rank0_only():
     with redirect_stdout(buf):
         assert b.run_reference(A, 1, 2) is None
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_on_rank0():
+    """The oracle arm on rank 0: one JSON line with the median of the timed
+    steps, the sample stated, the per-column fit non-negative."""
+    import json
+    b = _bench()
+
+    class A:
+        lmax = 2
+        steps = 2
+        warmup = 1
+        gpus = 1
+        workload = "chain"
+        ncarbon = 8
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        b.run_reference(A, 0, 1)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "s" and line["value"] > 0
+    assert line["higher_is_better"] is False and line["dtype"] == "f64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and "median of 2 steps" in cb["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_sample_fit():
+    """F + u n extrapolation: the fitted per-column time is non-negative and
+    the extrapolated build is at least the sampled work."""
+    b = _bench()
+    from paper_1708_05353_gb300 import inputs
+    s = inputs.alkane(8, lmax=2)
+    smp = b.OracleSample(s, 2, pair_stride=4)
+    v, th = smp.step()
+    assert smp.u >= 0 and smp.F >= 0
+    assert v >= th
+    assert v >= smp.F + smp.u * s.nocc - 1e-12
