@@ -677,7 +677,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         pa.rtA = a.pp_rtA; pa.offA = a.pp_offA; pa.KC = a.pp_KC; pa.jc = a.pp_jc; pa.it = a.pp_it;
         pa.kca = a.pp_kca; pa.offAa = a.pp_offAa; pa.offBa = a.pp_offBa;
         pa.max_rt = a.pp_max_rt; pa.max_kca = a.pp_max_kca; pa.nleaf = a.nleaf;
-        pa.leaf_rowoff = a.leaf_rowoff; pa.leaf_aos = a.leaf_aos;
+        pa.leaf_rowoff = a.leaf_rowoff; pa.leaf_aos = a.leaf_aos; pa.leaf_rowoff_host = a.leaf_rowoff_host;
         pa.Ct = (const float*)Ct; pa.W = (const float*)W; pa.Mbox = (const float*)Mb; pa.Obox = (float*)Ob;
         pa.KB = a.kb; pa.lscale = a.lscale;
         pa.nocc = nocc; pa.nrow = a.nrow; pa.nc = nc; pa.leaf_store0 = leaf_store0;

@@ -565,6 +565,65 @@ k_pgemm_a2p(int nocc, int nc, int ntile, int leaf_store0, int nleaf, Plan pl, co
     pgemm_persistent<P, 8>(nitems, src, epi, err);
 }
 
+// Step (e), persistent: one CTA per SM walks the output tiles (global row
+// tile of the stacked leaves, 128-orbital tile, K split), the orbital tile
+// fastest so that CTAs running together share a row tile's W panels in L2;
+// the stage ring and the TMEM ping-pong carry on across tiles, so a tile's
+// ring fill and its epilogue overlap the next tile's MMAs.  Eight epilogue
+// warps stage their FP64 stores through per-warp 32 x 33 tiles (each store
+// instruction writes 32 consecutive K entries of one row).
+template <int P>
+__global__ void __launch_bounds__(kA2pThreads, 1)
+k_pgemm_l2p_pers(const int* __restrict__ leaf_rowoff, int nocc, int nrow, int nsplit, int nleaf, Plan pl,
+                 const uint8_t* __restrict__ Apan, const uint8_t* __restrict__ Bpan, double* __restrict__ KB, int* err) {
+    const long long nrt = (pl.offA[nleaf - 1] + (long long)pl.rtA[nleaf - 1] * pl.KC) / pl.KC;
+    const long long nitems = nrt * pl.it * nsplit;
+    // item -> (leaf B, row tile rt of B, orbital tile t, split ks)
+    auto decode = [&](long long item, int& B, int& rt, int& t, int& ks) {
+        ks = (int)(item % nsplit);
+        const long long rest = item / nsplit;
+        t = (int)(rest % pl.it);
+        const long long g = rest / pl.it;                // global row tile
+        int lo = 0, hi = nleaf - 1;                      // last leaf with offA / KC <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pl.offA[mid] / pl.KC <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        B = lo;
+        rt = (int)(g - pl.offA[B] / pl.KC);
+    };
+    auto src = [&](long long item, const uint8_t*& A, const uint8_t*& Bp, int& nk) {
+        int B, rt, t, ks;
+        decode(item, B, rt, t, ks);
+        const int kc0 = (int)((long long)pl.KC * ks / nsplit), kc1 = (int)((long long)pl.KC * (ks + 1) / nsplit);
+        A = Apan + (size_t)(pl.offA[B] + (long long)rt * pl.KC + kc0) * Q<P>::pbytes;
+        Bp = Bpan + (size_t)(((long long)B * pl.it + t) * pl.KC + kc0) * Q<P>::pbytes;
+        nk = kc1 - kc0;
+    };
+    auto epi = [&](long long item, int row, int col0, const float* acc) {
+        extern __shared__ __align__(1024) uint8_t smem[];
+        int B, rt, t, ks;
+        decode(item, B, rt, t, ks);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        float* tile = reinterpret_cast<float*>(smem + Q<P>::smem) + (warp - 2) * 32 * 33;
+        const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+        const int r0 = rt * 128 + (row & ~31);                  // first row of this warp
+        double* out = KB + (size_t)ks * nrow * nocc + (size_t)rb0 * nocc;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) tile[lane * 33 + q] = acc[cc * 32 + q];
+            __syncwarp();
+            const int i = t * 128 + col0 + cc * 32 + lane;
+            for (int r = 0; r < 32; ++r)
+                if (r0 + r < nr && i < nocc) out[(size_t)(r0 + r) * nocc + i] = (double)tile[r * 33 + lane];
+            __syncwarp();
+        }
+    };
+    pgemm_persistent<P, 8>(nitems, src, epi, err);
+}
+
 // blockIdx.z = leaf * nsplit + split: a split runs its share of the K panels
 // and writes its own copy of KB (the K reduction adds the copies)
 template <int P>
@@ -650,6 +709,8 @@ cudaError_t attrs() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pgemm_a2p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kA2pSmem<P>);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pgemm_l2p_pers<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kA2pSmem<P>);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pgemm_plain<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q<P>::smem);
     if (e == cudaSuccess) done = true;
     return e;
@@ -663,9 +724,19 @@ cudaError_t l2p_typed(const PanelArgs& a, cudaStream_t s) {
     dim3 gA(a.KC, a.max_rt, a.nleaf), gB(a.KC, a.it, a.nleaf);
     k_panel_l2p_A<P><<<gA, 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, pl, a.lscale, a.panA);
     k_panel_l2p_B<P><<<gB, 128, 0, s>>>(a.Mbox, a.nocc, a.nc, a.leaf_store0, pl, a.lscale, a.panB);
-    dim3 g(a.max_rt, a.it, a.nleaf * a.nsplit);
-    k_pgemm_l2p<P><<<g, 192, Q<P>::smem, s>>>(a.leaf_rowoff, a.nocc, a.nrow, a.nsplit, pl, a.panA, a.panB, a.KB,
-                                              a.err);
+    // persistent: one CTA per SM over all (row tile, orbital tile, split)
+    // items (the per-tile grid form, k_pgemm_l2p, is kept for reference)
+    long long nrt = 0;
+    {
+        // total row tiles: from the host plan (rows of every leaf / 128)
+        for (int B = 0; B < a.nleaf; ++B)
+            nrt += (a.leaf_rowoff_host[B + 1] - a.leaf_rowoff_host[B] + 127) / 128;
+    }
+    const long long items = nrt * a.it * a.nsplit;
+    const int grid = (int)std::min<long long>(items, std::max(a.sm_count, 1));
+    if (grid > 0)
+        k_pgemm_l2p_pers<P><<<grid, kA2pThreads, kA2pSmem<P>, s>>>(a.leaf_rowoff, a.nocc, a.nrow, a.nsplit,
+                                                                 a.nleaf, pl, a.panA, a.panB, a.KB, a.err);
     return cudaGetLastError();
 }
 

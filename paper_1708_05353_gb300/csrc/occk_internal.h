@@ -313,6 +313,7 @@ struct PanelArgs {
     const int* kca; const long long* offAa; const long long* offBa;  // step (a) plan
     int max_rt, max_kca, nleaf;
     const int* leaf_rowoff; const int* leaf_aos;
+    const int* leaf_rowoff_host;           // host copy (row tiles of step (e))
     const float* Ct; const float* W; const float* Mbox; float* Obox; double* KB;
     const float* lscale;
     int nocc, nrow, nc, leaf_store0;
