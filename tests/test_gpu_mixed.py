@@ -69,6 +69,27 @@ def test_mixed_farfield_water(ctx, water_ref, prec):
     assert abs(E - Er) <= K_BOUND.get(prec, 1e-4) * abs(Er)
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tc_integer_products_exact(ctx, prec):
+    """Sums of products of small integers are exact on the tensor core: with
+    |a|, |b| <= 64 every product is an integer below 2^12 and every partial
+    sum below 2^24, so the FP32 accumulation (in TMEM within a stage, in
+    registers across stages) rounds nothing; mixed magnitudes within one MMA
+    (1 next to 64) lose no low bits either."""
+    from paper_1708_05353_gb300 import occk
+    g = torch.Generator(device="cpu").manual_seed(5)
+    K = 2048
+    A = torch.randint(-64, 65, (256, K), generator=g)
+    B = torch.randint(-64, 65, (192, K), generator=g)
+    A[:8] = 64                                          # worst case: K * 64 * 64 = 2^23
+    B[:8] = 64
+    A[8:16, ::2] = 1                                    # small next to large in every K step
+    ref = A.double() @ B.double().T
+    D = occk.debug_tc_gemm(ctx, prec, A.float().cuda(), B.float().cuda()).double().cpu()
+    assert float(ref.abs().max()) == 2.0 ** 23
+    assert torch.equal(D, ref)
+
+
 @pytest.mark.parametrize("prec,bound", [("fp16x3", 5e-7), ("bf16x3", 2e-6), ("tf32", 2e-5)])
 def test_tc_long_sum_unbiased(ctx, prec, bound):
     """The tensor core's FP32 accumulation is biased toward zero over long

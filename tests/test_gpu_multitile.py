@@ -4,8 +4,9 @@ The CUDA kernels tile the occupied index by 64 (FP64 step (a)), 128 (FP32
 step (a), the tensor-core panels and pair tiles) and 96 x 128 (FP32 step (e)),
 so systems with fewer than 129 occupied orbitals leave every tile ragged.
 These tests run the 60-carbon chain (241 occupied: two full 128-wide tiles and
-a ragged one) and the 150-carbon chain of the benchmark (601 occupied, five
-tiles) and compare K columns with the FP64 oracle's exact columns, stored in
+a ragged one), the 150-carbon chain (601 occupied, five tiles) and the
+protein-sized cluster the benchmark times (3577 AOs, 660 occupied, depth 3,
+12,330 M2L edges) and compare K columns with the FP64 oracle's exact columns, stored in
 tests/golden/oracle_columns.npz by tests/golden/make_columns.py (the oracle
 alone; a column needs only the pairs (i, j) of its own i, so it is exact).
 
@@ -38,6 +39,7 @@ SYSTEMS = {
     "chain150": lambda: inputs.alkane(150, lmax=2),
     "chain150loc": lambda: inputs.alkane_localised(150, lmax=2),
     "chain150loc_screen": lambda: inputs.alkane_localised(150, lmax=2),
+    "protein": lambda: inputs.protein_like(lmax=2),
 }
 
 
@@ -137,3 +139,11 @@ def test_chain150_localised_screened(ctx, prec):
     assert kept == int(GOLD[f"{name}/kept"])
     if prec in ("fp64", "fp32"):
         assert tiles[1] > 1 and 0 < tiles[0] < tiles[1], tiles
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16x3", "bf16x3"])
+def test_protein_benchmark_workload(ctx, prec):
+    """The benchmark's headline workload at full size, in the launch
+    configuration it times (default engine and tiles, no screening): FP64 at
+    the plain bar, the single-precision forms at their bounds."""
+    check(ctx, "protein", 2, prec)
