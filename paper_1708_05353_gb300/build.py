@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libocck.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_ops.cu", "kernels_fmm.cu", "kernels_tc2.cu", "kernels_tc_translate.cu", "kernels_mlp.cu", "kernels_batch.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_ops.cu", "kernels_fmm.cu", "kernels_tc2.cu", "kernels_tc_translate.cu", "kernels_mlp.cu", "kernels_batch.cu", "noalloc.cu", "kernels_f64s.cu"]
 CPP_SOURCES = ["host.cpp"]
 
 

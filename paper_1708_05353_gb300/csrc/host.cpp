@@ -817,6 +817,64 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         l2p_nsplit = std::max(1, std::min(l2p_nsplit, nkt / 8));
         if (ctx->l2p_split > 0) l2p_nsplit = std::min(ctx->l2p_split, std::max(1, nkt));
     }
+    // FP64 step (e) from integer slices on the tensor core: every pair, all
+    // columns (the DFMA kernel serves screening and column blocks)
+    const bool sliced = prec == OCCK_FP64 && ctx->l2p_slices > 0 && ctx->col_i1 == 0 && ctx->screen_tau <= 0;
+    occk::SliceArgs sa{};
+    if (sliced) {
+        const int SK = occk::slice_stage_k(), SN = occk::slice_tile_n();
+        const int jc = (nocc + SK - 1) / SK, KC = nc * jc, nct = (nocc + SN - 1) / SN;
+        std::vector<int> rtA(nleaf);
+        std::vector<long long> offA(nleaf), item0(nleaf + 1);
+        long long cA = 0, items1 = 0;
+        int max_rt = 0;
+        for (int B = 0; B < nleaf; ++B) {
+            rtA[B] = (t->leaf_rowoff[B + 1] - t->leaf_rowoff[B] + 127) / 128;
+            offA[B] = cA;
+            cA += (long long)rtA[B] * KC;
+            items1 += (long long)rtA[B] * nct;
+            max_rt = std::max(max_rt, rtA[B]);
+        }
+        // K splits: as many as the exact int32 group sums need, more while
+        // the tiles cover the GPU less than twice (each split writes a KB copy)
+        const int need = (KC + occk::slice_max_stages() - 1) / occk::slice_max_stages();
+        const long long fill = (2LL * std::max(ctx->sm_count, 1) + items1 - 1) / std::max<long long>(items1, 1);
+        const int nsplit = std::max<int>(need, (int)std::min<long long>(fill, std::max(1, KC / 16)));
+        item0[0] = 0;
+        for (int B = 0; B < nleaf; ++B) item0[B + 1] = item0[B] + (long long)rtA[B] * nct * nsplit;
+        auto al16 = [](size_t x) { return (x + 15) / 16 * 16; };
+        const size_t o_off = al16(4 * (size_t)nleaf), o_item = o_off + al16(8 * (size_t)nleaf);
+        const size_t o_erow = o_item + al16(8 * (size_t)(nleaf + 1)), o_fcol = o_erow + al16(4 * (size_t)nrow);
+        const size_t plan_bytes = o_fcol + al16(4 * (size_t)nleaf * nocc);
+        const size_t bytes_a = occk::slice_panel_bytes(ctx->l2p_slices, true) * (size_t)cA;
+        const size_t bytes_b = occk::slice_panel_bytes(ctx->l2p_slices, false) * (size_t)nleaf * nct * KC;
+        if ((e = ensure(ctx->splan, plan_bytes)) != cudaSuccess ||
+            (e = ensure(ctx->spanels, bytes_a + bytes_b)) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "slice panels of step (e)")
+                                                  : cuda_fail(ctx, e, "slice panels of step (e)");
+        std::vector<char> hp(o_erow, 0);
+        std::memcpy(hp.data(), rtA.data(), 4 * (size_t)nleaf);
+        std::memcpy(hp.data() + o_off, offA.data(), 8 * (size_t)nleaf);
+        std::memcpy(hp.data() + o_item, item0.data(), 8 * (size_t)(nleaf + 1));
+        if ((e = cudaMemcpy(ctx->splan.p, hp.data(), o_erow, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(ctx, e, "slice plan upload");
+        char* x = (char*)ctx->splan.p;
+        sa.S = ctx->l2p_slices;
+        sa.nocc = nocc; sa.nc = nc; sa.nrow = nrow; sa.nleaf = nleaf;
+        sa.leaf_store0 = t->level_off[D] - first;
+        sa.max_rt = max_rt; sa.nsplit = nsplit; sa.sm_count = std::max(ctx->sm_count, 1);
+        sa.nitems = item0[nleaf];
+        sa.leaf_rowoff = t->dev.leaf_rowoff;
+        sa.lscale = t->dev.lscale;
+        sa.rtA = (const int*)x;
+        sa.offA = (const long long*)(x + o_off);
+        sa.item0 = (const long long*)(x + o_item);
+        sa.erow = (int*)(x + o_erow);
+        sa.fcol = (int*)(x + o_fcol);
+        sa.panA = (uint8_t*)ctx->spanels.p;
+        sa.panB = (uint8_t*)ctx->spanels.p + bytes_a;
+        l2p_nsplit = nsplit;
+    }
     size_t bytes_kb = 8 * (size_t)nrow * nocc * l2p_nsplit;
     size_t bytes_part = 8 * (size_t)(4096 + 2);
     if ((e = ensure(ctx->ct, bytes_ct)) != cudaSuccess ||
@@ -851,6 +909,13 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.leaf_rowoff_host = t->leaf_rowoff.data();
     a.max_rows = max_rows;
     a.l2p_nsplit = l2p_nsplit;
+    if (sliced) {
+        sa.W = (const double*)ctx->w.p;
+        sa.Mbox = (const double*)ctx->mbox.p;
+        sa.KB = (double*)ctx->kb.p;
+        a.slices = &sa;
+    }
+    ctx->last_sliced = sliced ? 1 : 0;
     a.learned = 0;
     ctx->ranks_valid = 0;
     const int nm2l = (int)t->m2l_tgt.size();
@@ -1127,6 +1192,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.lscale = d.lscale;
     a.box_scale = d.box_scale;
     a.err_word = (int*)ctx->scratch.p;
+    sa.err = a.err_word;
     e = cudaMemsetAsync(a.err_word, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "error word");
     a.ev = nullptr;
@@ -1404,6 +1470,13 @@ extern "C" occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit) {
     if (!ctx) return OCCK_ERR_ARG;
     if (nsplit < 0 || nsplit > 64) return fail(ctx, OCCK_ERR_ARG, "nsplit must be 0..64");
     ctx->l2p_split = nsplit;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_l2p_slices(occk_ctx* ctx, int slices) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (slices != 0 && slices != 6 && slices != 7) return fail(ctx, OCCK_ERR_ARG, "slices must be 0, 6 or 7");
+    ctx->l2p_slices = slices;
     return OCCK_OK;
 }
 

@@ -1,0 +1,522 @@
+// Step (e) in FP64 from integer slices on tcgen05: the error-free splitting of
+// a matrix product into products of small-integer matrices (Ozaki, Ogita,
+// Oishi and Rump, Numer. Algorithms 59 (2012) 95-118), with the slice products
+// on the tensor core and every sum of them exact.
+//
+//   KB[row][i] = sum_{lm, j} A[row][(lm, j)] B[i][(lm, j)]              (Eq. kri)
+//   A = W[lm][row][j] s_lm,   B = w_lm Mcal[lm](i, j) / s_lm            (FP64)
+//
+// (s_lm ~ the leaf-level component scale that brings every component to O(1);
+// w_lm the real-form weight times the factor 2 of K.)  Each row of A is scaled
+// by 2^-e_row and each column i of B by 2^-f_i so that the entries lie in
+// (-1, 1); an entry x is then cut into S slices
+//   x = sum_{s=1..S} q_s 2^-c_s + r,   c_s = 6 + 7 (s - 1),   |q_s| <= 64,
+// q_s = rint(x_{s-1} 2^c_s), x_s = x_{s-1} - q_s 2^-c_s (all exact in FP64),
+// |r| <= 2^-(c_S + 1).  The slices are integers, exact in FP16, and the
+// product of two is an integer of magnitude <= 2^12.  A product of slices s
+// and t carries the scale 2^-(c_s + c_t) = 2^-(12 + 7 (d - 2)), d = s + t, so
+// all pairs with the same d add into one TMEM accumulator G_d; the pairs with
+// d <= S + 1 are formed: slice s of A meets slices 1 .. S + 1 - s of B in one
+// MMA of N = 32 (S + 1 - s), the B slices lying one after another along N and
+// the groups one after another in TMEM (S MMAs per K step of 16).  Over a
+// chunk of 512 K values |G_d| <= (d - 1) 2^12 512 < 2^24, so the tensor core's
+// FP32 accumulation is exact (pinned by tests/test_gpu_mixed.py on integer data);
+// after each chunk the epilogue converts G_d to int32 (exact) and adds it to an
+// int32 sum per group and column (exact below 2^31, i.e. up to 127 chunks;
+// longer K ranges are split).  At the end of a tile
+//   KB = 2^(e_row + f_i) sum_d 2^-(12 + 7 (d - 2)) G_d                 (FP64)
+// Scaling is by powers of two throughout (the component scales s_lm are
+// rounded down to powers of two), and the slices are cut from the bits of the
+// FP64 values with integer operations: FP64 arithmetic, two operations per
+// clock and SM on this GPU, is left to the final sums.
+// The only roundings are the slices' truncation (relative 2^-(c_S + 1) of the
+// row's and the column's largest entry per product, 2^-49 for S = 7), the
+// dropped pairs d > S + 1 (smaller still) and the final FP64 sum.
+//
+// GEMM: M = 128 rows, N = 32 orbitals, K = 32 values per stage; A panels hold
+// the S slices of a 128 x 32 block (S x 8 KB), B panels of a 32 x 32 block
+// (S x 2 KB), each in the K-major no-swizzle canonical layout (8-row x 16-byte
+// core matrices, LBO 128 bytes along K, SBO 512 bytes between row groups).
+// One CTA per SM walks the tiles (leaf, row tile, orbital tile, K split):
+// warp 0 copies panels into a ring of stages (cp.async.bulk, mbarrier
+// transaction counts), warp 1 issues the MMAs, warps 2-9 drain the group
+// accumulators after every chunk (two TMEM buffers of S x 32 columns
+// alternate, so the drain of one chunk overlaps the MMAs of the next) and
+// write the tile.  Every wait is bounded; on a timeout the CTA raises the
+// error word, waits (bounded) for its copies in flight, frees TMEM and returns.
+#include <algorithm>
+#include <cstdio>
+
+#include "occk_internal.h"
+#include "tc.cuh"
+
+namespace occk {
+
+namespace {
+
+using namespace tc;
+
+constexpr uint32_t kWaitS = 1u << 22;
+constexpr int kSK = 32;              // K values of one stage
+constexpr int kSN = 32;              // orbitals of one tile
+constexpr int kChunk = 16;           // stages of one exact chunk (512 K values)
+constexpr int kMaxChunks = 127;      // chunks of one tile (int32 group sums)
+constexpr uint32_t kSLBO = 128, kSSBO = 512;
+constexpr int kAPart = 128 * kSK * 2;   // bytes of one A slice (8 KB)
+constexpr int kBPart = kSN * kSK * 2;   // bytes of one B slice (2 KB)
+
+template <int S>
+struct SL {
+    static constexpr int a_bytes = S * kAPart, b_bytes = S * kBPart;
+    static constexpr int stage = a_bytes + b_bytes;
+    static constexpr int ring = S >= 7 ? 3 : 3;
+    static constexpr int smem = ring * stage;
+    static constexpr uint32_t buf = (uint32_t)S * kSN;   // TMEM columns of one accumulator set
+};
+
+__device__ __forceinline__ void s_bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void s_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void s_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool s_wait(uint64_t* bar, uint32_t parity, const int* flag) {
+    for (uint32_t it = 0; it < kWaitS; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(const volatile int*)flag) return false;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
+
+// byte offset of element (row, k) of one slice in the canonical layout
+__device__ __forceinline__ uint32_t s_off(int row, int k) {
+    return (uint32_t)(row >> 3) * kSSBO + (uint32_t)(k >> 3) * kSLBO + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
+}
+
+// Component scales as powers of two: k_lm = floor(log2 s_lm), so that scaling
+// is exact and done on exponents; the real-form weight times the factor 2 of
+// K (Eq. kri) is +-2^a_lm (2 for m = 0, 4 for cos, -4 for sin).
+__device__ __forceinline__ int s_klm(const float* lscale, int lm) { return ilogbf(lscale[lm]); }
+__device__ __forceinline__ void s_weight(int lm, int& a, bool& neg) {
+    int l = 0;
+    while ((l + 1) * (l + 1) <= lm) ++l;
+    a = lm == l * l ? 1 : 2;
+    neg = lm != l * l && !((lm - l * l) & 1);
+}
+
+__device__ __forceinline__ size_t s_tri(int i, int j, int n) {
+    return (size_t)i * (size_t)(2 * n - i + 1) / 2 + (size_t)(j - i);
+}
+
+// Smallest E with |v| < 2^E (from the exponent field; -2000 for zero and
+// subnormal values, which then never set a maximum).
+__device__ __forceinline__ int s_expo(double v) {
+    const int ef = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    return ef == 0 ? -2000 : ef - 1022;
+}
+
+// round(v 2^t) as a 64-bit integer, from the bits of v (integer operations
+// only; the caller guarantees |v 2^t| < 2^55)
+__device__ __forceinline__ long long s_fixed(double v, int t) {
+    const long long bits = __double_as_longlong(v);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    long long mant = bits & ((1LL << 52) - 1);
+    int E = -1074;
+    if (ef != 0) {
+        mant |= 1LL << 52;
+        E = ef - 1075;
+    }
+    const int sh = E + t;
+    long long r;
+    if (sh >= 0) r = mant << min(sh, 10);
+    else if (sh > -60) r = (mant + (1LL << (-sh - 1))) >> (-sh);
+    else r = 0;
+    return bits < 0 ? -r : r;
+}
+
+// 2^k for -1022 <= k <= 1023 (clamped), built from its bits
+__device__ __forceinline__ double s_pow2(int k) {
+    k = max(-1022, min(1023, k));
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+__device__ __forceinline__ int s_warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// e_row: one warp per stored row, the exponent bound of max |W 2^k_lm| over (lm, j)
+__global__ void k_s_rowexp(const double* __restrict__ W, const float* __restrict__ lscale, int nrow, int nocc,
+                           int nc, int* __restrict__ erow) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= nrow) return;
+    int m = -2000;
+    for (int lm = 0; lm < nc; ++lm) {
+        const int k = s_klm(lscale, lm);
+        const double* w = W + ((size_t)lm * nrow + row) * nocc;
+        for (int j = lane; j < nocc; j += 32) m = max(m, s_expo(w[j]) + k);
+    }
+    m = s_warp_max(m);
+    if (lane == 0) erow[row] = m <= -1000 ? 0 : m;
+}
+
+// f_i: one warp per (leaf, orbital i), the exponent bound of
+// max |w_lm Mcal(i, j) 2^-k_lm| over (lm, j)
+__global__ void k_s_colexp(const double* __restrict__ Mbox, const float* __restrict__ lscale, int nleaf, int nocc,
+                           int nc, int leaf_store0, int* __restrict__ fcol) {
+    const long long x = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (x >= (long long)nleaf * nocc) return;
+    const int B = (int)(x / nocc), i = (int)(x % nocc);
+    const size_t P = (size_t)nocc * (nocc + 1) / 2;
+    int m = -2000;
+    for (int lm = 0; lm < nc; ++lm) {
+        int a;
+        bool neg;
+        s_weight(lm, a, neg);
+        const int k = a - s_klm(lscale, lm);
+        const double* M = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
+        for (int j = lane; j < nocc; j += 32) m = max(m, s_expo(M[i <= j ? s_tri(i, j, nocc) : s_tri(j, i, nocc)]) + k);
+    }
+    m = s_warp_max(m);
+    if (lane == 0) fcol[x] = m <= -1000 ? 0 : m;
+}
+
+// Slices of 8 consecutive K values of one row, given as integers round(x 2^55)
+// (|x| < 1): slice s is round(r_s 2^-(49 - 7 s)) of the remainder r_s, so
+// |q| <= 64 and x = sum_s q_s 2^-(6 + 7 s) + O(2^-49); stored as FP16 in
+// 16-byte rows of core matrices, part s at dst + s * part_bytes.
+template <int S>
+__device__ __forceinline__ void s_put8(uint8_t* dst, uint32_t part_bytes, long long* r) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int sh = 49 - 7 * s;
+        __half h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long long qs = (r[q] + (1LL << (sh - 1))) >> sh;
+            r[q] -= qs << sh;
+            h[q] = __int2half_rn((int)qs);
+        }
+        *reinterpret_cast<uint4*>(dst + (size_t)s * part_bytes) = *reinterpret_cast<uint4*>(h);
+    }
+}
+
+// A panels: block (stage kc, row tile rt, leaf B), thread = panel row
+template <int S>
+__global__ void __launch_bounds__(128)
+k_s_panel_A(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const float* __restrict__ lscale,
+            const int* __restrict__ erow, int nocc, int nrow, int jc, int KC, const int* __restrict__ rtA,
+            const long long* __restrict__ offA, uint8_t* __restrict__ pan) {
+    const int kc = blockIdx.x, rt = blockIdx.y, B = blockIdx.z;
+    if (rt >= rtA[B]) return;
+    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+    const int r = rt * 128 + threadIdx.x;
+    const int lm = kc / jc, j0 = (kc % jc) * kSK;
+    const bool live = r < nr;
+    const double* w = W + ((size_t)lm * nrow + rb0 + (live ? r : 0)) * nocc;
+    const int t = s_klm(lscale, lm) - (live ? erow[rb0 + r] : 0) + 55;
+    uint8_t* panel = pan + (size_t)(offA[B] + (long long)rt * KC + kc) * SL<S>::a_bytes;
+#pragma unroll
+    for (int k8 = 0; k8 < kSK; k8 += 8) {
+        long long v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + k8 + q;
+            v[q] = (live && j < nocc) ? s_fixed(w[j], t) : 0;
+        }
+        s_put8<S>(panel + s_off(threadIdx.x, k8), kAPart, v);
+    }
+}
+
+// B panels: block (4 stages, orbital tile ct, leaf B), thread = (orbital, stage)
+template <int S>
+__global__ void __launch_bounds__(128)
+k_s_panel_B(const double* __restrict__ Mbox, const float* __restrict__ lscale, const int* __restrict__ fcol,
+            int nocc, int nc, int leaf_store0, int jc, int KC, int nct, uint8_t* __restrict__ pan) {
+    const int kc = blockIdx.x * 4 + (threadIdx.x >> 5), ct = blockIdx.y, B = blockIdx.z;
+    if (kc >= KC) return;
+    const int il = threadIdx.x & 31, i = ct * kSN + il;
+    const int lm = kc / jc, j0 = (kc % jc) * kSK;
+    int a;
+    bool neg;
+    s_weight(lm, a, neg);
+    const size_t P = (size_t)nocc * (nocc + 1) / 2;
+    const double* M = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
+    const bool live = i < nocc;
+    const int t = a - s_klm(lscale, lm) - (live ? fcol[(size_t)B * nocc + i] : 0) + 55;
+    uint8_t* panel = pan + (size_t)(((long long)B * nct + ct) * KC + kc) * SL<S>::b_bytes;
+#pragma unroll
+    for (int k8 = 0; k8 < kSK; k8 += 8) {
+        long long v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + k8 + q;
+            const long long x = (live && j < nocc) ? s_fixed(M[i <= j ? s_tri(i, j, nocc) : s_tri(j, i, nocc)], t) : 0;
+            v[q] = neg ? -x : x;
+        }
+        s_put8<S>(panel + s_off(il, k8), kBPart, v);
+    }
+}
+
+struct SState {
+    uint64_t full[4], empty[4], accf[2], acce[2];
+    uint32_t tmem;
+    int abort;
+    uint32_t gp, gm;   // stages issued by the producer, consumed by the MMA thread
+};
+
+struct SGemm {
+    const int* leaf_rowoff; const int* rtA; const long long* offA; const long long* item0;
+    const int* erow; const int* fcol;
+    const uint8_t* panA; const uint8_t* panB;
+    double* KB;
+    int nleaf, nocc, nrow, KC, nct, nsplit;
+    long long nitems;
+    int* err;
+};
+
+constexpr int kSEpi = 16;                       // epilogue warps: four per TMEM lane quarter
+constexpr int kSThreads = 64 + kSEpi * 32;
+constexpr int kSCols = kSN / (kSEpi / 4);        // orbitals per epilogue thread
+
+// TMEM -> registers: 32 lanes x 8 columns of 32 bit (completion by s_tmem_wait)
+__device__ __forceinline__ void s_tmem_ld8(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void s_tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int S>
+__global__ void __launch_bounds__(kSThreads, 1)
+k_s_gemm(SGemm g) {
+    using C = SL<S>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ SState st;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (warp == 2) {
+        tmem_alloc(&st.tmem, 512);
+        tmem_relinquish();
+    }
+    if (t == 0) {
+        for (int r = 0; r < C::ring; ++r) {
+            mbar_init(&st.full[r], 1);
+            mbar_init(&st.empty[r], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&st.accf[b], 1);
+            mbar_init(&st.acce[b], kSEpi * 32);
+        }
+        st.abort = 0;
+        st.gp = 0;
+        st.gm = 0;
+        mbar_fence_init();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = st.tmem;
+    const uint32_t sbase = smem_u32(smem);
+    auto stA = [&](int r) { return sbase + (uint32_t)r * C::stage; };
+    auto stB = [&](int r) { return sbase + (uint32_t)r * C::stage + C::a_bytes; };
+    // item -> (leaf B, row tile rt, orbital tile ct, split ks, K stages kc0..kc1)
+    auto decode = [&](long long it, int& B, int& rt, int& ct, int& ks, int& kc0, int& kc1) {
+        int lo = 0, hi = g.nleaf - 1;                 // last leaf with item0 <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.item0[mid] <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        B = lo;
+        int x = (int)(it - g.item0[B]);   // items of one leaf: below 2^31
+        ct = x % g.nct;
+        x /= g.nct;
+        rt = x % g.rtA[B];
+        ks = x / g.rtA[B];
+        kc0 = g.KC * ks / g.nsplit;       // KC * nsplit below 2^31
+        kc1 = g.KC * (ks + 1) / g.nsplit;
+    };
+    if (warp == 0) {
+        if (lane == 0) {   // producer
+            uint32_t gs = 0;
+            for (long long it = blockIdx.x; it < g.nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                int B, rt, ct, ks, kc0, kc1;
+                decode(it, B, rt, ct, ks, kc0, kc1);
+                const uint8_t* A = g.panA + (size_t)(g.offA[B] + (long long)rt * g.KC) * C::a_bytes;
+                const uint8_t* Bp = g.panB + (size_t)(((long long)B * g.nct + ct) * g.KC) * C::b_bytes;
+                for (int kc = kc0; kc < kc1; ++kc, ++gs) {
+                    const int r = (int)(gs % C::ring);
+                    if (gs >= (uint32_t)C::ring && !s_wait(&st.empty[r], ((gs / C::ring) - 1) & 1, &st.abort)) {
+                        st.abort = 1;
+                        break;
+                    }
+                    s_expect_tx(&st.full[r], (uint32_t)C::stage);
+                    s_bulk_g2s(stA(r), A + (size_t)kc * C::a_bytes, C::a_bytes, &st.full[r]);
+                    s_bulk_g2s(stB(r), Bp + (size_t)kc * C::b_bytes, C::b_bytes, &st.full[r]);
+                    st.gp = gs + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issue
+            uint32_t gs = 0, gc = 0;
+            for (long long it = blockIdx.x; it < g.nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                int B, rt, ct, ks, kc0, kc1;
+                decode(it, B, rt, ct, ks, kc0, kc1);
+                for (int kc = kc0; kc < kc1; ++kc, ++gs) {
+                    const int r = (int)(gs % C::ring), q = (kc - kc0) % kChunk;
+                    const int b = (int)(gc & 1);
+                    if (!s_wait(&st.full[r], (gs / C::ring) & 1, &st.abort) ||
+                        (q == 0 && gc >= 2 && !s_wait(&st.acce[b], ((gc >> 1) - 1) & 1, &st.abort))) {
+                        st.abort = 1;
+                        break;
+                    }
+                    fence_after_sync();
+                    // A slice s against B slices 0 .. S-1-s in one MMA: the B
+                    // slices lie one after another along N (32 rows each), and
+                    // the products land in groups s .. S-1, 32 TMEM columns each
+                    const uint32_t d0 = tmem + (uint32_t)b * C::buf;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const uint32_t idesc = instr_desc(128, kSN * (S - s), 0u);   // FP16 x FP16 -> FP32
+#pragma unroll
+                        for (int k16 = 0; k16 < kSK / 16; ++k16) {
+                            const uint32_t adv = (uint32_t)k16 * 2u * kSLBO;
+                            const uint64_t ad = smem_desc(stA(r) + (uint32_t)s * kAPart + adv, kSLBO, kSSBO);
+                            const uint64_t bd = smem_desc(stB(r) + adv, kSLBO, kSSBO);
+                            const uint32_t acc = (q == 0 && s == 0 && k16 == 0) ? 0u : 1u;
+                            mma_f16(d0 + (uint32_t)s * kSN, ad, bd, idesc, acc);
+                        }
+                    }
+                    mma_commit(&st.empty[r]);
+                    st.gm = gs + 1;
+                    if (q == kChunk - 1 || kc == kc1 - 1) {
+                        mma_commit(&st.accf[b]);
+                        ++gc;
+                    }
+                }
+            }
+            if (gc > 0) s_wait(&st.accf[(gc - 1) & 1], ((gc - 1) >> 1) & 1, &st.abort);
+        }
+    } else {   // warps 2..9: drain the group accumulators, write the tile
+        const int q4 = warp & 3, part = (warp - 2) >> 2;   // TMEM lane quarter, share of the orbitals
+        const int row = q4 * 32 + lane;
+        uint32_t gc = 0;
+        for (long long it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+            int B, rt, ct, ks, kc0, kc1;
+            decode(it, B, rt, ct, ks, kc0, kc1);
+            const int nch = (kc1 - kc0 + kChunk - 1) / kChunk;
+            int acc[S][kSCols];   // exact: every chunk adds less than 2^24, at most 127 chunks
+#pragma unroll
+            for (int d = 0; d < S; ++d)
+#pragma unroll
+                for (int c = 0; c < kSCols; ++c) acc[d][c] = 0;
+            bool ok = true;
+            for (int ch = 0; ch < nch; ++ch, ++gc) {
+                const int b = (int)(gc & 1);
+                if (*(volatile int*)&st.abort || !s_wait(&st.accf[b], (gc >> 1) & 1, &st.abort)) {
+                    st.abort = 1;
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t base =
+                    tmem + (uint32_t)b * C::buf + (uint32_t)(part * kSCols) + ((uint32_t)(q4 * 32) << 16);
+#pragma unroll
+                for (int d = 0; d < S; ++d) {
+                    uint32_t v[kSCols];
+#pragma unroll
+                    for (int c8 = 0; c8 < kSCols; c8 += 8) s_tmem_ld8(base + (uint32_t)(d * kSN + c8), v + c8);
+                    s_tmem_wait();
+#pragma unroll
+                    for (int c = 0; c < kSCols; ++c) acc[d][c] += __float2int_rn(__uint_as_float(v[c]));
+                }
+                fence_before_sync();
+                s_arrive(&st.acce[b]);
+            }
+            if (!ok) break;
+            const int rb0 = g.leaf_rowoff[B], nr = g.leaf_rowoff[B + 1] - rb0;
+            const int rr = rt * 128 + row;
+            if (rr >= nr) continue;
+            const double se = s_pow2(g.erow[rb0 + rr]);
+            double* out = g.KB + ((size_t)ks * g.nrow + rb0 + rr) * g.nocc;
+            const int* fc = g.fcol + (size_t)B * g.nocc;
+            // group by group, smallest first (each term is exact), so that a
+            // group's sums are dead once added
+            double v[kSCols];
+#pragma unroll
+            for (int c = 0; c < kSCols; ++c) v[c] = 0.0;
+#pragma unroll
+            for (int d = S - 1; d >= 0; --d)
+#pragma unroll
+                for (int c = 0; c < kSCols; ++c) v[c] = fma((double)acc[d][c], s_pow2(-(12 + 7 * d)), v[c]);
+#pragma unroll
+            for (int c = 0; c < kSCols; ++c) {
+                const int i = ct * kSN + part * kSCols + c;
+                if (i < g.nocc) out[i] = v[c] * se * s_pow2(fc[i]);
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (t == 0 && st.abort) {
+        atomicExch(g.err, 1);
+        // copies issued but never consumed: wait (bounded) until they land
+        for (uint32_t gs = st.gm; gs < st.gp; ++gs)
+            mbar_wait_bounded(&st.full[gs % C::ring], (gs / C::ring) & 1, kWaitS);
+    }
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 2) tmem_dealloc(tmem, 512);
+}
+
+template <int S>
+cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_s_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int jc = (a.nocc + kSK - 1) / kSK, KC = a.nc * jc, nct = (a.nocc + kSN - 1) / kSN;
+    k_s_rowexp<<<(a.nrow + 7) / 8, 256, 0, s>>>(a.W, a.lscale, a.nrow, a.nocc, a.nc, a.erow);
+    const long long ncol = (long long)a.nleaf * a.nocc;
+    k_s_colexp<<<(unsigned)((ncol + 7) / 8), 256, 0, s>>>(a.Mbox, a.lscale, a.nleaf, a.nocc, a.nc, a.leaf_store0,
+                                                          a.fcol);
+    k_s_panel_A<S><<<dim3(KC, a.max_rt, a.nleaf), 128, 0, s>>>(a.leaf_rowoff, a.W, a.lscale, a.erow, a.nocc, a.nrow,
+                                                               jc, KC, a.rtA, a.offA, a.panA);
+    k_s_panel_B<S><<<dim3((KC + 3) / 4, nct, a.nleaf), 128, 0, s>>>(a.Mbox, a.lscale, a.fcol, a.nocc, a.nc,
+                                                                    a.leaf_store0, jc, KC, nct, a.panB);
+    SGemm g{};
+    g.leaf_rowoff = a.leaf_rowoff; g.rtA = a.rtA; g.offA = a.offA; g.item0 = a.item0;
+    g.erow = a.erow; g.fcol = a.fcol; g.panA = a.panA; g.panB = a.panB; g.KB = a.KB;
+    g.nleaf = a.nleaf; g.nocc = a.nocc; g.nrow = a.nrow; g.KC = KC; g.nct = nct; g.nsplit = a.nsplit;
+    g.nitems = a.nitems; g.err = a.err;
+    const int grid = (int)std::min<long long>(a.nitems, a.sm_count);
+    if (grid > 0) k_s_gemm<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int slice_stage_k() { return kSK; }
+int slice_tile_n() { return kSN; }
+int slice_max_stages() { return kChunk * kMaxChunks; }
+size_t slice_panel_bytes(int S, bool a) { return (size_t)S * (a ? kAPart : kBPart); }
+
+cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s) {
+    if (a.S == 7) return l2p_slices_typed<7>(a, s);
+    if (a.S == 6) return l2p_slices_typed<6>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace occk

@@ -923,6 +923,10 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         pa.panB = a.pan_l2pB;
         cudaError_t e2 = panel_l2p(a.prec, pa, s);
         if (e2 != cudaSuccess) return e2;
+    } else if (sizeof(T) == 8 && a.slices) {
+        // FP64 from integer slices on the tensor core (kernels_f64s.cu)
+        cudaError_t e2 = l2p_slices(*a.slices, s);
+        if (e2 != cudaSuccess) return e2;
     } else if constexpr (sizeof(T) == 8) {
         // 32 AO rows x 128 orbitals per block: leaves hold ~70-600 AOs, and a
         // 64-row tile would spend a third of the DFMA on padding

@@ -1,0 +1,118 @@
+"""FP64 step (e) from integer slices on the tensor core (occk_set_l2p_slices).
+
+Step (e), K_ri = 2 sum_X sum_{j,lm} O^{rj,X}_lm Mcal^{ij}_lm(X) (Eq. kri), is
+computed from the error-free splitting of both operands into 7-bit integer
+slices (Ozaki, Ogita, Oishi and Rump 2012) with exact sums of the slice
+products on FP16 tensor-core MMAs; every other step is the FP64 path.  The
+result differs from the DFMA form only by the slices' truncation, about 2^-49
+(7 slices) or 2^-42 (6 slices) of the largest row and column entries per
+product; measured against the oracle's exact columns
+(tests/golden/oracle_columns.npz) that is about 1e-12 of max|K| for 7 slices,
+inside the plain FP64 bar (1e-10), and the tests hold it to 1e-11 (7 slices)
+and 1e-9 (6 slices), against the oracle and against the DFMA form.  Cases: several full 128-row and 32-orbital tiles (the 60-carbon
+chain, 241 orbitals, at L = 2 and L = 6), the benchmark's protein-sized
+cluster, a long K range at L = 10 (121 components, 23 exact chunks per tile)
+and a small system whose tiles are split along K to fill the GPU.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1708_05353_gb300 import inputs
+from tests.helpers import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLD = np.load(os.path.join(os.path.dirname(__file__), "golden", "oracle_columns.npz"))
+SYSTEMS = {
+    "chain60": lambda: inputs.alkane(60, lmax=2),
+    "chain20": lambda: inputs.alkane(20, lmax=10, seed_k=4),
+    "protein": lambda: inputs.protein_like(lmax=2),
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1708_05353_gb300 import occk
+    c = occk.Context(0)
+    yield c
+    c.set_l2p_slices(0)
+    c.set_pair_screen(0.0)
+
+
+def _build(ctx, s, L):
+    from paper_1708_05353_gb300 import occk
+    tree = occk.Tree(ctx, s.basis, depth=s.depth, target_atoms_per_leaf=s.target_atoms_per_leaf)
+    tree.pair_multipoles(L)
+    return tree, torch.tensor(s.C, dtype=torch.float64, device="cuda:0")
+
+
+def _run(ctx, tree, C, slices, tau=0.0):
+    from paper_1708_05353_gb300 import occk
+    ctx.set_l2p_slices(slices)
+    ctx.set_pair_screen(tau)
+    try:
+        K, E = occk.farfield_K(ctx, tree, C, prec="fp64", want_energy_host=True)
+        occk.device_status(ctx)
+    finally:
+        ctx.set_l2p_slices(0)
+        ctx.set_pair_screen(0.0)
+    return K.clone(), E
+
+
+@pytest.mark.parametrize("name,L,slices,bound", [("chain60", 2, 7, 1e-11), ("chain60", 6, 7, 1e-11),
+                                                 ("chain60", 2, 6, 1e-9), ("chain20", 10, 7, 1e-11),
+                                                 ("protein", 2, 7, 1e-11)])
+def test_sliced_l2p_oracle_columns(ctx, name, L, slices, bound):
+    s = SYSTEMS[name]()
+    tree, C = _build(ctx, s, L)
+    cols = GOLD[f"{name}/cols"]
+    Kr = GOLD[f"{name}/L{L}/K"]
+    Er = float(GOLD[f"{name}/L{L}/E_cols"])
+    K, E = _run(ctx, tree, C, slices)
+    K0, E0 = _run(ctx, tree, C, 0)
+    Kc = K[:, torch.as_tensor(cols, device=K.device)].cpu().numpy()
+    err = rel_err(Kc, Kr)
+    Ec = -0.5 * float(np.sum(s.C[:, cols] * Kc))
+    d_dfma = float((K - K0).abs().max() / K0.abs().max())
+    print(f"{name} L={L} {slices} slices: max|dK|/max|K| vs oracle {err:.2e}, vs DFMA {d_dfma:.2e}, "
+          f"|dE_cols| {abs(Ec - Er):.2e}, |E - E_dfma| {abs(E - E0):.2e}")
+    assert err < bound
+    assert abs(Ec - Er) <= bound * abs(Er)
+    assert d_dfma < bound
+    assert abs(E - E0) <= bound * abs(E0)
+
+
+def test_sliced_l2p_split_small_system(ctx):
+    """A water cluster has few tiles, so each is split along K (one K-row copy
+    per split, summed by the reduction); the result follows the DFMA form."""
+    s = inputs.water(nmol=12, lmax=4)
+    from paper_1708_05353_gb300 import occk
+    tree = occk.Tree(ctx, s.basis, depth=2)
+    tree.pair_multipoles(4)
+    C = torch.tensor(s.C, dtype=torch.float64, device="cuda:0")
+    K, E = _run(ctx, tree, C, 7)
+    K0, E0 = _run(ctx, tree, C, 0)
+    d = float((K - K0).abs().max() / K0.abs().max())
+    print(f"water12 L=4: vs DFMA {d:.2e}, |dE| {abs(E - E0):.2e}")
+    assert d < 1e-11 and abs(E - E0) <= 1e-11 * abs(E0)
+
+
+def test_screening_keeps_the_dfma_kernel(ctx):
+    """With pair screening the sliced form is not used: K equals the screened
+    DFMA result bit for bit."""
+    s = inputs.alkane_localised(30, lmax=2)
+    tree, C = _build(ctx, s, 2)
+    K1, E1 = _run(ctx, tree, C, 7, tau=1e-4)
+    K0, E0 = _run(ctx, tree, C, 0, tau=1e-4)
+    assert torch.equal(K1, K0) and E1 == E0
+
+
+def test_slices_argument(ctx):
+    from paper_1708_05353_gb300 import occk
+    for bad in (-1, 1, 5, 8):
+        with pytest.raises(occk.OcckError):
+            ctx.set_l2p_slices(bad)
