@@ -817,9 +817,9 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         l2p_nsplit = std::max(1, std::min(l2p_nsplit, nkt / 8));
         if (ctx->l2p_split > 0) l2p_nsplit = std::min(ctx->l2p_split, std::max(1, nkt));
     }
-    // FP64 step (e) from integer slices on the tensor core: every pair, all
-    // columns (the DFMA kernel serves screening and column blocks)
-    const bool sliced = prec == OCCK_FP64 && ctx->l2p_slices > 0 && ctx->col_i1 == 0 && ctx->screen_tau <= 0;
+    // FP64 steps (a) and (e) from integer slices on the tensor core: every
+    // pair, all columns (the DFMA kernels serve screening and column blocks)
+    const bool sliced = prec == OCCK_FP64 && ctx->f64_slices > 0 && ctx->col_i1 == 0 && ctx->screen_tau <= 0;
     occk::SliceArgs sa{};
     if (sliced) {
         const int SK = occk::slice_stage_k(), SN = occk::slice_tile_n();
@@ -845,21 +845,60 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         auto al16 = [](size_t x) { return (x + 15) / 16 * 16; };
         const size_t o_off = al16(4 * (size_t)nleaf), o_item = o_off + al16(8 * (size_t)nleaf);
         const size_t o_erow = o_item + al16(8 * (size_t)(nleaf + 1)), o_fcol = o_erow + al16(4 * (size_t)nrow);
-        const size_t plan_bytes = o_fcol + al16(4 * (size_t)nleaf * nocc);
-        const size_t bytes_a = occk::slice_panel_bytes(ctx->l2p_slices, true) * (size_t)cA;
-        const size_t bytes_b = occk::slice_panel_bytes(ctx->l2p_slices, false) * (size_t)nleaf * nct * KC;
+        // step (a): panels of C (128 orbitals x 32 AO rows) and of W (32
+        // orbitals x 32 AO rows) per leaf; output tiles: triangular pairs of
+        // a 128-orbital row tile and a 32-orbital column tile
+        const int nti = (nocc + 127) / 128;
+        std::vector<int> tpair, kca(nleaf);
+        std::vector<long long> offAa(nleaf), offBa(nleaf);
+        for (int ti = 0; ti < nti; ++ti)
+            for (int tj = ti * 128 / SN; tj < nct; ++tj) tpair.push_back(ti | (tj << 16));
+        long long cAa = 0, cBa = 0;
+        int max_kca = 0;
+        for (int B = 0; B < nleaf; ++B) {
+            kca[B] = (t->leaf_rowoff[B + 1] - t->leaf_rowoff[B] + SK - 1) / SK;
+            offAa[B] = cAa;
+            cAa += (long long)nti * kca[B];
+            offBa[B] = cBa;
+            cBa += (long long)nc * nct * kca[B];
+            max_kca = std::max(max_kca, kca[B]);
+        }
+        const size_t o_kca = o_fcol + al16(4 * (size_t)nleaf * nocc), o_offAa = o_kca + al16(4 * (size_t)nleaf);
+        const size_t o_offBa = o_offAa + al16(8 * (size_t)nleaf), o_tp = o_offBa + al16(8 * (size_t)nleaf);
+        const size_t o_eC = o_tp + al16(4 * tpair.size()), o_eW = o_eC + al16(4 * (size_t)nleaf * nocc);
+        const size_t plan_bytes = o_eW + al16(4 * (size_t)nleaf * nc * nocc);
+        const size_t bytes_a = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cA;
+        const size_t bytes_b = occk::slice_panel_bytes(ctx->f64_slices, false) * (size_t)nleaf * nct * KC;
+        const size_t bytes_aa = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cAa;
+        const size_t bytes_ba = occk::slice_panel_bytes(ctx->f64_slices, false) * (size_t)cBa;
         if ((e = ensure(ctx->splan, plan_bytes)) != cudaSuccess ||
-            (e = ensure(ctx->spanels, bytes_a + bytes_b)) != cudaSuccess)
-            return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "slice panels of step (e)")
-                                                  : cuda_fail(ctx, e, "slice panels of step (e)");
-        std::vector<char> hp(o_erow, 0);
+            (e = ensure(ctx->spanels, std::max(bytes_a + bytes_b, bytes_aa + bytes_ba))) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "slice panels of steps (a) and (e)")
+                                                  : cuda_fail(ctx, e, "slice panels of steps (a) and (e)");
+        std::vector<char> hp(plan_bytes, 0);
         std::memcpy(hp.data(), rtA.data(), 4 * (size_t)nleaf);
         std::memcpy(hp.data() + o_off, offA.data(), 8 * (size_t)nleaf);
         std::memcpy(hp.data() + o_item, item0.data(), 8 * (size_t)(nleaf + 1));
-        if ((e = cudaMemcpy(ctx->splan.p, hp.data(), o_erow, cudaMemcpyHostToDevice)) != cudaSuccess)
+        std::memcpy(hp.data() + o_kca, kca.data(), 4 * (size_t)nleaf);
+        std::memcpy(hp.data() + o_offAa, offAa.data(), 8 * (size_t)nleaf);
+        std::memcpy(hp.data() + o_offBa, offBa.data(), 8 * (size_t)nleaf);
+        std::memcpy(hp.data() + o_tp, tpair.data(), 4 * tpair.size());
+        if ((e = cudaMemcpy(ctx->splan.p, hp.data(), o_eC, cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(ctx, e, "slice plan upload");
         char* x = (char*)ctx->splan.p;
-        sa.S = ctx->l2p_slices;
+        sa.full = 1;
+        sa.max_kca = max_kca;
+        sa.ntp = (int)tpair.size();
+        sa.leaf_aos = t->dev.leaf_aos;
+        sa.kca = (const int*)(x + o_kca);
+        sa.offAa = (const long long*)(x + o_offAa);
+        sa.offBa = (const long long*)(x + o_offBa);
+        sa.tpair = (const int*)(x + o_tp);
+        sa.eC = (int*)(x + o_eC);
+        sa.eW = (int*)(x + o_eW);
+        sa.panAa = (uint8_t*)ctx->spanels.p;
+        sa.panBa = (uint8_t*)ctx->spanels.p + bytes_aa;
+        sa.S = ctx->f64_slices;
         sa.nocc = nocc; sa.nc = nc; sa.nrow = nrow; sa.nleaf = nleaf;
         sa.leaf_store0 = t->level_off[D] - first;
         sa.max_rt = max_rt; sa.nsplit = nsplit; sa.sm_count = std::max(ctx->sm_count, 1);
@@ -1473,10 +1512,10 @@ extern "C" occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit) {
     return OCCK_OK;
 }
 
-extern "C" occk_status occk_set_l2p_slices(occk_ctx* ctx, int slices) {
+extern "C" occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices) {
     if (!ctx) return OCCK_ERR_ARG;
     if (slices != 0 && slices != 6 && slices != 7) return fail(ctx, OCCK_ERR_ARG, "slices must be 0, 6 or 7");
-    ctx->l2p_slices = slices;
+    ctx->f64_slices = slices;
     return OCCK_OK;
 }
 

@@ -267,6 +267,82 @@ k_s_panel_B(const double* __restrict__ Mbox, const float* __restrict__ lscale, c
     }
 }
 
+// Step (a) operands: A[i][r] = C_ri (rows i, K = the leaf's AO rows r), one
+// exponent per (leaf, i); B[j][r] = W[lm][r][j], one exponent per (leaf, lm, j).
+__global__ void k_s_a2_expC(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos,
+                            const double* __restrict__ Ct, int nocc, int* __restrict__ eC) {
+    const int B = blockIdx.x, i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= nocc) return;
+    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+    int m = -2000;
+    for (int r = 0; r < nr; ++r) m = max(m, s_expo(Ct[(size_t)leaf_aos[rb0 + r] * nocc + i]));
+    eC[(size_t)B * nocc + i] = m <= -1000 ? 0 : m;
+}
+
+__global__ void k_s_a2_expW(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, int nocc, int nrow,
+                            int nc, int* __restrict__ eW) {
+    const int B = blockIdx.x / nc, lm = blockIdx.x % nc, j = blockIdx.y * blockDim.x + threadIdx.x;
+    if (j >= nocc) return;
+    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+    const double* w = W + ((size_t)lm * nrow + rb0) * nocc + j;
+    int m = -2000;
+    for (int r = 0; r < nr; ++r) m = max(m, s_expo(w[(size_t)r * nocc]));
+    eW[((size_t)B * nc + lm) * nocc + j] = m <= -1000 ? 0 : m;
+}
+
+// A panels of step (a): block (stage kc, row tile ti, leaf B), thread = orbital i
+template <int S>
+__global__ void __launch_bounds__(128)
+k_s_a2_panel_A(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const double* __restrict__ Ct,
+               const int* __restrict__ eC, int nocc, int nti, const int* __restrict__ kca,
+               const long long* __restrict__ offAa, uint8_t* __restrict__ pan) {
+    const int kc = blockIdx.x, ti = blockIdx.y, B = blockIdx.z;
+    if (kc >= kca[B]) return;
+    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+    const int i = ti * 128 + threadIdx.x;
+    const bool live = i < nocc;
+    const int t = 55 - (live ? eC[(size_t)B * nocc + i] : 0);
+    uint8_t* panel = pan + (size_t)(offAa[B] + (long long)ti * kca[B] + kc) * SL<S>::a_bytes;
+#pragma unroll
+    for (int k8 = 0; k8 < kSK; k8 += 8) {
+        long long v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = kc * kSK + k8 + q;
+            v[q] = (live && r < nr) ? s_fixed(Ct[(size_t)leaf_aos[rb0 + r] * nocc + i], t) : 0;
+        }
+        s_put8<S>(panel + s_off(threadIdx.x, k8), kAPart, v);
+    }
+}
+
+// B panels of step (a): block (4 stages, column tile tj, leaf B * nc + lm),
+// thread = (orbital j, stage)
+template <int S>
+__global__ void __launch_bounds__(128)
+k_s_a2_panel_B(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const int* __restrict__ eW,
+               int nocc, int nrow, int nc, int nct, const int* __restrict__ kca, const long long* __restrict__ offBa,
+               uint8_t* __restrict__ pan) {
+    const int B = blockIdx.z / nc, lm = blockIdx.z % nc, tj = blockIdx.y;
+    const int kc = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (kc >= kca[B]) return;
+    const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
+    const int jl = threadIdx.x & 31, j = tj * kSN + jl;
+    const bool live = j < nocc;
+    const int t = 55 - (live ? eW[((size_t)B * nc + lm) * nocc + j] : 0);
+    const double* w = W + ((size_t)lm * nrow + rb0) * nocc + j;
+    uint8_t* panel = pan + (size_t)(offBa[B] + ((long long)lm * nct + tj) * kca[B] + kc) * SL<S>::b_bytes;
+#pragma unroll
+    for (int k8 = 0; k8 < kSK; k8 += 8) {
+        long long v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = kc * kSK + k8 + q;
+            v[q] = (live && r < nr) ? s_fixed(w[(size_t)r * nocc], t) : 0;
+        }
+        s_put8<S>(panel + s_off(jl, k8), kBPart, v);
+    }
+}
+
 struct SState {
     uint64_t full[4], empty[4], accf[2], acce[2];
     uint32_t tmem;
@@ -274,12 +350,25 @@ struct SState {
     uint32_t gp, gm;   // stages issued by the producer, consumed by the MMA thread
 };
 
-struct SGemm {
+// step (e): tiles (leaf, row tile, orbital tile, K split)
+struct SGemmE {
     const int* leaf_rowoff; const int* rtA; const long long* offA; const long long* item0;
     const int* erow; const int* fcol;
     const uint8_t* panA; const uint8_t* panB;
     double* KB;
     int nleaf, nocc, nrow, KC, nct, nsplit;
+    long long nitems;
+    int* err;
+};
+
+// step (a): tiles (leaf, lm, triangular pair of a 128-orbital row tile and a
+// 32-orbital column tile)
+struct SGemmA {
+    const int* kca; const long long* offAa; const long long* offBa; const int* tpair;
+    const int* eC; const int* eW;
+    const uint8_t* panA; const uint8_t* panB;
+    double* Obox;
+    int nleaf, nocc, nc, nct, ntp, leaf_store0;
     long long nitems;
     int* err;
 };
@@ -296,9 +385,12 @@ __device__ __forceinline__ void s_tmem_ld8(uint32_t taddr, uint32_t* r) {
 }
 __device__ __forceinline__ void s_tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-template <int S>
-__global__ void __launch_bounds__(kSThreads, 1)
-k_s_gemm(SGemm g) {
+// One CTA per SM walks items it = blockIdx.x, + gridDim.x, ...:
+// src(it, A, B, nk) gives an item's first A and B panels (consecutive along K)
+// and its number of stages; out(it, row, part, acc) receives the exact group
+// sums of one output row and kSCols columns (part) at the end of the item.
+template <int S, typename Src, typename Out>
+__device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, int* err) {
     using C = SL<S>;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ SState st;
@@ -328,32 +420,14 @@ k_s_gemm(SGemm g) {
     const uint32_t sbase = smem_u32(smem);
     auto stA = [&](int r) { return sbase + (uint32_t)r * C::stage; };
     auto stB = [&](int r) { return sbase + (uint32_t)r * C::stage + C::a_bytes; };
-    // item -> (leaf B, row tile rt, orbital tile ct, split ks, K stages kc0..kc1)
-    auto decode = [&](long long it, int& B, int& rt, int& ct, int& ks, int& kc0, int& kc1) {
-        int lo = 0, hi = g.nleaf - 1;                 // last leaf with item0 <= it
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (g.item0[mid] <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        B = lo;
-        int x = (int)(it - g.item0[B]);   // items of one leaf: below 2^31
-        ct = x % g.nct;
-        x /= g.nct;
-        rt = x % g.rtA[B];
-        ks = x / g.rtA[B];
-        kc0 = g.KC * ks / g.nsplit;       // KC * nsplit below 2^31
-        kc1 = g.KC * (ks + 1) / g.nsplit;
-    };
     if (warp == 0) {
         if (lane == 0) {   // producer
             uint32_t gs = 0;
-            for (long long it = blockIdx.x; it < g.nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
-                int B, rt, ct, ks, kc0, kc1;
-                decode(it, B, rt, ct, ks, kc0, kc1);
-                const uint8_t* A = g.panA + (size_t)(g.offA[B] + (long long)rt * g.KC) * C::a_bytes;
-                const uint8_t* Bp = g.panB + (size_t)(((long long)B * g.nct + ct) * g.KC) * C::b_bytes;
-                for (int kc = kc0; kc < kc1; ++kc, ++gs) {
+            for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                const uint8_t *A, *Bp;
+                int nk;
+                src(it, A, Bp, nk);
+                for (int kc = 0; kc < nk; ++kc, ++gs) {
                     const int r = (int)(gs % C::ring);
                     if (gs >= (uint32_t)C::ring && !s_wait(&st.empty[r], ((gs / C::ring) - 1) & 1, &st.abort)) {
                         st.abort = 1;
@@ -369,11 +443,12 @@ k_s_gemm(SGemm g) {
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issue
             uint32_t gs = 0, gc = 0;
-            for (long long it = blockIdx.x; it < g.nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
-                int B, rt, ct, ks, kc0, kc1;
-                decode(it, B, rt, ct, ks, kc0, kc1);
-                for (int kc = kc0; kc < kc1; ++kc, ++gs) {
-                    const int r = (int)(gs % C::ring), q = (kc - kc0) % kChunk;
+            for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
+                const uint8_t *A, *Bp;
+                int nk;
+                src(it, A, Bp, nk);
+                for (int kc = 0; kc < nk; ++kc, ++gs) {
+                    const int r = (int)(gs % C::ring), q = kc % kChunk;
                     const int b = (int)(gc & 1);
                     if (!s_wait(&st.full[r], (gs / C::ring) & 1, &st.abort) ||
                         (q == 0 && gc >= 2 && !s_wait(&st.acce[b], ((gc >> 1) - 1) & 1, &st.abort))) {
@@ -399,7 +474,7 @@ k_s_gemm(SGemm g) {
                     }
                     mma_commit(&st.empty[r]);
                     st.gm = gs + 1;
-                    if (q == kChunk - 1 || kc == kc1 - 1) {
+                    if (q == kChunk - 1 || kc == nk - 1) {
                         mma_commit(&st.accf[b]);
                         ++gc;
                     }
@@ -411,10 +486,11 @@ k_s_gemm(SGemm g) {
         const int q4 = warp & 3, part = (warp - 2) >> 2;   // TMEM lane quarter, share of the orbitals
         const int row = q4 * 32 + lane;
         uint32_t gc = 0;
-        for (long long it = blockIdx.x; it < g.nitems; it += gridDim.x) {
-            int B, rt, ct, ks, kc0, kc1;
-            decode(it, B, rt, ct, ks, kc0, kc1);
-            const int nch = (kc1 - kc0 + kChunk - 1) / kChunk;
+        for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const uint8_t *A, *Bp;
+            int nk;
+            src(it, A, Bp, nk);
+            const int nch = (nk + kChunk - 1) / kChunk;
             int acc[S][kSCols];   // exact: every chunk adds less than 2^24, at most 127 chunks
 #pragma unroll
             for (int d = 0; d < S; ++d)
@@ -444,32 +520,13 @@ k_s_gemm(SGemm g) {
                 s_arrive(&st.acce[b]);
             }
             if (!ok) break;
-            const int rb0 = g.leaf_rowoff[B], nr = g.leaf_rowoff[B + 1] - rb0;
-            const int rr = rt * 128 + row;
-            if (rr >= nr) continue;
-            const double se = s_pow2(g.erow[rb0 + rr]);
-            double* out = g.KB + ((size_t)ks * g.nrow + rb0 + rr) * g.nocc;
-            const int* fc = g.fcol + (size_t)B * g.nocc;
-            // group by group, smallest first (each term is exact), so that a
-            // group's sums are dead once added
-            double v[kSCols];
-#pragma unroll
-            for (int c = 0; c < kSCols; ++c) v[c] = 0.0;
-#pragma unroll
-            for (int d = S - 1; d >= 0; --d)
-#pragma unroll
-                for (int c = 0; c < kSCols; ++c) v[c] = fma((double)acc[d][c], s_pow2(-(12 + 7 * d)), v[c]);
-#pragma unroll
-            for (int c = 0; c < kSCols; ++c) {
-                const int i = ct * kSN + part * kSCols + c;
-                if (i < g.nocc) out[i] = v[c] * se * s_pow2(fc[i]);
-            }
+            out(it, row, part, acc);
         }
     }
     fence_before_sync();
     __syncthreads();
     if (t == 0 && st.abort) {
-        atomicExch(g.err, 1);
+        atomicExch(err, 1);
         // copies issued but never consumed: wait (bounded) until they land
         for (uint32_t gs = st.gm; gs < st.gp; ++gs)
             mbar_wait_bounded(&st.full[gs % C::ring], (gs / C::ring) & 1, kWaitS);
@@ -479,14 +536,126 @@ k_s_gemm(SGemm g) {
     if (warp == 2) tmem_dealloc(tmem, 512);
 }
 
+
+// sum_d 2^-(12 + 7 d) G_d for kSCols columns, group by group and smallest
+// first (every term exact), so that a group's sums are dead once added
 template <int S>
-cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
+__device__ __forceinline__ void s_combine(const int (&acc)[S][kSCols], double* v) {
+#pragma unroll
+    for (int c = 0; c < kSCols; ++c) v[c] = 0.0;
+#pragma unroll
+    for (int d = S - 1; d >= 0; --d)
+#pragma unroll
+        for (int c = 0; c < kSCols; ++c) v[c] = fma((double)acc[d][c], s_pow2(-(12 + 7 * d)), v[c]);
+}
+
+// Step (e): KB[ks][row][i] for the leaf's rows and a 32-orbital tile
+template <int S>
+__global__ void __launch_bounds__(kSThreads, 1)
+k_s_gemm_e(SGemmE g) {
+    using C = SL<S>;
+    auto decode = [&](long long it, int& B, int& rt, int& ct, int& ks, int& kc0, int& kc1) {
+        int lo = 0, hi = g.nleaf - 1;                 // last leaf with item0 <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.item0[mid] <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        B = lo;
+        int x = (int)(it - g.item0[B]);   // items of one leaf: below 2^31
+        ct = x % g.nct;
+        x /= g.nct;
+        rt = x % g.rtA[B];
+        ks = x / g.rtA[B];
+        kc0 = g.KC * ks / g.nsplit;       // KC * nsplit below 2^31
+        kc1 = g.KC * (ks + 1) / g.nsplit;
+    };
+    auto src = [&](long long it, const uint8_t*& A, const uint8_t*& Bp, int& nk) {
+        int B, rt, ct, ks, kc0, kc1;
+        decode(it, B, rt, ct, ks, kc0, kc1);
+        A = g.panA + (size_t)(g.offA[B] + (long long)rt * g.KC + kc0) * C::a_bytes;
+        Bp = g.panB + (size_t)(((long long)B * g.nct + ct) * g.KC + kc0) * C::b_bytes;
+        nk = kc1 - kc0;
+    };
+    auto out = [&](long long it, int row, int part, const int (&acc)[S][kSCols]) {
+        int B, rt, ct, ks, kc0, kc1;
+        decode(it, B, rt, ct, ks, kc0, kc1);
+        const int rb0 = g.leaf_rowoff[B], nr = g.leaf_rowoff[B + 1] - rb0;
+        const int rr = rt * 128 + row;
+        if (rr >= nr) return;
+        double v[kSCols];
+        s_combine<S>(acc, v);
+        const double se = s_pow2(g.erow[rb0 + rr]);
+        double* o = g.KB + ((size_t)ks * g.nrow + rb0 + rr) * g.nocc;
+        const int* fc = g.fcol + (size_t)B * g.nocc;
+#pragma unroll
+        for (int c = 0; c < kSCols; ++c) {
+            const int i = ct * kSN + part * kSCols + c;
+            if (i < g.nocc) o[i] = v[c] * se * s_pow2(fc[i]);
+        }
+    };
+    s_gemm_body<S>(g.nitems, src, out, g.err);
+}
+
+// Step (a): O[B][lm][(i, j)] = sum_r C_ri W[lm][r][j] for i <= j, rows i of a
+// 128-orbital tile, columns j of a 32-orbital tile (Eq. motrans)
+template <int S>
+__global__ void __launch_bounds__(kSThreads, 1)
+k_s_gemm_a(SGemmA g) {
+    using C = SL<S>;
+    auto decode = [&](long long it, int& B, int& lm, int& ti, int& tj) {
+        const int tt = (int)(it % g.ntp);
+        const long long x = it / g.ntp;
+        lm = (int)(x % g.nc);
+        B = (int)(x / g.nc);
+        ti = g.tpair[tt] & 0xFFFF;
+        tj = g.tpair[tt] >> 16;
+    };
+    auto src = [&](long long it, const uint8_t*& A, const uint8_t*& Bp, int& nk) {
+        int B, lm, ti, tj;
+        decode(it, B, lm, ti, tj);
+        const int kca = g.kca[B];
+        A = g.panA + (size_t)(g.offAa[B] + (long long)ti * kca) * C::a_bytes;
+        Bp = g.panB + (size_t)(g.offBa[B] + ((long long)lm * g.nct + tj) * kca) * C::b_bytes;
+        nk = kca;
+    };
+    const size_t P = (size_t)g.nocc * (g.nocc + 1) / 2;
+    auto out = [&](long long it, int row, int part, const int (&acc)[S][kSCols]) {
+        int B, lm, ti, tj;
+        decode(it, B, lm, ti, tj);
+        const int i = ti * 128 + row;
+        if (i >= g.nocc) return;
+        double v[kSCols];
+        s_combine<S>(acc, v);
+        const double se = s_pow2(g.eC[(size_t)B * g.nocc + i]);
+        const int* ew = g.eW + ((size_t)B * g.nc + lm) * g.nocc;
+        double* o = g.Obox + ((size_t)(g.leaf_store0 + B) * g.nc + lm) * P + s_tri(i, i, g.nocc) - (size_t)i;
+#pragma unroll
+        for (int c = 0; c < kSCols; ++c) {
+            const int j = tj * kSN + part * kSCols + c;
+            if (j >= i && j < g.nocc) o[j] = v[c] * se * s_pow2(ew[j]);
+        }
+    };
+    s_gemm_body<S>(g.nitems, src, out, g.err);
+}
+
+template <int S>
+cudaError_t l2p_attrs() {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_s_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
+        cudaError_t e = cudaFuncSetAttribute(k_s_gemm_e<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_s_gemm_a<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    return cudaSuccess;
+}
+
+template <int S>
+cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
+    cudaError_t e0 = l2p_attrs<S>();
+    if (e0 != cudaSuccess) return e0;
     const int jc = (a.nocc + kSK - 1) / kSK, KC = a.nc * jc, nct = (a.nocc + kSN - 1) / kSN;
     k_s_rowexp<<<(a.nrow + 7) / 8, 256, 0, s>>>(a.W, a.lscale, a.nrow, a.nocc, a.nc, a.erow);
     const long long ncol = (long long)a.nleaf * a.nocc;
@@ -496,13 +665,35 @@ cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
                                                                jc, KC, a.rtA, a.offA, a.panA);
     k_s_panel_B<S><<<dim3((KC + 3) / 4, nct, a.nleaf), 128, 0, s>>>(a.Mbox, a.lscale, a.fcol, a.nocc, a.nc,
                                                                     a.leaf_store0, jc, KC, nct, a.panB);
-    SGemm g{};
+    SGemmE g{};
     g.leaf_rowoff = a.leaf_rowoff; g.rtA = a.rtA; g.offA = a.offA; g.item0 = a.item0;
     g.erow = a.erow; g.fcol = a.fcol; g.panA = a.panA; g.panB = a.panB; g.KB = a.KB;
     g.nleaf = a.nleaf; g.nocc = a.nocc; g.nrow = a.nrow; g.KC = KC; g.nct = nct; g.nsplit = a.nsplit;
     g.nitems = a.nitems; g.err = a.err;
     const int grid = (int)std::min<long long>(a.nitems, a.sm_count);
-    if (grid > 0) k_s_gemm<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    if (grid > 0) k_s_gemm_e<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t full_slices_typed(const SliceArgs& a, const double* Ct, double* Obox, cudaStream_t s) {
+    cudaError_t e = l2p_attrs<S>();
+    if (e != cudaSuccess) return e;
+    const int nct = (a.nocc + kSN - 1) / kSN, nti = (a.nocc + 127) / 128;
+    k_s_a2_expC<<<dim3(a.nleaf, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.nocc, a.eC);
+    k_s_a2_expW<<<dim3(a.nleaf * a.nc, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, a.nc,
+                                                                            a.eW);
+    k_s_a2_panel_A<S><<<dim3(a.max_kca, nti, a.nleaf), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.eC, a.nocc, nti,
+                                                                     a.kca, a.offAa, a.panAa);
+    k_s_a2_panel_B<S><<<dim3((a.max_kca + 3) / 4, nct, a.nleaf * a.nc), 128, 0, s>>>(
+        a.leaf_rowoff, a.W, a.eW, a.nocc, a.nrow, a.nc, nct, a.kca, a.offBa, a.panBa);
+    SGemmA g{};
+    g.kca = a.kca; g.offAa = a.offAa; g.offBa = a.offBa; g.tpair = a.tpair;
+    g.eC = a.eC; g.eW = a.eW; g.panA = a.panAa; g.panB = a.panBa; g.Obox = Obox;
+    g.nleaf = a.nleaf; g.nocc = a.nocc; g.nc = a.nc; g.nct = nct; g.ntp = a.ntp; g.leaf_store0 = a.leaf_store0;
+    g.nitems = (long long)a.nleaf * a.nc * a.ntp; g.err = a.err;
+    const int grid = (int)std::min<long long>(g.nitems, a.sm_count);
+    if (grid > 0) k_s_gemm_a<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -512,6 +703,12 @@ int slice_stage_k() { return kSK; }
 int slice_tile_n() { return kSN; }
 int slice_max_stages() { return kChunk * kMaxChunks; }
 size_t slice_panel_bytes(int S, bool a) { return (size_t)S * (a ? kAPart : kBPart); }
+
+cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cudaStream_t s) {
+    if (a.S == 7) return full_slices_typed<7>(a, Ct, Obox, s);
+    if (a.S == 6) return full_slices_typed<6>(a, Ct, Obox, s);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s) {
     if (a.S == 7) return l2p_slices_typed<7>(a, s);

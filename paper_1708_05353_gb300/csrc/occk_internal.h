@@ -165,8 +165,8 @@ struct occk_ctx {
     occk::DevBuf scr_o, scr_m, scr_aux;     // compacted pair expansions; norms, keep/inverse maps, count
     int last_slot = 0;                      // last run used the slot pipeline
     int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
-    int l2p_slices = 0;                     // FP64 step (e) from integer slices on the tensor core (0: DFMA)
-    int last_sliced = 0;                    // the last occk_farfield_K ran step (e) from slices
+    int f64_slices = 0;                     // FP64 steps (a), (e) from integer slices on the tensor core (0: DFMA)
+    int last_sliced = 0;                    // the last occk_farfield_K ran steps (a), (e) from slices
     occk::DevBuf splan, spanels;            // its plan (row tiles, panel and item offsets, exponents), panels
     // stage timers
     int timing = 0;
@@ -207,7 +207,7 @@ struct FmmArgs {
     const int* leaf_rowoff_host;     // host copy (max rows)
     int max_rows;
     int l2p_nsplit;                  // step (e) K-range splits, FP32 and mixed forms (KB holds that many copies)
-    const SliceArgs* slices;         // FP64 step (e) from integer slices (nullptr: DFMA kernel)
+    const SliceArgs* slices;         // FP64 steps (a), (e) from integer slices (nullptr: DFMA kernels)
     cudaEvent_t* ev;                 // OCCK_NSTAGE+1 events or nullptr
     // tensor-core forms
     const float* lscale;             // [nc] sqrt((l+m)!(l-m)!) / h_leaf^l
@@ -332,7 +332,7 @@ int panel_elem_bytes(int prec);
 int panel_bytes(int prec);
 cudaError_t panel_l2p(int prec, const PanelArgs& a, cudaStream_t s);
 cudaError_t panel_a2(int prec, const PanelArgs& a, cudaStream_t s);
-// ----- FP64 step (e) from integer slices on the tensor core (kernels_f64s.cu) -----
+// ----- FP64 steps (a) and (e) from integer slices on the tensor core (kernels_f64s.cu) -----
 struct SliceArgs {
     int S;                                  // slices per operand (6 or 7)
     int nocc, nc, nrow, nleaf, leaf_store0, max_rt, nsplit, sm_count;
@@ -344,12 +344,20 @@ struct SliceArgs {
     uint8_t* panA; uint8_t* panB;
     double* KB;
     int* err;
+    // step (a) (the full transform) from slices
+    int full;                               // step (a) too
+    int max_kca, ntp;                       // K stages of the largest leaf, triangular tile pairs
+    const int* leaf_aos;
+    const int* kca; const long long* offAa; const long long* offBa; const int* tpair;
+    int* eC; int* eW;                       // exponents of C (leaf, i) and W (leaf, lm, j)
+    uint8_t* panAa; uint8_t* panBa;
 };
 int slice_stage_k();                        // K values of one panel stage
 int slice_tile_n();                         // orbitals of one GEMM tile
 int slice_max_stages();                     // stages of one tile (exact int32 group sums)
 size_t slice_panel_bytes(int S, bool a);    // bytes of one A (a) or B panel
 cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s);
+cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cudaStream_t s);
 
 // Polls allowed to the MMA thread's operand wait in the panel GEMMs of steps
 // (a) and (e) on the current device (< 0 restores the default 2^22).

@@ -79,7 +79,7 @@ _SIGS = {
     "occk_set_translate_engine": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "occk_set_l2p_split": (ctypes.c_int, [_vp, ctypes.c_int]),
-    "occk_set_l2p_slices": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_set_fp64_slices": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_pair_screen": (ctypes.c_int, [_vp, ctypes.c_double]),
     "occk_pair_screen_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "occk_farfield_J": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp,
@@ -200,10 +200,10 @@ class Context:
         """K-range splits of the FP32 SIMT step (e); 0 chooses automatically."""
         self.check(lib().occk_set_l2p_split(self._h, int(nsplit)), "occk_set_l2p_split")
 
-    def set_l2p_slices(self, slices: int = 0):
-        """FP64 step (e) from integer slices on the tensor core (6 or 7
-        slices; 0: the DFMA kernel)."""
-        self.check(lib().occk_set_l2p_slices(self._h, int(slices)), "occk_set_l2p_slices")
+    def set_fp64_slices(self, slices: int = 0):
+        """FP64 steps (a) and (e) from integer slices on the tensor core (6
+        or 7 slices; 0: the DFMA kernels)."""
+        self.check(lib().occk_set_fp64_slices(self._h, int(slices)), "occk_set_fp64_slices")
 
     def set_pair_screen(self, tau: float = 0.0):
         """Occupied-pair screening threshold for occk_farfield_K (0: off)."""

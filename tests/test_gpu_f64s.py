@@ -1,18 +1,21 @@
-"""FP64 step (e) from integer slices on the tensor core (occk_set_l2p_slices).
+"""FP64 steps (a) and (e) from integer slices on the tensor core
+(occk_set_fp64_slices).
 
-Step (e), K_ri = 2 sum_X sum_{j,lm} O^{rj,X}_lm Mcal^{ij}_lm(X) (Eq. kri), is
-computed from the error-free splitting of both operands into 7-bit integer
+The full transform O^{ij}_lm = sum_r C_ri O^{rj}_lm (Eq. motrans) and the K
+assembly K_ri = 2 sum_X sum_{j,lm} O^{rj,X}_lm Mcal^{ij}_lm(X) (Eq. kri) are
+computed from the error-free splitting of their operands into 7-bit integer
 slices (Ozaki, Ogita, Oishi and Rump 2012) with exact sums of the slice
 products on FP16 tensor-core MMAs; every other step is the FP64 path.  The
-result differs from the DFMA form only by the slices' truncation, about 2^-49
-(7 slices) or 2^-42 (6 slices) of the largest row and column entries per
-product; measured against the oracle's exact columns
+result differs from the DFMA forms only by the slices' truncation, about
+2^-49 (7 slices) or 2^-42 (6 slices) of the largest row and column entries
+per product.  Against the oracle's exact columns
 (tests/golden/oracle_columns.npz) that is about 1e-12 of max|K| for 7 slices,
-inside the plain FP64 bar (1e-10), and the tests hold it to 1e-11 (7 slices)
-and 1e-9 (6 slices), against the oracle and against the DFMA form.  Cases: several full 128-row and 32-orbital tiles (the 60-carbon
-chain, 241 orbitals, at L = 2 and L = 6), the benchmark's protein-sized
-cluster, a long K range at L = 10 (121 components, 23 exact chunks per tile)
-and a small system whose tiles are split along K to fill the GPU.
+inside the plain FP64 bar (1e-10); the tests hold it to 1e-11 (7 slices) and
+1e-9 (6 slices), against the oracle and against the DFMA forms.  Cases:
+several full 128-row and 32-orbital tiles (the 60-carbon chain, 241 orbitals,
+at L = 2 and L = 6), the benchmark's protein-sized cluster, a long K range at
+L = 10 (121 components, 23 exact chunks per step (e) tile) and a small system
+whose step (e) tiles are split along K to fill the GPU.
 """
 import os
 
@@ -39,7 +42,7 @@ def ctx():
     from paper_1708_05353_gb300 import occk
     c = occk.Context(0)
     yield c
-    c.set_l2p_slices(0)
+    c.set_fp64_slices(0)
     c.set_pair_screen(0.0)
 
 
@@ -52,13 +55,13 @@ def _build(ctx, s, L):
 
 def _run(ctx, tree, C, slices, tau=0.0):
     from paper_1708_05353_gb300 import occk
-    ctx.set_l2p_slices(slices)
+    ctx.set_fp64_slices(slices)
     ctx.set_pair_screen(tau)
     try:
         K, E = occk.farfield_K(ctx, tree, C, prec="fp64", want_energy_host=True)
         occk.device_status(ctx)
     finally:
-        ctx.set_l2p_slices(0)
+        ctx.set_fp64_slices(0)
         ctx.set_pair_screen(0.0)
     return K.clone(), E
 
@@ -115,4 +118,4 @@ def test_slices_argument(ctx):
     from paper_1708_05353_gb300 import occk
     for bad in (-1, 1, 5, 8):
         with pytest.raises(occk.OcckError):
-            ctx.set_l2p_slices(bad)
+            ctx.set_fp64_slices(bad)
