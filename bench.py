@@ -44,6 +44,9 @@ METRIC = ("far-field K_ri build time (s) & TFLOP/s at stated error vs FP64 oracl
           "learned/mixed vs plain")
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_columns.npz")
 MIXED = ["fp32", "tf32", "bf16", "fp16", "bf16x3", "fp16x3"]
+# FP64 with steps (a) and (e) from 7-bit integer slices on the tensor core
+# (occk_set_fp64_slices): FP64 arithmetic everywhere else, exact slice sums
+SLICED = {"fp64s": 7, "fp64s6": 6}
 
 
 def parse(argv=None):
@@ -58,7 +61,7 @@ def parse(argv=None):
     p.add_argument("--ncarbon", type=int, default=150)
     p.add_argument("--lmax", type=int, default=2)
     p.add_argument("--prec", default="fp64", help="precision of the headline line")
-    p.add_argument("--variants", default=",".join(MIXED),
+    p.add_argument("--variants", default=",".join(["fp64s"] + MIXED),
                    help="other precisions timed on the same workload (comma list, or 'none')")
     p.add_argument("--learned-rank", type=int, default=10,
                    help="reference rank of the learned-selector comparison on the protein workload (0: skip)")
@@ -559,8 +562,8 @@ def learned_object(args, ctx, dev, system, tm):
 
 
 def chain_object(args, ctx, dev, tm):
-    """C150H302 at rank 2: FP32 (SIMT) and FP16X3 (tensor core), against the
-    FP64 GPU form and the oracle's exact columns."""
+    """C150H302 at rank 2: FP64 from integer slices, FP32 (SIMT) and FP16X3
+    (tensor core), against the FP64 GPU form and the oracle's exact columns."""
     import torch
     from paper_1708_05353_gb300 import occk
     s = make_system("chain", 2, args.ncarbon)
@@ -576,8 +579,13 @@ def chain_object(args, ctx, dev, tm):
     E64 = float(Ex.item())
     K64 = K.clone()
     out["fp64"] = {"ms": round(ms64, 4), "E": E64, **oracle_errors(gold, K64, s.C)}
-    for p in ("fp32", "fp16x3"):
-        ms, st = tm.run(lambda: occk.farfield_K(ctx, tree, C, prec=p, K=K, Ex=Ex), n, stages=True)
+    for p in ("fp64s", "fp32", "fp16x3"):
+        ctx.set_fp64_slices(SLICED.get(p, 0))
+        try:
+            ms, st = tm.run(lambda: occk.farfield_K(ctx, tree, C, prec="fp64" if p in SLICED else p, K=K, Ex=Ex), n,
+                            stages=True)
+        finally:
+            ctx.set_fp64_slices(0)
         out[p] = {"ms": round(ms, 4), "speedup_vs_fp64": round(ms64 / ms, 3),
                   "abs_dE_vs_fp64_Eh": abs(float(Ex.item()) - E64),
                   "rel_dK_vs_fp64": float((K - K64).abs().max() / K64.abs().max()),
@@ -829,8 +837,12 @@ def main(argv=None):
             kmax = float(K64.abs().max())
             var = {}
             for vp in [v for v in args.variants.split(",") if v and v != args.prec]:
-                vms, vst = tm.run(lambda: occk.farfield_K(ctx, tree, Cf, prec=vp, K=K, Ex=Ex),
-                                  max(5, args.steps // 2), stages=True)
+                ctx.set_fp64_slices(SLICED.get(vp, 0))
+                try:
+                    vms, vst = tm.run(lambda: occk.farfield_K(ctx, tree, Cf, prec="fp64" if vp in SLICED else vp,
+                                                              K=K, Ex=Ex), max(5, args.steps // 2), stages=True)
+                finally:
+                    ctx.set_fp64_slices(0)
                 var[vp] = {"ms": round(vms, 4), "speedup_vs_fp64": round(ms64 / vms, 3),
                            "tflops": round(total_flops / (vms * 1e-3) / 1e12, 3),
                            "abs_dE_vs_fp64_Eh": abs(float(Ex.item()) - E64),
@@ -840,7 +852,9 @@ def main(argv=None):
             result["variants"] = var
             result["variants_reference"] = ("speed-up and errors against the FP64 GPU form of the same run "
                                             f"({ms64:.2f} ms, E = {E64:.10f} Eh), which matches the oracle's "
-                                            "columns to the stated error")
+                                            "columns to the stated error; fp64s / fp64s6: FP64 with steps (a) "
+                                            "and (e) from 7 / 6 integer slices on the tensor core (tflops: FP64 "
+                                            "FLOPs of the algorithm per second)")
         if args.workload == "protein" and args.learned_rank > 0:
             try:
                 result["learned"] = learned_object(args, ctx, dev, system, tm)

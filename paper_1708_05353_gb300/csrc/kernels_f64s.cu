@@ -537,16 +537,24 @@ __device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, 
 }
 
 
-// sum_d 2^-(12 + 7 d) G_d for kSCols columns, group by group and smallest
-// first (every term exact), so that a group's sums are dead once added
+// sum_d 2^-(12 + 7 d) G_d for kSCols columns.  The groups are first combined
+// exactly in two 64-bit integers, vh = sum_{d<3} G_d 2^(7 (2 - d)) (below
+// 2^46) and vl = sum_{d>=3} G_d 2^(7 (S - 1 - d)) (below 2^60), so that only
+// two conversions and one FMA run on the FP64 pipe (two operations per clock
+// and SM on this GPU): vh converts exactly, vl with a rounding far below the
+// result's last bit.
 template <int S>
 __device__ __forceinline__ void s_combine(const int (&acc)[S][kSCols], double* v) {
 #pragma unroll
-    for (int c = 0; c < kSCols; ++c) v[c] = 0.0;
+    for (int c = 0; c < kSCols; ++c) {
+        long long vh = 0, vl = 0;
 #pragma unroll
-    for (int d = S - 1; d >= 0; --d)
-#pragma unroll
-        for (int c = 0; c < kSCols; ++c) v[c] = fma((double)acc[d][c], s_pow2(-(12 + 7 * d)), v[c]);
+        for (int d = 0; d < S; ++d) {
+            if (d < 3) vh += (long long)acc[d][c] << (7 * (2 - d));
+            else vl += (long long)acc[d][c] << (7 * (S - 1 - d));
+        }
+        v[c] = fma((double)vl, s_pow2(-(12 + 7 * (S - 1))), (double)vh * s_pow2(-26));
+    }
 }
 
 // Step (e): KB[ks][row][i] for the leaf's rows and a 32-orbital tile
@@ -585,13 +593,13 @@ k_s_gemm_e(SGemmE g) {
         if (rr >= nr) return;
         double v[kSCols];
         s_combine<S>(acc, v);
-        const double se = s_pow2(g.erow[rb0 + rr]);
+        const int er = g.erow[rb0 + rr];
         double* o = g.KB + ((size_t)ks * g.nrow + rb0 + rr) * g.nocc;
         const int* fc = g.fcol + (size_t)B * g.nocc;
 #pragma unroll
         for (int c = 0; c < kSCols; ++c) {
             const int i = ct * kSN + part * kSCols + c;
-            if (i < g.nocc) o[i] = v[c] * se * s_pow2(fc[i]);
+            if (i < g.nocc) o[i] = v[c] * s_pow2(er + fc[i]);
         }
     };
     s_gemm_body<S>(g.nitems, src, out, g.err);
@@ -627,13 +635,13 @@ k_s_gemm_a(SGemmA g) {
         if (i >= g.nocc) return;
         double v[kSCols];
         s_combine<S>(acc, v);
-        const double se = s_pow2(g.eC[(size_t)B * g.nocc + i]);
+        const int ec = g.eC[(size_t)B * g.nocc + i];
         const int* ew = g.eW + ((size_t)B * g.nc + lm) * g.nocc;
         double* o = g.Obox + ((size_t)(g.leaf_store0 + B) * g.nc + lm) * P + s_tri(i, i, g.nocc) - (size_t)i;
 #pragma unroll
         for (int c = 0; c < kSCols; ++c) {
             const int j = tj * kSN + part * kSCols + c;
-            if (j >= i && j < g.nocc) o[j] = v[c] * se * s_pow2(ew[j]);
+            if (j >= i && j < g.nocc) o[j] = v[c] * s_pow2(ec + ew[j]);
         }
     };
     s_gemm_body<S>(g.nitems, src, out, g.err);
