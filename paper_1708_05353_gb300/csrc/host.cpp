@@ -866,7 +866,9 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         const size_t o_kca = o_fcol + al16(4 * (size_t)nleaf * nocc), o_offAa = o_kca + al16(4 * (size_t)nleaf);
         const size_t o_offBa = o_offAa + al16(8 * (size_t)nleaf), o_tp = o_offBa + al16(8 * (size_t)nleaf);
         const size_t o_eC = o_tp + al16(4 * tpair.size()), o_eW = o_eC + al16(4 * (size_t)nleaf * nocc);
-        const size_t plan_bytes = o_eW + al16(4 * (size_t)nleaf * nc * nocc);
+        const size_t nops = t->ops.size();
+        const size_t o_ff = o_eW + al16(4 * (size_t)nleaf * nc * nocc);
+        const size_t plan_bytes = o_ff + al16(8 * nops * nc * nc);
         const size_t bytes_a = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cA;
         const size_t bytes_b = occk::slice_panel_bytes(ctx->f64_slices, false) * (size_t)nleaf * nct * KC;
         const size_t bytes_aa = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cAa;
@@ -896,6 +898,9 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         sa.tpair = (const int*)(x + o_tp);
         sa.eC = (int*)(x + o_eC);
         sa.eW = (int*)(x + o_eW);
+        sa.ff = 1;
+        sa.nops = (int)nops;
+        sa.ops_ff = (float2*)(x + o_ff);
         sa.panAa = (uint8_t*)ctx->spanels.p;
         sa.panBa = (uint8_t*)ctx->spanels.p + bytes_aa;
         sa.S = ctx->f64_slices;

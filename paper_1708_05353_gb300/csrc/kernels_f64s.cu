@@ -647,6 +647,120 @@ k_s_gemm_a(SGemmA g) {
     s_gemm_body<S>(g.nitems, src, out, g.err);
 }
 
+// ---------------------------------------------------------------------------
+// M2L with L2L (Eqs. fmmex, fmm2, fmm3) in double-FP32 arithmetic for the
+// sliced FP64 form: every value is an unevaluated sum hi + lo of two FP32
+// numbers (about 48 significant bits) and every multiply-add is done with the
+// error-free product (FMA) and sum (Knuth's TwoSum) of Dekker's and Knuth's
+// double-length arithmetic, about 11 FP32 operations on the FP32 pipe, which
+// issues 64 times as many operations per clock as the FP64 pipe here.  The
+// multipoles are split into (hi, lo) in place before the level loop and the
+// local expansions joined back to FP64 after it; the kernel is the per-level
+// fused pass of the FP64 form (each target written once from its interaction
+// list and its parent's finished expansion), the same sums in the same order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ff_fma(float& h, float& l, float2 w, float2 v) {
+    const float p = __fmul_rn(w.x, v.x);
+    float e = fmaf(w.x, v.x, -p);                 // p + e = w.x v.x exactly
+    e = fmaf(w.x, v.y, e);
+    e = fmaf(w.y, v.x, e);
+    const float sum = __fadd_rn(h, p);            // TwoSum(h, p)
+    const float bb = __fsub_rn(sum, h);
+    const float t = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+    l = __fadd_rn(l, __fadd_rn(t, e));
+    h = sum;
+}
+
+__global__ void k_ff_split(double* x, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double v = x[k];
+        const float h = __double2float_rn(v);
+        const float l = __double2float_rn(v - (double)h);
+        reinterpret_cast<float2*>(x)[k] = make_float2(h, l);
+    }
+}
+
+__global__ void k_ff_join(double* x, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const float2 f = reinterpret_cast<const float2*>(x)[k];
+        x[k] = (double)f.x + (double)f.y;
+    }
+}
+
+__global__ void k_ff_ops(const double* __restrict__ ops, size_t n, float2* __restrict__ out) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double v = ops[k];
+        const float h = __double2float_rn(v);
+        out[k] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+}
+
+constexpr int kFFNcMax = 169;
+
+// one level: block (target, 128 pairs, chunk of LMC output components)
+template <int LMC>
+__global__ void __launch_bounds__(128)
+k_m2l_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr, const int* __restrict__ list,
+         const int* __restrict__ opidx, const int* __restrict__ lmax_e, const int* __restrict__ parent,
+         const int* __restrict__ l2l_opidx, const float2* __restrict__ ops, const float2* __restrict__ in,
+         float2* out) {
+    __shared__ float2 sop[kFFNcMax][LMC];   // [input component][output component of the chunk]
+    const int tgt = tgt0 + blockIdx.x;
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    const int c0 = blockIdx.z * LMC;
+    const int ncl = min(LMC, nc - c0);
+    const bool live = p < P;
+    float ah[LMC], al[LMC];
+#pragma unroll
+    for (int q = 0; q < LMC; ++q) ah[q] = al[q] = 0.f;
+    const int e0 = ptr[tgt], e1 = ptr[tgt + 1];
+    const int eend = e1 + (parent[tgt] >= first_box ? 1 : 0);   // then the parent's local expansion
+    int llo = 0;
+    while ((llo + 1) * (llo + 1) <= c0) ++llo;
+    for (int e = e0; e < eend; ++e) {
+        const bool l2l = e == e1;
+        int src, op, Le = L;
+        if (!l2l) {
+            src = list[e];
+            op = opidx[e];
+            if (lmax_e) Le = lmax_e[e];
+        } else {
+            src = parent[tgt];
+            op = l2l_opidx[tgt];
+        }
+        const int ncr = (Le + 1) * (Le + 1);
+        if (c0 >= ncr) continue;   // uniform across the block
+        const int cb0 = l2l ? llo * llo : 0, cb1 = ncr;
+        const float2* Tm = ops + (size_t)op * nc * nc;
+        __syncthreads();
+        for (int x = threadIdx.x; x < LMC * (cb1 - cb0); x += blockDim.x) {
+            const int q = x / (cb1 - cb0), c = cb0 + (x - q * (cb1 - cb0));
+            sop[c][q] = (q < ncl && c0 + q < ncr) ? Tm[(size_t)(c0 + q) * nc + c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2* xs = (l2l ? out : in) + (size_t)(src - first_box) * nc * P + p;
+        for (int cb = cb0; cb < cb1; cb += 4) {
+            float2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = (cb + u < cb1 && live) ? xs[(size_t)(cb + u) * P] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (cb + u >= cb1) break;      // uniform across the block
+#pragma unroll
+                for (int q = 0; q < LMC; ++q) ff_fma(ah[q], al[q], sop[cb + u][q], v[u]);
+            }
+        }
+    }
+    if (!live) return;
+    float2* o = out + ((size_t)(tgt - first_box) * nc + c0) * P + p;
+#pragma unroll
+    for (int q = 0; q < LMC; ++q)
+        if (q < ncl) {
+            const float h = __fadd_rn(ah[q], al[q]);       // renormalise (Fast2Sum)
+            o[(size_t)q * P] = make_float2(h, __fsub_rn(al[q], __fsub_rn(h, ah[q])));
+        }
+}
+
 template <int S>
 cudaError_t l2p_attrs() {
     static bool attr = false;
@@ -716,6 +830,36 @@ cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cuda
     if (a.S == 7) return full_slices_typed<7>(a, Ct, Obox, s);
     if (a.S == 6) return full_slices_typed<6>(a, Ct, Obox, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {
+    const size_t nops = (size_t)f.nops * f.nc * f.nc;
+    const size_t n = (size_t)f.nstore * f.nc * f.P;
+    const int blocks = 4 * std::max(f.sm_count, 1);
+    k_ff_ops<<<std::max(1, (int)std::min<size_t>((nops + 255) / 256, 4096)), 256, 0, s>>>(f.ops, nops, f.ops_ff);
+    k_ff_split<<<blocks, 256, 0, s>>>(f.Ob, n);
+    const int lmc = f.nc <= 4 ? 4 : f.nc <= 9 ? 9 : f.nc <= 16 ? 16 : 25;
+    const int nchunk = (f.nc + lmc - 1) / lmc;
+    for (int lev = 2; lev <= f.D; ++lev) {
+        const int t0 = f.level_off[lev], nt = f.level_off[lev + 1] - t0;
+        if (nt <= 0) continue;
+        dim3 g(nt, (unsigned)((f.P + 127) / 128), nchunk);
+        auto* in = reinterpret_cast<const float2*>(f.Ob);
+        auto* out = reinterpret_cast<float2*>(f.Mb);
+        switch (lmc) {
+            case 4: k_m2l_ff<4><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
+                                                  f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
+            case 9: k_m2l_ff<9><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
+                                                  f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
+            case 16: k_m2l_ff<16><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
+                                                    f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
+            default: k_m2l_ff<25><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
+                                                    f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
+        }
+    }
+    k_ff_join<<<blocks, 256, 0, s>>>(f.Ob, n);
+    k_ff_join<<<blocks, 256, 0, s>>>(f.Mb, n);
+    return cudaGetLastError();
 }
 
 cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s) {

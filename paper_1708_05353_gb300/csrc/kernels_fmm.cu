@@ -858,7 +858,24 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
     } else if (fused) {
         // (c) and (d) together, level by level: each target is written once
         // from its interaction list and its parent's finished expansion
-        for (int lev = 2; lev <= D; ++lev) {
+        bool done = false;
+        if constexpr (sizeof(T) == 8) {
+            if (a.slices && a.slices->ff && !a.screen) {
+                // the sliced FP64 form: the same pass in double-FP32 arithmetic
+                FFArgs f{};
+                f.P = (int)P; f.nc = nc; f.L = a.L; f.D = D; f.first_box = a.first_box;
+                f.nstore = a.nbox - a.first_box; f.nops = a.slices->nops; f.sm_count = a.sm_count;
+                f.level_off = a.level_off;
+                f.m2l_ptr = a.m2l_ptr; f.m2l_src = a.m2l_src; f.m2l_op = a.m2l_op; f.lmax_e = lmax_e;
+                f.parent = a.parent; f.l2l_op = a.l2l_op;
+                f.ops = (const double*)tops; f.ops_ff = a.slices->ops_ff;
+                f.Ob = (double*)Ob; f.Mb = (double*)Mb;
+                cudaError_t e2 = m2l_ff(f, s);
+                if (e2 != cudaSuccess) return e2;
+                done = true;
+            }
+        }
+        for (int lev = 2; lev <= D && !done; ++lev) {
             int t0 = a.level_off[lev], nt = a.level_off[lev + 1] - t0;
             if (nt <= 0) continue;
             if constexpr (sizeof(T) == 4) {

@@ -351,6 +351,9 @@ struct SliceArgs {
     const int* kca; const long long* offAa; const long long* offBa; const int* tpair;
     int* eC; int* eW;                       // exponents of C (leaf, i) and W (leaf, lm, j)
     uint8_t* panAa; uint8_t* panBa;
+    // steps (c), (d) in double-FP32 arithmetic
+    int ff, nops;
+    float2* ops_ff;                         // [nops][nc][nc] (hi, lo) operators (workspace)
 };
 int slice_stage_k();                        // K values of one panel stage
 int slice_tile_n();                         // orbitals of one GEMM tile
@@ -358,6 +361,17 @@ int slice_max_stages();                     // stages of one tile (exact int32 g
 size_t slice_panel_bytes(int S, bool a);    // bytes of one A (a) or B panel
 cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s);
 cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cudaStream_t s);
+// M2L with L2L, fused per level, in double-FP32 arithmetic on the FP32 pipe
+// (the sliced FP64 form); O and Mcal are FP64 before and after the call
+struct FFArgs {
+    int P, nc, L, D, first_box, nstore, nops, sm_count;
+    const int* level_off;                   // host
+    const int* m2l_ptr; const int* m2l_src; const int* m2l_op; const int* lmax_e;
+    const int* parent; const int* l2l_op;
+    const double* ops; float2* ops_ff;      // FP64 operators; their (hi, lo) copy (written)
+    double* Ob; double* Mb;
+};
+cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s);
 
 // Polls allowed to the MMA thread's operand wait in the panel GEMMs of steps
 // (a) and (e) on the current device (< 0 restores the default 2^22).
