@@ -868,7 +868,9 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         const size_t o_eC = o_tp + al16(4 * tpair.size()), o_eW = o_eC + al16(4 * (size_t)nleaf * nocc);
         const size_t nops = t->ops.size();
         const size_t o_ff = o_eW + al16(4 * (size_t)nleaf * nc * nocc);
-        const size_t plan_bytes = o_ff + al16(8 * nops * nc * nc);
+        const size_t o_vff = o_ff + al16(8 * nops * nc * nc);
+        const size_t o_cff = o_vff + al16(8 * (size_t)t->nvals * nc);
+        const size_t plan_bytes = o_cff + al16(8 * (size_t)t->nao * nocc);
         const size_t bytes_a = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cA;
         const size_t bytes_b = occk::slice_panel_bytes(ctx->f64_slices, false) * (size_t)nleaf * nct * KC;
         const size_t bytes_aa = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cAa;
@@ -901,6 +903,9 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         sa.ff = 1;
         sa.nops = (int)nops;
         sa.ops_ff = (float2*)(x + o_ff);
+        sa.nvals = t->nvals;
+        sa.vals_ff = (float2*)(x + o_vff);
+        sa.C_ff = (float2*)(x + o_cff);
         sa.panAa = (uint8_t*)ctx->spanels.p;
         sa.panBa = (uint8_t*)ctx->spanels.p + bytes_aa;
         sa.S = ctx->f64_slices;

@@ -761,6 +761,49 @@ k_m2l_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ 
         }
 }
 
+// Step (a), first half (Eq. motrans, first line), in double-FP32 arithmetic:
+// W[lm][row][j] = sum over the row's ordered entries (r, s) of O^{rs}_lm C_sj,
+// one block per (stored AO row, chunk of LMC components), one orbital j per
+// thread, entries staged in shared memory CH at a time; C and the pair
+// values arrive split into (hi, lo), W leaves in FP64.
+template <int LMC>
+__global__ void k_half_ff(const int* __restrict__ row_ptr, const int* __restrict__ ent_col,
+                          const int* __restrict__ ent_val, const float2* __restrict__ vals, int nc,
+                          const float2* __restrict__ Cff, int nocc, int nrow, double* __restrict__ W) {
+    constexpr int CH = 64;
+    __shared__ float2 sv[CH][LMC];
+    __shared__ int scol[CH];
+    const int row = blockIdx.x, c0 = blockIdx.y * LMC;
+    const int e0 = row_ptr[row], e1 = row_ptr[row + 1];
+    const int ncl = min(LMC, nc - c0);
+    for (int jb = 0; jb < nocc; jb += blockDim.x) {
+        const int j = jb + threadIdx.x;
+        float ah[LMC], al[LMC];
+#pragma unroll
+        for (int q = 0; q < LMC; ++q) ah[q] = al[q] = 0.f;
+        for (int ec = e0; ec < e1; ec += CH) {
+            const int n = min(CH, e1 - ec);
+            __syncthreads();
+            for (int x = threadIdx.x; x < n * LMC; x += blockDim.x) {
+                const int k = x / LMC, q = x - k * LMC;
+                sv[k][q] = q < ncl ? vals[(size_t)ent_val[ec + k] * nc + c0 + q] : make_float2(0.f, 0.f);
+            }
+            for (int x = threadIdx.x; x < n; x += blockDim.x) scol[x] = ent_col[ec + x];
+            __syncthreads();
+            for (int k = 0; k < n; ++k) {
+                const float2 c = j < nocc ? Cff[(size_t)scol[k] * nocc + j] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < LMC; ++q) ff_fma(ah[q], al[q], sv[k][q], c);
+            }
+        }
+        if (j < nocc) {
+#pragma unroll
+            for (int q = 0; q < LMC; ++q)
+                if (q < ncl) W[((size_t)(c0 + q) * nrow + row) * nocc + j] = (double)ah[q] + (double)al[q];
+        }
+    }
+}
+
 template <int S>
 cudaError_t l2p_attrs() {
     static bool attr = false;
@@ -830,6 +873,24 @@ cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cuda
     if (a.S == 7) return full_slices_typed<7>(a, Ct, Obox, s);
     if (a.S == 6) return full_slices_typed<6>(a, Ct, Obox, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t half_ff(const HalfFFArgs& h, cudaStream_t s) {
+    const size_t nv = (size_t)h.nvals * h.nc, ncf = (size_t)h.nao * h.nocc;
+    k_ff_ops<<<std::max(1, (int)std::min<size_t>((nv + 255) / 256, 8192)), 256, 0, s>>>(h.vals, nv, h.vals_ff);
+    k_ff_ops<<<std::max(1, (int)std::min<size_t>((ncf + 255) / 256, 8192)), 256, 0, s>>>(h.Ct, ncf, h.C_ff);
+    dim3 g(h.nrow, (h.nc + h.lmc - 1) / h.lmc);
+    switch (h.lmc) {
+        case 4: k_half_ff<4><<<g, h.nth, 0, s>>>(h.row_ptr, h.ent_col, h.ent_val, h.vals_ff, h.nc, h.C_ff, h.nocc,
+                                                 h.nrow, h.W); break;
+        case 9: k_half_ff<9><<<g, h.nth, 0, s>>>(h.row_ptr, h.ent_col, h.ent_val, h.vals_ff, h.nc, h.C_ff, h.nocc,
+                                                 h.nrow, h.W); break;
+        case 25: k_half_ff<25><<<g, h.nth, 0, s>>>(h.row_ptr, h.ent_col, h.ent_val, h.vals_ff, h.nc, h.C_ff, h.nocc,
+                                                   h.nrow, h.W); break;
+        default: k_half_ff<16><<<g, h.nth, 0, s>>>(h.row_ptr, h.ent_col, h.ent_val, h.vals_ff, h.nc, h.C_ff, h.nocc,
+                                                   h.nrow, h.W); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {

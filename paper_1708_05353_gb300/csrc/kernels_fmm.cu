@@ -662,7 +662,18 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         const int LMC = half_chunk(nc);
         const int nth = half_threads(nocc, sizeof(T) == 4 ? 4 : 1);
         dim3 g(a.nrow, (nc + LMC - 1) / LMC);
-        switch (LMC) {
+        if (sizeof(T) == 8 && a.slices && a.slices->ff) {
+            // the sliced FP64 form: double-FP32 arithmetic (kernels_f64s.cu)
+            HalfFFArgs h{};
+            h.nao = a.nao; h.nocc = nocc; h.nrow = a.nrow; h.nc = nc; h.nvals = a.slices->nvals;
+            h.lmc = LMC; h.nth = nth;
+            h.row_ptr = a.row_ptr; h.ent_col = a.ent_col; h.ent_val = a.ent_val;
+            h.vals = (const double*)vals; h.Ct = (const double*)Ct;
+            h.vals_ff = a.slices->vals_ff; h.C_ff = a.slices->C_ff;
+            h.W = (double*)W;
+            cudaError_t e2 = half_ff(h, s);
+            if (e2 != cudaSuccess) return e2;
+        } else switch (LMC) {
             case 4: k_half<T, 4><<<g, nth, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W); break;
             case 9: k_half<T, 9><<<g, nth, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W); break;
             case 25: k_half<T, 25><<<g, nth, 0, s>>>(a.row_ptr, a.ent_col, a.ent_val, vals, nc, Ct, nocc, a.nrow, W); break;

@@ -352,8 +352,9 @@ struct SliceArgs {
     int* eC; int* eW;                       // exponents of C (leaf, i) and W (leaf, lm, j)
     uint8_t* panAa; uint8_t* panBa;
     // steps (c), (d) in double-FP32 arithmetic
-    int ff, nops;
+    int ff, nops, nvals;
     float2* ops_ff;                         // [nops][nc][nc] (hi, lo) operators (workspace)
+    float2* vals_ff; float2* C_ff;          // (hi, lo) pair values and transposed C (workspace)
 };
 int slice_stage_k();                        // K values of one panel stage
 int slice_tile_n();                         // orbitals of one GEMM tile
@@ -372,6 +373,15 @@ struct FFArgs {
     double* Ob; double* Mb;
 };
 cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s);
+// step (a), first half, in double-FP32 arithmetic (the sliced FP64 form)
+struct HalfFFArgs {
+    int nao, nocc, nrow, nc, nvals, lmc, nth;
+    const int* row_ptr; const int* ent_col; const int* ent_val;
+    const double* vals; const double* Ct;   // FP64 inputs
+    float2* vals_ff; float2* C_ff;          // their (hi, lo) copies (workspace, written)
+    double* W;
+};
+cudaError_t half_ff(const HalfFFArgs& h, cudaStream_t s);
 
 // Polls allowed to the MMA thread's operand wait in the panel GEMMs of steps
 // (a) and (e) on the current device (< 0 restores the default 2^22).
