@@ -450,27 +450,32 @@ occk_status occk_set_m2l_group(occk_ctx* ctx, int mode);
  * choice. */
 occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit);
 
-/* Steps (a) and (e) of the OCCK_FP64 form on the tensor core from integer
- * slices instead of DFMA: the full transform O^{ij,X}_lm = sum_r C_ri
- * O^{rj,X}_lm (Sec. II, Eq. motrans, second line) and the K assembly K^ff_ri =
- * 2 sum_X sum_{j,lm} O^{rj,X}_lm Mcal^{ij}_lm(X) (Eq. kri).  Every operand row
- * (step (a): C's orbital columns per leaf, W's orbital columns per leaf and
- * component; step (e): W's AO rows, Mcal's orbital columns per leaf) is scaled
- * by a power of two into (-1, 1) and cut into `slices` integer slices of at
- * most 7 bits (the error-free splitting of Ozaki, Ogita, Oishi and Rump, Numer.
- * Algorithms 59 (2012) 95); the slice products are summed exactly (small
- * integers on FP16 MMAs, exact FP32 sums per 512 K values, exact int32 sums
- * across them) and combined in FP64.  The result differs from the DFMA form
- * by the slices' truncation: relative to the largest entries of the row and
- * column, about 2^-49 per product for 7 slices and 2^-42 for 6 (measured on K:
- * about 1e-12 and 1e-10 of max|K|).  Steps a0, (b)-(d) and the reductions are
- * unchanged (FP64).  slices = 0 (default) keeps the DFMA kernels; 6 or 7
- * enable the sliced form for calls with prec = OCCK_FP64 and no pair screening
- * or column block (those keep the DFMA kernels).  Workspace: the slice panels
- * of the larger of the two steps, about 14 x slices bytes per (stored AO row
- * or leaf orbital) x n_occ x (L+1)^2 (18 GB for 3577 AOs, 660 orbitals,
- * L = 2, 7 slices), allocated on the next call.  OCCK_ERR_ARG for other
- * values.  No paper counterpart: an implementation choice of this library. */
+/* A faster FP64-accurate form of OCCK_FP64 that keeps its arithmetic off
+ * the FP64 pipe.  The full transform O^{ij,X}_lm = sum_r C_ri O^{rj,X}_lm
+ * (Sec. II, Eq. motrans, second line) and the K assembly K^ff_ri = 2 sum_X
+ * sum_{j,lm} O^{rj,X}_lm Mcal^{ij}_lm(X) (Eq. kri) run on the tensor core from
+ * integer slices: every operand row (step (a): C's orbital columns per leaf,
+ * W's orbital columns per leaf and component; step (e): W's AO rows, Mcal's
+ * orbital columns per leaf) is scaled by a power of two into (-1, 1) and cut
+ * into `slices` integer slices of at most 7 bits (the error-free splitting of
+ * Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012) 95); the slice
+ * products are summed exactly (small integers on FP16 MMAs, exact FP32 sums per
+ * 512 K values, exact integer sums across them) and combined in FP64.  The
+ * half transform W = O^{rj,X} (Eq. motrans, first line) and the M2L + L2L
+ * passes (Eqs. fmmex, fmm2, fmm3) run in double-FP32 arithmetic on the FP32
+ * pipe (each value hi + lo, each multiply-add an error-free FMA product and
+ * TwoSum).  M2M, the reductions and the energy stay FP64.  The result differs
+ * from the DFMA form by the slices' truncation, relative to the largest
+ * entries of each row and column about 2^-49 per product for 7 slices and
+ * 2^-42 for 6 (measured on K: about 1.6e-12 and 1.3e-10 of max|K|; E within
+ * about 1e-14 Eh).  slices = 0 (default) keeps the DFMA kernels; 6 or 7
+ * enable the form for calls with prec = OCCK_FP64 and no pair screening or
+ * column block (those keep the DFMA kernels).  Workspace: the slice panels of
+ * the larger of the two sliced steps, about 14 x slices bytes per (stored AO
+ * row or leaf orbital) x n_occ x (L+1)^2 (18 GB for 3577 AOs, 660 orbitals,
+ * L = 2, 7 slices), and double-FP32 copies of C, the pair values and the
+ * operators, allocated on the next call.  OCCK_ERR_ARG for other values.  No
+ * paper counterpart: an implementation choice of this library. */
 occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices);
 
 /* D = A B^T on the tensor-core engine used by the mixed forms, for checking
