@@ -671,12 +671,14 @@ __device__ __forceinline__ void ff_fma(float& h, float& l, float2 w, float2 v) {
     h = sum;
 }
 
+// x (FP64) -> (hi, lo): hi = x rounded to FP32, lo = (x - hi) rounded to FP32
+// (x - hi is exact in FP64), in place in the same 8 bytes
 __global__ void k_ff_split(double* x, size_t n) {
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    {
         const double v = x[k];
         const float h = __double2float_rn(v);
-        const float l = __double2float_rn(v - (double)h);
-        reinterpret_cast<float2*>(x)[k] = make_float2(h, l);
+        reinterpret_cast<float2*>(x)[k] = make_float2(h, __double2float_rn(v - (double)h));
     }
 }
 
@@ -697,13 +699,14 @@ __global__ void k_ff_ops(const double* __restrict__ ops, size_t n, float2* __res
 
 constexpr int kFFNcMax = 169;
 
-// one level: block (target, 128 pairs, chunk of LMC output components)
-template <int LMC>
+// one level: block (target, 128 pairs, chunk of LMC output components).
+// MODE 0: M2M, the target gathers its children (Eq. fmm1); MODE 3: M2L over
+// the interaction list, then the parent's finished local expansion (L2L).
+template <int LMC, int MODE>
 __global__ void __launch_bounds__(128)
-k_m2l_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr, const int* __restrict__ list,
-         const int* __restrict__ opidx, const int* __restrict__ lmax_e, const int* __restrict__ parent,
-         const int* __restrict__ l2l_opidx, const float2* __restrict__ ops, const float2* __restrict__ in,
-         float2* out) {
+k_translate_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr, const int* __restrict__ list,
+               const int* __restrict__ opidx, const int* __restrict__ lmax_e, const int* __restrict__ parent,
+               const int* __restrict__ l2l_opidx, const float2* __restrict__ ops, const float2* in, float2* out) {
     __shared__ float2 sop[kFFNcMax][LMC];   // [input component][output component of the chunk]
     const int tgt = tgt0 + blockIdx.x;
     const int p = blockIdx.y * blockDim.x + threadIdx.x;
@@ -714,13 +717,18 @@ k_m2l_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ 
 #pragma unroll
     for (int q = 0; q < LMC; ++q) ah[q] = al[q] = 0.f;
     const int e0 = ptr[tgt], e1 = ptr[tgt + 1];
-    const int eend = e1 + (parent[tgt] >= first_box ? 1 : 0);   // then the parent's local expansion
+    const int eend = e1 + ((MODE == 3 && parent[tgt] >= first_box) ? 1 : 0);   // then the parent's expansion
     int llo = 0;
     while ((llo + 1) * (llo + 1) <= c0) ++llo;
+    int lhi = 0;
+    while ((lhi + 1) * (lhi + 1) <= c0 + ncl - 1) ++lhi;
     for (int e = e0; e < eend; ++e) {
-        const bool l2l = e == e1;
+        const bool l2l = MODE == 3 && e == e1;
         int src, op, Le = L;
-        if (!l2l) {
+        if (MODE == 0) {
+            src = list[e];
+            op = opidx[src];
+        } else if (!l2l) {
             src = list[e];
             op = opidx[e];
             if (lmax_e) Le = lmax_e[e];
@@ -730,7 +738,8 @@ k_m2l_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ 
         }
         const int ncr = (Le + 1) * (Le + 1);
         if (c0 >= ncr) continue;   // uniform across the block
-        const int cb0 = l2l ? llo * llo : 0, cb1 = ncr;
+        // M2M: output rank l takes input ranks up to l; L2L: from l up
+        const int cb0 = l2l ? llo * llo : 0, cb1 = MODE == 0 ? min(ncr, (lhi + 1) * (lhi + 1)) : ncr;
         const float2* Tm = ops + (size_t)op * nc * nc;
         __syncthreads();
         for (int x = threadIdx.x; x < LMC * (cb1 - cb0); x += blockDim.x) {
@@ -759,6 +768,16 @@ k_m2l_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ 
             const float h = __fadd_rn(ah[q], al[q]);       // renormalise (Fast2Sum)
             o[(size_t)q * P] = make_float2(h, __fsub_rn(al[q], __fsub_rn(h, ah[q])));
         }
+}
+
+template <int MODE, typename... Args>
+void launch_translate_ff(int lmc, dim3 g, cudaStream_t s, Args... args) {
+    switch (lmc) {
+        case 4: k_translate_ff<4, MODE><<<g, 128, 0, s>>>(args...); break;
+        case 9: k_translate_ff<9, MODE><<<g, 128, 0, s>>>(args...); break;
+        case 16: k_translate_ff<16, MODE><<<g, 128, 0, s>>>(args...); break;
+        default: k_translate_ff<25, MODE><<<g, 128, 0, s>>>(args...); break;
+    }
 }
 
 // Step (a), first half (Eq. motrans, first line), in double-FP32 arithmetic:
@@ -893,30 +912,46 @@ cudaError_t half_ff(const HalfFFArgs& h, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {
+static int ff_lmc(int nc) { return nc <= 4 ? 4 : nc <= 9 ? 9 : nc <= 16 ? 16 : 25; }
+
+cudaError_t m2m_ff(const FFArgs& f, cudaStream_t s) {
+    // the leaves' multipoles (FP64 from step (a)) to (hi, lo); M2M writes
+    // the parents' in (hi, lo)
+    const size_t nleafv = (size_t)(f.nstore - f.leaf_store0) * f.nc * f.P;
+    const int blocks = 4 * std::max(f.sm_count, 1);
+    k_ff_split<<<blocks, 256, 0, s>>>(f.Ob + (size_t)f.leaf_store0 * f.nc * f.P, nleafv);
     const size_t nops = (size_t)f.nops * f.nc * f.nc;
+    k_ff_ops<<<std::max(1, (int)std::min<size_t>((nops + 255) / 256, 4096)), 256, 0, s>>>(f.ops, nops, f.ops_ff);
+    const int lmc = ff_lmc(f.nc), nchunk = (f.nc + lmc - 1) / lmc;
+    auto* ob = reinterpret_cast<float2*>(f.Ob);
+    for (int lev = f.D; lev >= 3; --lev) {
+        const int t0 = f.level_off[lev - 1], nt = f.level_off[lev] - t0;
+        if (nt <= 0) continue;
+        dim3 g(nt, (unsigned)((f.P + 127) / 128), nchunk);
+        launch_translate_ff<0>(lmc, g, s, f.P, f.nc, f.L, f.first_box, t0, f.child_ptr, f.child_list, f.m2m_op,
+                               (const int*)nullptr, f.parent, (const int*)nullptr, (const float2*)f.ops_ff,
+                               (const float2*)ob, ob);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {
     const size_t n = (size_t)f.nstore * f.nc * f.P;
     const int blocks = 4 * std::max(f.sm_count, 1);
-    k_ff_ops<<<std::max(1, (int)std::min<size_t>((nops + 255) / 256, 4096)), 256, 0, s>>>(f.ops, nops, f.ops_ff);
-    k_ff_split<<<blocks, 256, 0, s>>>(f.Ob, n);
-    const int lmc = f.nc <= 4 ? 4 : f.nc <= 9 ? 9 : f.nc <= 16 ? 16 : 25;
-    const int nchunk = (f.nc + lmc - 1) / lmc;
+    if (!f.m2m_done) {   // multipoles still FP64 (the FP64 M2M ran)
+        const size_t nops = (size_t)f.nops * f.nc * f.nc;
+        k_ff_ops<<<std::max(1, (int)std::min<size_t>((nops + 255) / 256, 4096)), 256, 0, s>>>(f.ops, nops,
+                                                                                              f.ops_ff);
+        k_ff_split<<<blocks, 256, 0, s>>>(f.Ob, n);
+    }
+    const int lmc = ff_lmc(f.nc), nchunk = (f.nc + lmc - 1) / lmc;
     for (int lev = 2; lev <= f.D; ++lev) {
         const int t0 = f.level_off[lev], nt = f.level_off[lev + 1] - t0;
         if (nt <= 0) continue;
         dim3 g(nt, (unsigned)((f.P + 127) / 128), nchunk);
-        auto* in = reinterpret_cast<const float2*>(f.Ob);
-        auto* out = reinterpret_cast<float2*>(f.Mb);
-        switch (lmc) {
-            case 4: k_m2l_ff<4><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
-                                                  f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
-            case 9: k_m2l_ff<9><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
-                                                  f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
-            case 16: k_m2l_ff<16><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
-                                                    f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
-            default: k_m2l_ff<25><<<g, 128, 0, s>>>(f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
-                                                    f.lmax_e, f.parent, f.l2l_op, f.ops_ff, in, out); break;
-        }
+        launch_translate_ff<3>(lmc, g, s, f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op, f.lmax_e,
+                               f.parent, f.l2l_op, (const float2*)f.ops_ff, reinterpret_cast<const float2*>(f.Ob),
+                               reinterpret_cast<float2*>(f.Mb));
     }
     k_ff_join<<<blocks, 256, 0, s>>>(f.Ob, n);
     k_ff_join<<<blocks, 256, 0, s>>>(f.Mb, n);

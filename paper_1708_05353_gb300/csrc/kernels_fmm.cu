@@ -829,7 +829,29 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         }
         if (e2 != cudaSuccess) return e2;
     }
-    for (int lev = D; lev >= 3 && !slots; --lev) {
+    // the sliced FP64 form: M2M in double-FP32 arithmetic (not with the
+    // learned selector, whose features read the FP64 multipoles of every box)
+    FFArgs ffa{};
+    bool m2m_ff_done = false;
+    if constexpr (sizeof(T) == 8) {
+        if (a.slices && a.slices->ff && !a.screen) {
+            ffa.P = (int)P; ffa.nc = nc; ffa.L = a.L; ffa.D = D; ffa.first_box = a.first_box;
+            ffa.nstore = a.nbox - a.first_box; ffa.leaf_store0 = leaf_store0; ffa.nops = a.slices->nops;
+            ffa.sm_count = a.sm_count; ffa.level_off = a.level_off;
+            ffa.m2l_ptr = a.m2l_ptr; ffa.m2l_src = a.m2l_src; ffa.m2l_op = a.m2l_op;
+            ffa.parent = a.parent; ffa.l2l_op = a.l2l_op;
+            ffa.child_ptr = a.child_ptr; ffa.child_list = a.child_list; ffa.m2m_op = a.m2m_op;
+            ffa.ops = (const double*)tops; ffa.ops_ff = a.slices->ops_ff;
+            ffa.Ob = (double*)Ob; ffa.Mb = (double*)Mb;
+            if (!a.learned) {
+                cudaError_t e2 = m2m_ff(ffa, s);
+                if (e2 != cudaSuccess) return e2;
+                m2m_ff_done = true;
+                ffa.m2m_done = 1;
+            }
+        }
+    }
+    for (int lev = D; lev >= 3 && !slots && !m2m_ff_done; --lev) {
         int t0 = a.level_off[lev - 1], nt = a.level_off[lev] - t0;
         if (trc && (a.tr_mask & 1)) {
             cudaError_t e2 = tr_translate(a.prec, th, 0, t0, nt, a.child_ptr, a.child_list, a.m2m_op,
@@ -873,15 +895,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         if constexpr (sizeof(T) == 8) {
             if (a.slices && a.slices->ff && !a.screen) {
                 // the sliced FP64 form: the same pass in double-FP32 arithmetic
-                FFArgs f{};
-                f.P = (int)P; f.nc = nc; f.L = a.L; f.D = D; f.first_box = a.first_box;
-                f.nstore = a.nbox - a.first_box; f.nops = a.slices->nops; f.sm_count = a.sm_count;
-                f.level_off = a.level_off;
-                f.m2l_ptr = a.m2l_ptr; f.m2l_src = a.m2l_src; f.m2l_op = a.m2l_op; f.lmax_e = lmax_e;
-                f.parent = a.parent; f.l2l_op = a.l2l_op;
-                f.ops = (const double*)tops; f.ops_ff = a.slices->ops_ff;
-                f.Ob = (double*)Ob; f.Mb = (double*)Mb;
-                cudaError_t e2 = m2l_ff(f, s);
+                ffa.lmax_e = lmax_e;
+                cudaError_t e2 = m2l_ff(ffa, s);
                 if (e2 != cudaSuccess) return e2;
                 done = true;
             }

@@ -365,13 +365,16 @@ cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cuda
 // M2L with L2L, fused per level, in double-FP32 arithmetic on the FP32 pipe
 // (the sliced FP64 form); O and Mcal are FP64 before and after the call
 struct FFArgs {
-    int P, nc, L, D, first_box, nstore, nops, sm_count;
+    int P, nc, L, D, first_box, nstore, leaf_store0, nops, sm_count;
+    int m2m_done;                           // m2m_ff ran: the multipoles are (hi, lo) already
     const int* level_off;                   // host
     const int* m2l_ptr; const int* m2l_src; const int* m2l_op; const int* lmax_e;
     const int* parent; const int* l2l_op;
+    const int* child_ptr; const int* child_list; const int* m2m_op;
     const double* ops; float2* ops_ff;      // FP64 operators; their (hi, lo) copy (written)
     double* Ob; double* Mb;
 };
+cudaError_t m2m_ff(const FFArgs& f, cudaStream_t s);   // (b) in double-FP32; splits the leaves first
 cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s);
 // step (a), first half, in double-FP32 arithmetic (the sliced FP64 form)
 struct HalfFFArgs {
