@@ -61,6 +61,9 @@ def parse(argv=None):
     p.add_argument("--ncarbon", type=int, default=150)
     p.add_argument("--lmax", type=int, default=2)
     p.add_argument("--prec", default="fp64", help="precision of the headline line")
+    p.add_argument("--fp64-slices", type=int, default=0, choices=[0, 6, 7],
+                   help="with --prec fp64: steps (a), (e) from this many integer slices on the tensor core and "
+                        "the half transform and tree passes in double-FP32 (0: the DFMA form)")
     p.add_argument("--variants", default=",".join(["fp64s"] + MIXED),
                    help="other precisions timed on the same workload (comma list, or 'none')")
     p.add_argument("--learned-rank", type=int, default=10,
@@ -684,6 +687,8 @@ def main(argv=None):
 
     if args.workload == "chain-loc":
         ctx.set_pair_screen(args.screen_tau)     # every build below is screened
+    if args.fp64_slices and args.prec == "fp64":
+        ctx.set_fp64_slices(args.fp64_slices)    # the main line and e2e; variants reset it
 
     def step():
         if world > 1:
@@ -768,6 +773,9 @@ def main(argv=None):
                     "c_m2l": "k_translate(M2L+L2L)" if fused_cd else "k_translate(M2L)",
                     "d_l2l": "k_translate(L2L)", "e_l2p": "k_l2p_r32" if args.prec == "fp64" else "k_l2p",
                     "reduce": "k_reduce_K"}
+    if args.fp64_slices and args.prec == "fp64":
+        kernel_names.update({"a_half": "k_half_ff", "a_full": "k_s_gemm_a", "b_m2m": "k_translate_ff(M2M)",
+                             "c_m2l": "k_translate_ff(M2L+L2L)", "e_l2p": "k_s_gemm_e"})
     achieved = fl[dom] / (stage_ms[dom] * 1e-3)
     roof = {"bound": "alu", "kernel": kernel_names[dom], "stage": dom,
             "achieved": achieved / 1e12, "peak": probe / 1e12, "unit": "TFLOP/s",
@@ -798,7 +806,9 @@ def main(argv=None):
                                               if args.workload == "chain-loc" else ""),
                    "nao": system.basis.nao, "nocc": system.nocc,
                    "lmax": L, "depth": D, "nbox": info["nbox"], "nm2l": info["nm2l"],
-                   "precision": args.prec,
+                   "precision": args.prec + (f" (steps a, e from {args.fp64_slices} integer slices on the tensor "
+                                             "core; half transform and tree passes in double-FP32)"
+                                             if args.fp64_slices and args.prec == "fp64" else ""),
                    "parallelism": (f"occupied column blocks x{world} (gathered over NCCL)" if world > 1
                                    else "one GPU"),
                    "l2": "flushed (256 MB write) before every timed step",
@@ -828,8 +838,9 @@ def main(argv=None):
     if rank == 0 and world == 1:
         # ---- the mixed forms on the same workload: time, speed-up over the
         # FP64 GPU form, error against it and against the oracle's columns
+        ctx.set_fp64_slices(0)
         if args.variants != "none":
-            if args.prec == "fp64":
+            if args.prec == "fp64" and not args.fp64_slices:
                 ms64, E64, K64 = ms_max, E_main, K_main
             else:
                 ms64, _ = tm.run(lambda: occk.farfield_K(ctx, tree, Cf, prec="fp64", K=K, Ex=Ex), 3, warm=1)
