@@ -461,10 +461,11 @@ occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit);
  * Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012) 95); the slice
  * products are summed exactly (small integers on FP16 MMAs, exact FP32 sums per
  * 512 K values, exact integer sums across them) and combined in FP64.  The
- * half transform W = O^{rj,X} (Eq. motrans, first line) and the M2L + L2L
- * passes (Eqs. fmmex, fmm2, fmm3) run in double-FP32 arithmetic on the FP32
- * pipe (each value hi + lo, each multiply-add an error-free FMA product and
- * TwoSum).  M2M, the reductions and the energy stay FP64.  The result differs
+ * half transform W = O^{rj,X} (Eq. motrans, first line) and the M2M, M2L and
+ * L2L passes (Eqs. fmm1, fmmex, fmm2, fmm3) run in double-FP32 arithmetic on
+ * the FP32 pipe (each value hi + lo, each multiply-add an error-free FMA
+ * product and TwoSum; M2M stays FP64 with the learned selector, whose features
+ * read the FP64 multipoles).  The reductions and the energy stay FP64.  The result differs
  * from the DFMA form by the slices' truncation, relative to the largest
  * entries of each row and column about 2^-49 per product for 7 slices and
  * 2^-42 for 6 (measured on K: about 1.6e-12 and 1.3e-10 of max|K|; E within
