@@ -890,7 +890,9 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         if ((e = cudaMemcpy(ctx->splan.p, hp.data(), o_eC, cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(ctx, e, "slice plan upload");
         char* x = (char*)ctx->splan.p;
-        sa.full = 1;
+        // step (a) from slices while a leaf's K range fits the exact int32
+        // group sums (about 4000 AO rows); the DFMA kernel otherwise
+        sa.full = max_kca <= occk::slice_max_stages() ? 1 : 0;
         sa.max_kca = max_kca;
         sa.ntp = (int)tpair.size();
         sa.leaf_aos = t->dev.leaf_aos;

@@ -119,3 +119,56 @@ def test_slices_argument(ctx):
     for bad in (-1, 1, 5, 8):
         with pytest.raises(occk.OcckError):
             ctx.set_fp64_slices(bad)
+
+
+def test_sliced_per_edge_ranks(ctx):
+    """Per-edge M2L ranks (lmax_policy 1): the double-FP32 M2L reads each
+    edge's rank; K follows the oracle with the same ranks."""
+    from oracle import fmm
+    from oracle import tree as otree
+    s = inputs.small_sp(natom=6, nocc=4, spacing=3.0, depth=3)
+    L = 4
+    tr = otree.build_tree(s.basis, 3, 8.0)
+    ranks = np.random.default_rng(3).integers(0, L + 1, size=len(tr["m2l_tgt"]))
+    from paper_1708_05353_gb300 import occk
+    tree = occk.Tree(ctx, s.basis, depth=3)
+    tree.pair_multipoles(L)
+    tree.set_edge_lmax(ranks)
+    C = torch.tensor(s.C, dtype=torch.float64, device="cuda:0")
+    ctx.set_fp64_slices(7)
+    try:
+        K, E = occk.farfield_K(ctx, tree, C, prec="fp64", lmax_policy=1, want_energy_host=True)
+    finally:
+        ctx.set_fp64_slices(0)
+    Kr, Er = fmm.farfield(s, L=L, tree=tr, lmax_edges=ranks)
+    err = rel_err(K.cpu().numpy(), Kr)
+    print(f"per-edge ranks, 7 slices: {err:.2e}, |dE| {abs(E - Er):.2e}")
+    assert err < 1e-11 and abs(E - Er) <= 1e-11 * abs(Er)
+
+
+def test_sliced_learned_selector(ctx):
+    """The learned selector (lmax_policy 2) reads the FP64 multipoles of every
+    box, so the sliced form keeps the FP64 M2M there; with the same network the
+    chosen ranks and K follow the DFMA form."""
+    from oracle import mlp
+    from paper_1708_05353_gb300 import occk
+    rng = np.random.default_rng(5)
+    theta = mlp.init(occk.MLP_NIN, occk.MLP_HIDDEN, occk.MLP_NOUT, 5)
+    norm = np.concatenate([rng.normal(size=occk.MLP_NIN), rng.uniform(0.5, 2.0, size=occk.MLP_NIN),
+                           np.zeros(occk.MLP_NOUT), np.ones(occk.MLP_NOUT)])
+    occk.mlp_set(ctx, theta, norm)
+    s = inputs.alkane(30, lmax=6)
+    tree, C = _build(ctx, s, 6)
+    out = {}
+    for sl in (0, 7):
+        ctx.set_fp64_slices(sl)
+        try:
+            K, E = occk.farfield_K(ctx, tree, C, prec="fp64", lmax_policy=2, want_energy_host=True)
+            out[sl] = (K.clone(), E, occk.edge_ranks(ctx, tree))
+        finally:
+            ctx.set_fp64_slices(0)
+    (K0, E0, r0), (K7, E7, r7) = out[0], out[7]
+    d = float((K7 - K0).abs().max() / K0.abs().max())
+    print(f"learned ranks, 7 slices vs DFMA: {d:.2e}, |dE| {abs(E7 - E0):.2e}")
+    assert np.array_equal(r0, r7)
+    assert d < 1e-11 and abs(E7 - E0) <= 1e-11 * abs(E0)
