@@ -472,12 +472,20 @@ occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit);
  * about 1e-14 Eh).  slices = 0 (default) keeps the DFMA kernels; 6 or 7
  * enable the form for calls with prec = OCCK_FP64 and no pair screening or
  * column block (those keep the DFMA kernels).  Workspace: the slice panels of
- * the larger of the two sliced steps, about 14 x slices bytes per (stored AO
- * row or leaf orbital) x n_occ x (L+1)^2 (18 GB for 3577 AOs, 660 orbitals,
- * L = 2, 7 slices), and double-FP32 copies of C, the pair values and the
- * operators, allocated on the next call.  OCCK_ERR_ARG for other values.  No
+ * a batch of leaves (about 14 x slices bytes per (stored AO row or leaf
+ * orbital) x n_occ x (L+1)^2 in all, 18 GB for 3577 AOs, 660 orbitals, L = 2,
+ * 7 slices; batches keep it within occk_set_slice_workspace's budget), and
+ * double-FP32 copies of C, the pair values and the operators, allocated on
+ * the next call.  OCCK_ERR_ARG for other values.  No
  * paper counterpart: an implementation choice of this library. */
 occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices);
+
+/* Largest workspace of slice panels of the form above, in bytes (0, the
+ * default: 32 GB).  The leaves are processed in batches whose panels fit
+ * (a leaf larger than the budget is a batch of its own); the result does not
+ * depend on the batching (each output tile is computed the same way).
+ * OCCK_ERR_ARG for bytes < 0.  No paper counterpart. */
+occk_status occk_set_slice_workspace(occk_ctx* ctx, long long bytes);
 
 /* D = A B^T on the tensor-core engine used by the mixed forms, for checking
  * it: A [M x K], B [N x K], D [M x N], all FP32 row-major device buffers; prec

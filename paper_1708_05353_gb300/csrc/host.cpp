@@ -821,11 +821,13 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     // pair, all columns (the DFMA kernels serve screening and column blocks)
     const bool sliced = prec == OCCK_FP64 && ctx->f64_slices > 0 && ctx->col_i1 == 0 && ctx->screen_tau <= 0;
     occk::SliceArgs sa{};
+    // host plan of the sliced steps, alive until the launches below
+    std::vector<long long> offA(nleaf + 1), item0(nleaf + 1), offAa(nleaf + 1), offBa(nleaf + 1);
+    std::vector<int> batch_e, batch_a;
     if (sliced) {
         const int SK = occk::slice_stage_k(), SN = occk::slice_tile_n();
         const int jc = (nocc + SK - 1) / SK, KC = nc * jc, nct = (nocc + SN - 1) / SN;
         std::vector<int> rtA(nleaf);
-        std::vector<long long> offA(nleaf), item0(nleaf + 1);
         long long cA = 0, items1 = 0;
         int max_rt = 0;
         for (int B = 0; B < nleaf; ++B) {
@@ -835,6 +837,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
             items1 += (long long)rtA[B] * nct;
             max_rt = std::max(max_rt, rtA[B]);
         }
+        offA[nleaf] = cA;
         // K splits: as many as the exact int32 group sums need, more while
         // the tiles cover the GPU less than twice (each split writes a KB copy)
         const int need = (KC + occk::slice_max_stages() - 1) / occk::slice_max_stages();
@@ -850,7 +853,6 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         // a 128-orbital row tile and a 32-orbital column tile
         const int nti = (nocc + 127) / 128;
         std::vector<int> tpair, kca(nleaf);
-        std::vector<long long> offAa(nleaf), offBa(nleaf);
         for (int ti = 0; ti < nti; ++ti)
             for (int tj = ti * 128 / SN; tj < nct; ++tj) tpair.push_back(ti | (tj << 16));
         long long cAa = 0, cBa = 0;
@@ -863,6 +865,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
             cBa += (long long)nc * nct * kca[B];
             max_kca = std::max(max_kca, kca[B]);
         }
+        offAa[nleaf] = cAa;
+        offBa[nleaf] = cBa;
         const size_t o_kca = o_fcol + al16(4 * (size_t)nleaf * nocc), o_offAa = o_kca + al16(4 * (size_t)nleaf);
         const size_t o_offBa = o_offAa + al16(8 * (size_t)nleaf), o_tp = o_offBa + al16(8 * (size_t)nleaf);
         const size_t o_eC = o_tp + al16(4 * tpair.size()), o_eW = o_eC + al16(4 * (size_t)nleaf * nocc);
@@ -871,12 +875,33 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         const size_t o_vff = o_ff + al16(8 * nops * nc * nc);
         const size_t o_cff = o_vff + al16(8 * (size_t)t->nvals * nc);
         const size_t plan_bytes = o_cff + al16(8 * (size_t)t->nao * nocc);
-        const size_t bytes_a = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cA;
-        const size_t bytes_b = occk::slice_panel_bytes(ctx->f64_slices, false) * (size_t)nleaf * nct * KC;
-        const size_t bytes_aa = occk::slice_panel_bytes(ctx->f64_slices, true) * (size_t)cAa;
-        const size_t bytes_ba = occk::slice_panel_bytes(ctx->f64_slices, false) * (size_t)cBa;
+        // leaf batches whose panels fit a workspace of at most 32 GB (one
+        // batch for the protein-sized cluster at L = 2; several at high rank)
+        const size_t pa = occk::slice_panel_bytes(ctx->f64_slices, true);
+        const size_t pbb = occk::slice_panel_bytes(ctx->f64_slices, false);
+        const size_t budget = ctx->slice_budget > 0 ? ctx->slice_budget : size_t(32) << 30;
+        auto e_bytes = [&](int B0, int B1) {
+            return pa * (size_t)(offA[B1] - offA[B0]) + pbb * (size_t)(B1 - B0) * nct * KC;
+        };
+        auto a_bytes = [&](int B0, int B1) {
+            return pa * (size_t)(offAa[B1] - offAa[B0]) + pbb * (size_t)(offBa[B1] - offBa[B0]);
+        };
+        size_t need_bytes = 0;
+        auto cut = [&](std::vector<int>& bt, auto bytes) {
+            bt.assign(1, 0);
+            int b0 = 0;
+            for (int B = 1; B <= nleaf; ++B)
+                if (bytes(b0, B) > budget && B - 1 > b0) {
+                    bt.push_back(B - 1);
+                    b0 = B - 1;
+                }
+            bt.push_back(nleaf);
+            for (size_t k = 0; k + 1 < bt.size(); ++k) need_bytes = std::max(need_bytes, bytes(bt[k], bt[k + 1]));
+        };
+        cut(batch_e, e_bytes);
+        cut(batch_a, a_bytes);
         if ((e = ensure(ctx->splan, plan_bytes)) != cudaSuccess ||
-            (e = ensure(ctx->spanels, std::max(bytes_a + bytes_b, bytes_aa + bytes_ba))) != cudaSuccess)
+            (e = ensure(ctx->spanels, need_bytes)) != cudaSuccess)
             return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "slice panels of steps (a) and (e)")
                                                   : cuda_fail(ctx, e, "slice panels of steps (a) and (e)");
         std::vector<char> hp(plan_bytes, 0);
@@ -909,7 +934,14 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         sa.vals_ff = (float2*)(x + o_vff);
         sa.C_ff = (float2*)(x + o_cff);
         sa.panAa = (uint8_t*)ctx->spanels.p;
-        sa.panBa = (uint8_t*)ctx->spanels.p + bytes_aa;
+        sa.nbatch_e = (int)batch_e.size() - 1;
+        sa.nbatch_a = (int)batch_a.size() - 1;
+        sa.batch_e = batch_e.data();
+        sa.batch_a = batch_a.data();
+        sa.offA_h = offA.data();
+        sa.item0_h = item0.data();
+        sa.offAa_h = offAa.data();
+        sa.offBa_h = offBa.data();
         sa.S = ctx->f64_slices;
         sa.nocc = nocc; sa.nc = nc; sa.nrow = nrow; sa.nleaf = nleaf;
         sa.leaf_store0 = t->level_off[D] - first;
@@ -923,7 +955,6 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         sa.erow = (int*)(x + o_erow);
         sa.fcol = (int*)(x + o_fcol);
         sa.panA = (uint8_t*)ctx->spanels.p;
-        sa.panB = (uint8_t*)ctx->spanels.p + bytes_a;
         l2p_nsplit = nsplit;
     }
     size_t bytes_kb = 8 * (size_t)nrow * nocc * l2p_nsplit;
@@ -1521,6 +1552,13 @@ extern "C" occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit) {
     if (!ctx) return OCCK_ERR_ARG;
     if (nsplit < 0 || nsplit > 64) return fail(ctx, OCCK_ERR_ARG, "nsplit must be 0..64");
     ctx->l2p_split = nsplit;
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_slice_workspace(occk_ctx* ctx, long long bytes) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (bytes < 0) return fail(ctx, OCCK_ERR_ARG, "bytes must be >= 0");
+    ctx->slice_budget = (size_t)bytes;
     return OCCK_OK;
 }
 

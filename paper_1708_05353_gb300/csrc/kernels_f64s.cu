@@ -215,8 +215,8 @@ template <int S>
 __global__ void __launch_bounds__(128)
 k_s_panel_A(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const float* __restrict__ lscale,
             const int* __restrict__ erow, int nocc, int nrow, int jc, int KC, const int* __restrict__ rtA,
-            const long long* __restrict__ offA, uint8_t* __restrict__ pan) {
-    const int kc = blockIdx.x, rt = blockIdx.y, B = blockIdx.z;
+            const long long* __restrict__ offA, int B0, long long pan0, uint8_t* __restrict__ pan) {
+    const int kc = blockIdx.x, rt = blockIdx.y, B = B0 + blockIdx.z;
     if (rt >= rtA[B]) return;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
     const int r = rt * 128 + threadIdx.x;
@@ -224,7 +224,7 @@ k_s_panel_A(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, c
     const bool live = r < nr;
     const double* w = W + ((size_t)lm * nrow + rb0 + (live ? r : 0)) * nocc;
     const int t = s_klm(lscale, lm) - (live ? erow[rb0 + r] : 0) + 55;
-    uint8_t* panel = pan + (size_t)(offA[B] + (long long)rt * KC + kc) * SL<S>::a_bytes;
+    uint8_t* panel = pan + (size_t)(offA[B] - pan0 + (long long)rt * KC + kc) * SL<S>::a_bytes;
 #pragma unroll
     for (int k8 = 0; k8 < kSK; k8 += 8) {
         long long v[8];
@@ -241,8 +241,8 @@ k_s_panel_A(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, c
 template <int S>
 __global__ void __launch_bounds__(128)
 k_s_panel_B(const double* __restrict__ Mbox, const float* __restrict__ lscale, const int* __restrict__ fcol,
-            int nocc, int nc, int leaf_store0, int jc, int KC, int nct, uint8_t* __restrict__ pan) {
-    const int kc = blockIdx.x * 4 + (threadIdx.x >> 5), ct = blockIdx.y, B = blockIdx.z;
+            int nocc, int nc, int leaf_store0, int jc, int KC, int nct, int B0, uint8_t* __restrict__ pan) {
+    const int kc = blockIdx.x * 4 + (threadIdx.x >> 5), ct = blockIdx.y, B = B0 + blockIdx.z;
     if (kc >= KC) return;
     const int il = threadIdx.x & 31, i = ct * kSN + il;
     const int lm = kc / jc, j0 = (kc % jc) * kSK;
@@ -253,7 +253,7 @@ k_s_panel_B(const double* __restrict__ Mbox, const float* __restrict__ lscale, c
     const double* M = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
     const bool live = i < nocc;
     const int t = a - s_klm(lscale, lm) - (live ? fcol[(size_t)B * nocc + i] : 0) + 55;
-    uint8_t* panel = pan + (size_t)(((long long)B * nct + ct) * KC + kc) * SL<S>::b_bytes;
+    uint8_t* panel = pan + (size_t)(((long long)(B - B0) * nct + ct) * KC + kc) * SL<S>::b_bytes;
 #pragma unroll
     for (int k8 = 0; k8 < kSK; k8 += 8) {
         long long v[8];
@@ -295,14 +295,14 @@ template <int S>
 __global__ void __launch_bounds__(128)
 k_s_a2_panel_A(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const double* __restrict__ Ct,
                const int* __restrict__ eC, int nocc, int nti, const int* __restrict__ kca,
-               const long long* __restrict__ offAa, uint8_t* __restrict__ pan) {
-    const int kc = blockIdx.x, ti = blockIdx.y, B = blockIdx.z;
+               const long long* __restrict__ offAa, int B0, long long pan0, uint8_t* __restrict__ pan) {
+    const int kc = blockIdx.x, ti = blockIdx.y, B = B0 + blockIdx.z;
     if (kc >= kca[B]) return;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
     const int i = ti * 128 + threadIdx.x;
     const bool live = i < nocc;
     const int t = 55 - (live ? eC[(size_t)B * nocc + i] : 0);
-    uint8_t* panel = pan + (size_t)(offAa[B] + (long long)ti * kca[B] + kc) * SL<S>::a_bytes;
+    uint8_t* panel = pan + (size_t)(offAa[B] - pan0 + (long long)ti * kca[B] + kc) * SL<S>::a_bytes;
 #pragma unroll
     for (int k8 = 0; k8 < kSK; k8 += 8) {
         long long v[8];
@@ -321,8 +321,8 @@ template <int S>
 __global__ void __launch_bounds__(128)
 k_s_a2_panel_B(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const int* __restrict__ eW,
                int nocc, int nrow, int nc, int nct, const int* __restrict__ kca, const long long* __restrict__ offBa,
-               uint8_t* __restrict__ pan) {
-    const int B = blockIdx.z / nc, lm = blockIdx.z % nc, tj = blockIdx.y;
+               int B0, long long pan0, uint8_t* __restrict__ pan) {
+    const int B = B0 + blockIdx.z / nc, lm = blockIdx.z % nc, tj = blockIdx.y;
     const int kc = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (kc >= kca[B]) return;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
@@ -330,7 +330,7 @@ k_s_a2_panel_B(const int* __restrict__ leaf_rowoff, const double* __restrict__ W
     const bool live = j < nocc;
     const int t = 55 - (live ? eW[((size_t)B * nc + lm) * nocc + j] : 0);
     const double* w = W + ((size_t)lm * nrow + rb0) * nocc + j;
-    uint8_t* panel = pan + (size_t)(offBa[B] + ((long long)lm * nct + tj) * kca[B] + kc) * SL<S>::b_bytes;
+    uint8_t* panel = pan + (size_t)(offBa[B] - pan0 + ((long long)lm * nct + tj) * kca[B] + kc) * SL<S>::b_bytes;
 #pragma unroll
     for (int k8 = 0; k8 < kSK; k8 += 8) {
         long long v[8];
@@ -357,7 +357,8 @@ struct SGemmE {
     const uint8_t* panA; const uint8_t* panB;
     double* KB;
     int nleaf, nocc, nrow, KC, nct, nsplit;
-    long long nitems;
+    int B0;                                  // first leaf of the batch (panels hold leaves B0 ..)
+    long long it0, nitems, panA0;            // items it0 .. it0 + nitems - 1; offA of leaf B0
     int* err;
 };
 
@@ -369,7 +370,8 @@ struct SGemmA {
     const uint8_t* panA; const uint8_t* panB;
     double* Obox;
     int nleaf, nocc, nc, nct, ntp, leaf_store0;
-    long long nitems;
+    int B0;                                  // first leaf of the batch
+    long long nitems, panA0, panB0;          // offAa, offBa of leaf B0
     int* err;
 };
 
@@ -563,7 +565,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
 k_s_gemm_e(SGemmE g) {
     using C = SL<S>;
     auto decode = [&](long long it, int& B, int& rt, int& ct, int& ks, int& kc0, int& kc1) {
-        int lo = 0, hi = g.nleaf - 1;                 // last leaf with item0 <= it
+        it += g.it0;
+        int lo = g.B0, hi = g.nleaf - 1;              // last leaf with item0 <= it
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (g.item0[mid] <= it) lo = mid;
@@ -581,8 +584,8 @@ k_s_gemm_e(SGemmE g) {
     auto src = [&](long long it, const uint8_t*& A, const uint8_t*& Bp, int& nk) {
         int B, rt, ct, ks, kc0, kc1;
         decode(it, B, rt, ct, ks, kc0, kc1);
-        A = g.panA + (size_t)(g.offA[B] + (long long)rt * g.KC + kc0) * C::a_bytes;
-        Bp = g.panB + (size_t)(((long long)B * g.nct + ct) * g.KC + kc0) * C::b_bytes;
+        A = g.panA + (size_t)(g.offA[B] - g.panA0 + (long long)rt * g.KC + kc0) * C::a_bytes;
+        Bp = g.panB + (size_t)(((long long)(B - g.B0) * g.nct + ct) * g.KC + kc0) * C::b_bytes;
         nk = kc1 - kc0;
     };
     auto out = [&](long long it, int row, int part, const int (&acc)[S][kSCols]) {
@@ -615,7 +618,7 @@ k_s_gemm_a(SGemmA g) {
         const int tt = (int)(it % g.ntp);
         const long long x = it / g.ntp;
         lm = (int)(x % g.nc);
-        B = (int)(x / g.nc);
+        B = g.B0 + (int)(x / g.nc);
         ti = g.tpair[tt] & 0xFFFF;
         tj = g.tpair[tt] >> 16;
     };
@@ -623,8 +626,8 @@ k_s_gemm_a(SGemmA g) {
         int B, lm, ti, tj;
         decode(it, B, lm, ti, tj);
         const int kca = g.kca[B];
-        A = g.panA + (size_t)(g.offAa[B] + (long long)ti * kca) * C::a_bytes;
-        Bp = g.panB + (size_t)(g.offBa[B] + ((long long)lm * g.nct + tj) * kca) * C::b_bytes;
+        A = g.panA + (size_t)(g.offAa[B] - g.panA0 + (long long)ti * kca) * C::a_bytes;
+        Bp = g.panB + (size_t)(g.offBa[B] - g.panB0 + ((long long)lm * g.nct + tj) * kca) * C::b_bytes;
         nk = kca;
     };
     const size_t P = (size_t)g.nocc * (g.nocc + 1) / 2;
@@ -845,17 +848,25 @@ cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
     const long long ncol = (long long)a.nleaf * a.nocc;
     k_s_colexp<<<(unsigned)((ncol + 7) / 8), 256, 0, s>>>(a.Mbox, a.lscale, a.nleaf, a.nocc, a.nc, a.leaf_store0,
                                                           a.fcol);
-    k_s_panel_A<S><<<dim3(KC, a.max_rt, a.nleaf), 128, 0, s>>>(a.leaf_rowoff, a.W, a.lscale, a.erow, a.nocc, a.nrow,
-                                                               jc, KC, a.rtA, a.offA, a.panA);
-    k_s_panel_B<S><<<dim3((KC + 3) / 4, nct, a.nleaf), 128, 0, s>>>(a.Mbox, a.lscale, a.fcol, a.nocc, a.nc,
-                                                                    a.leaf_store0, jc, KC, nct, a.panB);
-    SGemmE g{};
-    g.leaf_rowoff = a.leaf_rowoff; g.rtA = a.rtA; g.offA = a.offA; g.item0 = a.item0;
-    g.erow = a.erow; g.fcol = a.fcol; g.panA = a.panA; g.panB = a.panB; g.KB = a.KB;
-    g.nleaf = a.nleaf; g.nocc = a.nocc; g.nrow = a.nrow; g.KC = KC; g.nct = nct; g.nsplit = a.nsplit;
-    g.nitems = a.nitems; g.err = a.err;
-    const int grid = (int)std::min<long long>(a.nitems, a.sm_count);
-    if (grid > 0) k_s_gemm_e<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    // leaf batches whose panels fit the workspace: build, then multiply
+    for (int bt = 0; bt < a.nbatch_e; ++bt) {
+        const int B0 = a.batch_e[bt], B1 = a.batch_e[bt + 1];
+        if (B1 <= B0) continue;
+        const long long pA0 = a.offA_h[B0];
+        uint8_t* panB = a.panA + (size_t)(a.offA_h[B1] - pA0) * SL<S>::a_bytes;
+        k_s_panel_A<S><<<dim3(KC, a.max_rt, B1 - B0), 128, 0, s>>>(a.leaf_rowoff, a.W, a.lscale, a.erow, a.nocc,
+                                                                   a.nrow, jc, KC, a.rtA, a.offA, B0, pA0, a.panA);
+        k_s_panel_B<S><<<dim3((KC + 3) / 4, nct, B1 - B0), 128, 0, s>>>(a.Mbox, a.lscale, a.fcol, a.nocc, a.nc,
+                                                                        a.leaf_store0, jc, KC, nct, B0, panB);
+        SGemmE g{};
+        g.leaf_rowoff = a.leaf_rowoff; g.rtA = a.rtA; g.offA = a.offA; g.item0 = a.item0;
+        g.erow = a.erow; g.fcol = a.fcol; g.panA = a.panA; g.panB = panB; g.KB = a.KB;
+        g.nleaf = B1; g.nocc = a.nocc; g.nrow = a.nrow; g.KC = KC; g.nct = nct; g.nsplit = a.nsplit;
+        g.B0 = B0; g.it0 = a.item0_h[B0]; g.nitems = a.item0_h[B1] - a.item0_h[B0]; g.panA0 = pA0;
+        g.err = a.err;
+        const int grid = (int)std::min<long long>(g.nitems, a.sm_count);
+        if (grid > 0) k_s_gemm_e<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    }
     return cudaGetLastError();
 }
 
@@ -867,17 +878,24 @@ cudaError_t full_slices_typed(const SliceArgs& a, const double* Ct, double* Obox
     k_s_a2_expC<<<dim3(a.nleaf, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.nocc, a.eC);
     k_s_a2_expW<<<dim3(a.nleaf * a.nc, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, a.nc,
                                                                             a.eW);
-    k_s_a2_panel_A<S><<<dim3(a.max_kca, nti, a.nleaf), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.eC, a.nocc, nti,
-                                                                     a.kca, a.offAa, a.panAa);
-    k_s_a2_panel_B<S><<<dim3((a.max_kca + 3) / 4, nct, a.nleaf * a.nc), 128, 0, s>>>(
-        a.leaf_rowoff, a.W, a.eW, a.nocc, a.nrow, a.nc, nct, a.kca, a.offBa, a.panBa);
-    SGemmA g{};
-    g.kca = a.kca; g.offAa = a.offAa; g.offBa = a.offBa; g.tpair = a.tpair;
-    g.eC = a.eC; g.eW = a.eW; g.panA = a.panAa; g.panB = a.panBa; g.Obox = Obox;
-    g.nleaf = a.nleaf; g.nocc = a.nocc; g.nc = a.nc; g.nct = nct; g.ntp = a.ntp; g.leaf_store0 = a.leaf_store0;
-    g.nitems = (long long)a.nleaf * a.nc * a.ntp; g.err = a.err;
-    const int grid = (int)std::min<long long>(g.nitems, a.sm_count);
-    if (grid > 0) k_s_gemm_a<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    for (int bt = 0; bt < a.nbatch_a; ++bt) {
+        const int B0 = a.batch_a[bt], B1 = a.batch_a[bt + 1];
+        if (B1 <= B0) continue;
+        const long long pA0 = a.offAa_h[B0], pB0 = a.offBa_h[B0];
+        uint8_t* panB = a.panAa + (size_t)(a.offAa_h[B1] - pA0) * SL<S>::a_bytes;
+        k_s_a2_panel_A<S><<<dim3(a.max_kca, nti, B1 - B0), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.eC, a.nocc,
+                                                                         nti, a.kca, a.offAa, B0, pA0, a.panAa);
+        k_s_a2_panel_B<S><<<dim3((a.max_kca + 3) / 4, nct, (B1 - B0) * a.nc), 128, 0, s>>>(
+            a.leaf_rowoff, a.W, a.eW, a.nocc, a.nrow, a.nc, nct, a.kca, a.offBa, B0, pB0, panB);
+        SGemmA g{};
+        g.kca = a.kca; g.offAa = a.offAa; g.offBa = a.offBa; g.tpair = a.tpair;
+        g.eC = a.eC; g.eW = a.eW; g.panA = a.panAa; g.panB = panB; g.Obox = Obox;
+        g.nleaf = a.nleaf; g.nocc = a.nocc; g.nc = a.nc; g.nct = nct; g.ntp = a.ntp; g.leaf_store0 = a.leaf_store0;
+        g.B0 = B0; g.nitems = (long long)(B1 - B0) * a.nc * a.ntp; g.panA0 = pA0; g.panB0 = pB0;
+        g.err = a.err;
+        const int grid = (int)std::min<long long>(g.nitems, a.sm_count);
+        if (grid > 0) k_s_gemm_a<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    }
     return cudaGetLastError();
 }
 

@@ -167,6 +167,7 @@ struct occk_ctx {
     int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
     int f64_slices = 0;                     // FP64 steps (a), (e) from integer slices on the tensor core (0: DFMA)
     int last_sliced = 0;                    // the last occk_farfield_K ran steps (a), (e) from slices
+    size_t slice_budget = 0;                // largest slice-panel workspace (0: 32 GB)
     occk::DevBuf splan, spanels;            // its plan (row tiles, panel and item offsets, exponents), panels
     // stage timers
     int timing = 0;
@@ -341,7 +342,7 @@ struct SliceArgs {
     const double* W; const double* Mbox; const float* lscale;
     int* erow; int* fcol;                   // row and column exponents (written)
     const int* rtA; const long long* offA; const long long* item0;   // plan
-    uint8_t* panA; uint8_t* panB;
+    uint8_t* panA;                          // panels of a leaf batch: A, then B
     double* KB;
     int* err;
     // step (a) (the full transform) from slices
@@ -350,7 +351,13 @@ struct SliceArgs {
     const int* leaf_aos;
     const int* kca; const long long* offAa; const long long* offBa; const int* tpair;
     int* eC; int* eW;                       // exponents of C (leaf, i) and W (leaf, lm, j)
-    uint8_t* panAa; uint8_t* panBa;
+    uint8_t* panAa;                         // (the same workspace)
+    // leaf batches whose panels fit the workspace (host): leaves
+    // batch_e[b] .. batch_e[b+1]-1 for step (e), batch_a[] for step (a);
+    // host copies of the panel and item offsets
+    int nbatch_e, nbatch_a;
+    const int* batch_e; const int* batch_a;
+    const long long* offA_h; const long long* item0_h; const long long* offAa_h; const long long* offBa_h;
     // steps (c), (d) in double-FP32 arithmetic
     int ff, nops, nvals;
     float2* ops_ff;                         // [nops][nc][nc] (hi, lo) operators (workspace)

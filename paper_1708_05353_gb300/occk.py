@@ -80,6 +80,7 @@ _SIGS = {
     "occk_batch_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "occk_set_l2p_split": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_fp64_slices": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "occk_set_slice_workspace": (ctypes.c_int, [_vp, ctypes.c_longlong]),
     "occk_set_pair_screen": (ctypes.c_int, [_vp, ctypes.c_double]),
     "occk_pair_screen_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "occk_farfield_J": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp,
@@ -204,6 +205,10 @@ class Context:
         """FP64 steps (a) and (e) from integer slices on the tensor core (6
         or 7 slices; 0: the DFMA kernels)."""
         self.check(lib().occk_set_fp64_slices(self._h, int(slices)), "occk_set_fp64_slices")
+
+    def set_slice_workspace(self, nbytes: int = 0):
+        """Largest slice-panel workspace of the sliced FP64 form (0: 32 GB)."""
+        self.check(lib().occk_set_slice_workspace(self._h, int(nbytes)), "occk_set_slice_workspace")
 
     def set_pair_screen(self, tau: float = 0.0):
         """Occupied-pair screening threshold for occk_farfield_K (0: off)."""

@@ -172,3 +172,21 @@ def test_sliced_learned_selector(ctx):
     print(f"learned ranks, 7 slices vs DFMA: {d:.2e}, |dE| {abs(E7 - E0):.2e}")
     assert np.array_equal(r0, r7)
     assert d < 1e-11 and abs(E7 - E0) <= 1e-11 * abs(E0)
+
+
+def test_sliced_leaf_batches_are_bit_identical(ctx):
+    """With a small slice workspace the leaves run in many batches (panels
+    built and multiplied batch by batch); every output tile is computed the
+    same way, so K and E are bit for bit those of one batch."""
+    from paper_1708_05353_gb300 import occk
+    s = SYSTEMS["chain60"]()
+    tree, C = _build(ctx, s, 6)
+    K1, E1 = _run(ctx, tree, C, 7)
+    ctx.set_slice_workspace(48 << 20)
+    try:
+        K2, E2 = _run(ctx, tree, C, 7)
+    finally:
+        ctx.set_slice_workspace(0)
+    assert torch.equal(K1, K2) and E1 == E2
+    with pytest.raises(occk.OcckError):
+        ctx.set_slice_workspace(-1)
