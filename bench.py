@@ -513,17 +513,19 @@ def learned_object(args, ctx, dev, system, tm):
     K = occk.empty_fortran(system.basis.nao, system.nocc, torch.float64, dev)
     Ex = torch.empty((), dtype=torch.float64, device=dev)
     out = {"lref": Lr, "tau_Eh": args.learned_tau, "what": (
-        "FP64: one build each; split-FP16: one build each after one untimed call; every form on a context "
+        "FP64 and FP64 from integer slices (fp64s): one build each; split-FP16: one build each after one "
+        "untimed call; every form on a context "
         "of its own (the rank-10 workspaces of one form are freed before the next); M2L FLOP ratio from the "
         "chosen ranks, sum_e (L_e+1)^4 vs fixed rank")}
     res = {}
     state = {}
 
-    def one(prec, policy, warm):
+    def one(prec, policy, warm, slices=0):
         # a fresh context and tree per form: FP64 at rank 10 holds ~90 GB of
         # multipoles and local expansions, the tensor-core form its slots and
         # panels; one context with both would not fit
         c2 = occk.Context(ctx.device)
+        c2.set_fp64_slices(slices)
         tree = occk.Tree(c2, system.basis, depth=system.depth, target_atoms_per_leaf=system.target_atoms_per_leaf)
         tree.pair_multipoles(Lr)
         learn.load(c2)
@@ -554,6 +556,15 @@ def learned_object(args, ctx, dev, system, tm):
                            "rank_histogram": [int(x) for x in
                                               __import__("numpy").bincount(ranks, minlength=Lr + 1)],
                            "stage_ms": st_l}
+    # the FP64-accurate form from integer slices and double-FP32 arithmetic
+    ms_sf, E_sf, st_sf = one("fp64", 0, 0, slices=7)
+    res["fp64s_fixed"] = {"ms": round(ms_sf, 2), "abs_dE_vs_fixed_fp64_Eh": abs(E_sf - E_f),
+                          "speedup_vs_fixed_fp64": round(ms_f / ms_sf, 3), "stage_ms": st_sf}
+    ms_sl, E_sl, st_sl = one("fp64", 2, 0, slices=7)
+    res["fp64s_learned"] = {"ms": round(ms_sl, 2), "abs_dE_vs_fixed_fp64_Eh": abs(E_sl - E_f),
+                            "abs_dE_vs_fp64_learned_Eh": abs(E_sl - E_l),
+                            "speedup_vs_fixed_fp64": round(ms_f / ms_sl, 3),
+                            "speedup_vs_fixed_fp64s": round(ms_sf / ms_sl, 3), "stage_ms": st_sl}
     ms_hf, E_hf, _ = one("fp16x3", 0, 1)
     res["fp16x3_fixed"] = {"ms": round(ms_hf, 2), "abs_dE_vs_fixed_fp64_Eh": abs(E_hf - E_f),
                            "speedup_vs_fixed_fp64": round(ms_f / ms_hf, 3)}
