@@ -476,7 +476,8 @@ occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit);
  * orbital) x n_occ x (L+1)^2 in all, 18 GB for 3577 AOs, 660 orbitals, L = 2,
  * 7 slices; batches keep it within occk_set_slice_workspace's budget), and
  * double-FP32 copies of C, the pair values and the operators, allocated on
- * the next call.  OCCK_ERR_ARG for other values.  No
+ * the next call and released (after a device synchronisation) when the form
+ * is turned off with slices = 0.  OCCK_ERR_ARG for other values.  No
  * paper counterpart: an implementation choice of this library. */
 occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices);
 

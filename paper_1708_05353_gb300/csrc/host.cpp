@@ -1566,6 +1566,14 @@ extern "C" occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices) {
     if (!ctx) return OCCK_ERR_ARG;
     if (slices != 0 && slices != 6 && slices != 7) return fail(ctx, OCCK_ERR_ARG, "slices must be 0, 6 or 7");
     ctx->f64_slices = slices;
+    if (slices == 0 && (ctx->spanels.p || ctx->splan.p)) {
+        // the form is off: give its panels and plan back (a later call
+        // allocates them again); wait for work in flight that may use them
+        if (ctx->device >= 0) cudaSetDevice(ctx->device);
+        cudaDeviceSynchronize();
+        ensure(ctx->spanels, 0);
+        ensure(ctx->splan, 0);
+    }
     return OCCK_OK;
 }
 
