@@ -119,7 +119,7 @@ extern "C" void occk_destroy(occk_ctx* c) {
                                 &c->scratch, &c->mlp_prm, &c->mlp_norm, &c->mlp_m, &c->mlp_v, &c->mlp_h,
                                 &c->mlp_grad, &c->mlp_ws, &c->feat, &c->pred, &c->ranks, &c->nrm, &c->gram,
                                 &c->pplan, &c->panels, &c->tpan, &c->tscale, &c->tops, &c->sob, &c->smb,
-                                &c->jbox, &c->scr_o, &c->scr_m, &c->scr_aux}) {
+                                &c->jbox, &c->scr_o, &c->scr_m, &c->scr_aux, &c->splan, &c->spanels}) {
             if (b->p) cudaFree(b->p);
             b->p = nullptr;
         }

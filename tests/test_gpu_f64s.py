@@ -190,3 +190,29 @@ def test_sliced_leaf_batches_are_bit_identical(ctx):
     assert torch.equal(K1, K2) and E1 == E2
     with pytest.raises(occk.OcckError):
         ctx.set_slice_workspace(-1)
+
+
+def test_sliced_workspaces_are_released():
+    """A context that ran the sliced form gives every workspace back when it
+    is destroyed, and the form's panels when it is turned off."""
+    from paper_1708_05353_gb300 import occk
+    s = SYSTEMS["chain60"]()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    c2 = occk.Context(0)
+    tree, C = _build(c2, s, 6)
+    c2.set_fp64_slices(7)
+    occk.farfield_K(c2, tree, C, prec="fp64", want_energy_host=True)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    c2.set_fp64_slices(0)
+    free2 = torch.cuda.mem_get_info()[0]
+    tree.close()
+    c2.close()
+    del C
+    torch.cuda.empty_cache()
+    free3 = torch.cuda.mem_get_info()[0]
+    print(f"free GB: before {free0 / 1e9:.2f}, in use {free1 / 1e9:.2f}, form off {free2 / 1e9:.2f}, "
+          f"closed {free3 / 1e9:.2f}")
+    assert free2 > free1
+    assert free3 >= free0 - (64 << 20)
