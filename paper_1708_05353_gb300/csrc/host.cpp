@@ -1571,8 +1571,11 @@ extern "C" occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices) {
         // allocates them again); wait for work in flight that may use them
         if (ctx->device >= 0) cudaSetDevice(ctx->device);
         cudaDeviceSynchronize();
-        ensure(ctx->spanels, 0);
-        ensure(ctx->splan, 0);
+        for (occk::DevBuf* b : {&ctx->spanels, &ctx->splan}) {
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+            b->bytes = 0;
+        }
     }
     return OCCK_OK;
 }
