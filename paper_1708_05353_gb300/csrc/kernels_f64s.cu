@@ -1,7 +1,9 @@
-// Step (e) in FP64 from integer slices on tcgen05: the error-free splitting of
-// a matrix product into products of small-integer matrices (Ozaki, Ogita,
-// Oishi and Rump, Numer. Algorithms 59 (2012) 95-118), with the slice products
-// on the tensor core and every sum of them exact.
+// The FP64-accurate form off the FP64 pipe.  Steps (a) (full transform) and (e)
+// in FP64 from integer slices on tcgen05: the error-free splitting of a matrix
+// product into products of small-integer matrices (Ozaki, Ogita, Oishi and
+// Rump, Numer. Algorithms 59 (2012) 95-118), with the slice products on the
+// tensor core and every sum of them exact.  The half transform and the tree
+// passes in double-FP32 arithmetic further down.  Step (e) reads
 //
 //   KB[row][i] = sum_{lm, j} A[row][(lm, j)] B[i][(lm, j)]              (Eq. kri)
 //   A = W[lm][row][j] s_lm,   B = w_lm Mcal[lm](i, j) / s_lm            (FP64)
@@ -39,7 +41,7 @@
 // core matrices, LBO 128 bytes along K, SBO 512 bytes between row groups).
 // One CTA per SM walks the tiles (leaf, row tile, orbital tile, K split):
 // warp 0 copies panels into a ring of stages (cp.async.bulk, mbarrier
-// transaction counts), warp 1 issues the MMAs, warps 2-9 drain the group
+// transaction counts), warp 1 issues the MMAs, warps 2-17 drain the group
 // accumulators after every chunk (two TMEM buffers of S x 32 columns
 // alternate, so the drain of one chunk overlaps the MMAs of the next) and
 // write the tile.  Every wait is bounded; on a timeout the CTA raises the
@@ -484,7 +486,7 @@ __device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, 
             }
             if (gc > 0) s_wait(&st.accf[(gc - 1) & 1], ((gc - 1) >> 1) & 1, &st.abort);
         }
-    } else {   // warps 2..9: drain the group accumulators, write the tile
+    } else {   // warps 2..17: drain the group accumulators, write the tile
         const int q4 = warp & 3, part = (warp - 2) >> 2;   // TMEM lane quarter, share of the orbitals
         const int row = q4 * 32 + lane;
         uint32_t gc = 0;
