@@ -47,6 +47,8 @@ MIXED = ["fp32", "tf32", "bf16", "fp16", "bf16x3", "fp16x3"]
 # FP64 with steps (a) and (e) from 7-bit integer slices on the tensor core
 # (occk_set_fp64_slices): FP64 arithmetic everywhere else, exact slice sums
 SLICED = {"fp64s": 7, "fp64s6": 6}
+# FP32 with steps (a) and (e) from 4 integer slices (exact sums) on the tensor core
+F32SLICED = {"fp32s": 4}
 
 
 def parse(argv=None):
@@ -64,7 +66,7 @@ def parse(argv=None):
     p.add_argument("--fp64-slices", type=int, default=0, choices=[0, 6, 7],
                    help="with --prec fp64: steps (a), (e) from this many integer slices on the tensor core and "
                         "the half transform and tree passes in double-FP32 (0: the DFMA form)")
-    p.add_argument("--variants", default=",".join(["fp64s"] + MIXED),
+    p.add_argument("--variants", default=",".join(["fp64s", "fp32s"] + MIXED),
                    help="other precisions timed on the same workload (comma list, or 'none')")
     p.add_argument("--learned-rank", type=int, default=10,
                    help="reference rank of the learned-selector comparison on the protein workload (0: skip)")
@@ -860,11 +862,14 @@ def main(argv=None):
             var = {}
             for vp in [v for v in args.variants.split(",") if v and v != args.prec]:
                 ctx.set_fp64_slices(SLICED.get(vp, 0))
+                ctx.set_fp32_slices(F32SLICED.get(vp, 0))
+                vprec = "fp64" if vp in SLICED else "fp32" if vp in F32SLICED else vp
                 try:
-                    vms, vst = tm.run(lambda: occk.farfield_K(ctx, tree, Cf, prec="fp64" if vp in SLICED else vp,
-                                                              K=K, Ex=Ex), max(5, args.steps // 2), stages=True)
+                    vms, vst = tm.run(lambda: occk.farfield_K(ctx, tree, Cf, prec=vprec, K=K, Ex=Ex),
+                                      max(5, args.steps // 2), stages=True)
                 finally:
                     ctx.set_fp64_slices(0)
+                    ctx.set_fp32_slices(0)
                 var[vp] = {"ms": round(vms, 4), "speedup_vs_fp64": round(ms64 / vms, 3),
                            "tflops": round(total_flops / (vms * 1e-3) / 1e12, 3),
                            "abs_dE_vs_fp64_Eh": abs(float(Ex.item()) - E64),
@@ -875,8 +880,9 @@ def main(argv=None):
             result["variants_reference"] = ("speed-up and errors against the FP64 GPU form of the same run "
                                             f"({ms64:.2f} ms, E = {E64:.10f} Eh), which matches the oracle's "
                                             "columns to the stated error; fp64s / fp64s6: FP64 with steps (a) "
-                                            "and (e) from 7 / 6 integer slices on the tensor core (tflops: FP64 "
-                                            "FLOPs of the algorithm per second)")
+                                            "and (e) from 7 / 6 integer slices on the tensor core and the other "
+                                            "passes in double-FP32; fp32s: FP32 with steps (a) and (e) from 4 "
+                                            "integer slices (tflops: FLOPs of the algorithm per second)")
         if args.workload == "protein" and args.learned_rank > 0:
             try:
                 result["learned"] = learned_object(args, ctx, dev, system, tm)

@@ -477,11 +477,25 @@ occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit);
  * 7 slices; batches keep it within occk_set_slice_workspace's budget), and
  * double-FP32 copies of C, the pair values and the operators, allocated on
  * the next call and released (after a device synchronisation) when the form
- * is turned off with slices = 0.  OCCK_ERR_ARG for other values.  No
+ * is turned off with slices = 0 (and the FP32 form below is off too).  OCCK_ERR_ARG for other values.  No
  * paper counterpart: an implementation choice of this library. */
 occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices);
 
-/* Largest workspace of slice panels of the form above, in bytes (0, the
+/* Steps (a) (full transform, Eq. motrans) and (e) (Eq. kri) of the OCCK_FP32
+ * form on the tensor core from 4 integer slices per operand, with the same
+ * engine as occk_set_fp64_slices: 4 slices of at most 7 bits hold every FP32
+ * operand within 2^-28 of its row's largest entry (exactly where the row's
+ * entries are within a factor 16 of each other), the slice products are summed
+ * exactly and combined in FP64, so these two steps carry no FP32 rounding and
+ * no bias of the tensor core's accumulation; the half transform, M2M, M2L and
+ * L2L stay FP32 SIMT.  slices = 0 (default) keeps the FP32 SIMT GEMMs; 4
+ * enables the form for calls with prec = OCCK_FP32 and no pair screening or
+ * column block.  Workspace as for occk_set_fp64_slices (4/7 of it per leaf
+ * batch), released when both forms are off.  OCCK_ERR_ARG for other values.
+ * No paper counterpart: an implementation choice of this library. */
+occk_status occk_set_fp32_slices(occk_ctx* ctx, int slices);
+
+/* Largest workspace of slice panels of the forms above, in bytes (0, the
  * default: 32 GB).  The leaves are processed in batches whose panels fit
  * (a leaf larger than the budget is a batch of its own); the result does not
  * depend on the batching (each output tile is computed the same way).

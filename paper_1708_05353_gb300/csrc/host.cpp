@@ -819,7 +819,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     }
     // FP64 steps (a) and (e) from integer slices on the tensor core: every
     // pair, all columns (the DFMA kernels serve screening and column blocks)
-    const bool sliced = prec == OCCK_FP64 && ctx->f64_slices > 0 && ctx->col_i1 == 0 && ctx->screen_tau <= 0;
+    const int nslices = prec == OCCK_FP64 ? ctx->f64_slices : prec == OCCK_FP32 ? ctx->f32_slices : 0;
+    const bool sliced = nslices > 0 && ctx->col_i1 == 0 && ctx->screen_tau <= 0;
     occk::SliceArgs sa{};
     // host plan of the sliced steps, alive until the launches below
     std::vector<long long> offA(nleaf + 1), item0(nleaf + 1), offAa(nleaf + 1), offBa(nleaf + 1);
@@ -877,8 +878,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         const size_t plan_bytes = o_cff + al16(8 * (size_t)t->nao * nocc);
         // leaf batches whose panels fit a workspace of at most 32 GB (one
         // batch for the protein-sized cluster at L = 2; several at high rank)
-        const size_t pa = occk::slice_panel_bytes(ctx->f64_slices, true);
-        const size_t pbb = occk::slice_panel_bytes(ctx->f64_slices, false);
+        const size_t pa = occk::slice_panel_bytes(nslices, true);
+        const size_t pbb = occk::slice_panel_bytes(nslices, false);
         const size_t budget = ctx->slice_budget > 0 ? ctx->slice_budget : size_t(32) << 30;
         auto e_bytes = [&](int B0, int B1) {
             return pa * (size_t)(offA[B1] - offA[B0]) + pbb * (size_t)(B1 - B0) * nct * KC;
@@ -927,7 +928,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         sa.tpair = (const int*)(x + o_tp);
         sa.eC = (int*)(x + o_eC);
         sa.eW = (int*)(x + o_eW);
-        sa.ff = 1;
+        sa.ff = prec == OCCK_FP64 ? 1 : 0;   // the FP32 form keeps its FP32 SIMT passes
+        sa.f32 = prec == OCCK_FP32 ? 1 : 0;
         sa.nops = (int)nops;
         sa.ops_ff = (float2*)(x + o_ff);
         sa.nvals = t->nvals;
@@ -942,7 +944,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         sa.item0_h = item0.data();
         sa.offAa_h = offAa.data();
         sa.offBa_h = offBa.data();
-        sa.S = ctx->f64_slices;
+        sa.S = nslices;
         sa.nocc = nocc; sa.nc = nc; sa.nrow = nrow; sa.nleaf = nleaf;
         sa.leaf_store0 = t->level_off[D] - first;
         sa.max_rt = max_rt; sa.nsplit = nsplit; sa.sm_count = std::max(ctx->sm_count, 1);
@@ -992,8 +994,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     a.max_rows = max_rows;
     a.l2p_nsplit = l2p_nsplit;
     if (sliced) {
-        sa.W = (const double*)ctx->w.p;
-        sa.Mbox = (const double*)ctx->mbox.p;
+        sa.W = ctx->w.p;
+        sa.Mbox = ctx->mbox.p;
         sa.KB = (double*)ctx->kb.p;
         a.slices = &sa;
     }
@@ -1555,6 +1557,22 @@ extern "C" occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit) {
     return OCCK_OK;
 }
 
+extern "C" occk_status occk_set_fp32_slices(occk_ctx* ctx, int slices) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (slices != 0 && slices != 4) return fail(ctx, OCCK_ERR_ARG, "slices must be 0 or 4");
+    ctx->f32_slices = slices;
+    if (slices == 0 && ctx->f64_slices == 0 && (ctx->spanels.p || ctx->splan.p)) {
+        if (ctx->device >= 0) cudaSetDevice(ctx->device);
+        cudaDeviceSynchronize();
+        for (occk::DevBuf* b : {&ctx->spanels, &ctx->splan}) {
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+            b->bytes = 0;
+        }
+    }
+    return OCCK_OK;
+}
+
 extern "C" occk_status occk_set_slice_workspace(occk_ctx* ctx, long long bytes) {
     if (!ctx) return OCCK_ERR_ARG;
     if (bytes < 0) return fail(ctx, OCCK_ERR_ARG, "bytes must be >= 0");
@@ -1566,7 +1584,7 @@ extern "C" occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices) {
     if (!ctx) return OCCK_ERR_ARG;
     if (slices != 0 && slices != 6 && slices != 7) return fail(ctx, OCCK_ERR_ARG, "slices must be 0, 6 or 7");
     ctx->f64_slices = slices;
-    if (slices == 0 && (ctx->spanels.p || ctx->splan.p)) {
+    if (slices == 0 && ctx->f32_slices == 0 && (ctx->spanels.p || ctx->splan.p)) {
         // the form is off: give its panels and plan back (a later call
         // allocates them again); wait for work in flight that may use them
         if (ctx->device >= 0) cudaSetDevice(ctx->device);

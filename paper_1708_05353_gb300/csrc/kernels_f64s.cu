@@ -71,7 +71,7 @@ template <int S>
 struct SL {
     static constexpr int a_bytes = S * kAPart, b_bytes = S * kBPart;
     static constexpr int stage = a_bytes + b_bytes;
-    static constexpr int ring = S >= 7 ? 3 : 3;
+    static constexpr int ring = S <= 4 ? 4 : 3;
     static constexpr int smem = ring * stage;
     static constexpr uint32_t buf = (uint32_t)S * kSN;   // TMEM columns of one accumulator set
 };
@@ -143,6 +143,28 @@ __device__ __forceinline__ long long s_fixed(double v, int t) {
     return bits < 0 ? -r : r;
 }
 
+// The same for FP32 operands (the FP32 form): |v| < 2^E, and round(v 2^t).
+__device__ __forceinline__ int s_expo(float v) {
+    const int ef = (int)((__float_as_uint(v) >> 23) & 0xFF);
+    return ef == 0 ? -2000 : ef - 126;
+}
+__device__ __forceinline__ long long s_fixed(float v, int t) {
+    const unsigned bits = __float_as_uint(v);
+    const int ef = (int)((bits >> 23) & 0xFF);
+    long long mant = bits & 0x7FFFFF;
+    int E = -149;
+    if (ef != 0) {
+        mant |= 1LL << 23;
+        E = ef - 150;
+    }
+    const int sh = E + t;
+    long long r;
+    if (sh >= 0) r = mant << min(sh, 40);
+    else if (sh > -40) r = (mant + (1LL << (-sh - 1))) >> (-sh);
+    else r = 0;
+    return (bits >> 31) ? -r : r;
+}
+
 // 2^k for -1022 <= k <= 1023 (clamped), built from its bits
 __device__ __forceinline__ double s_pow2(int k) {
     k = max(-1022, min(1023, k));
@@ -156,14 +178,15 @@ __device__ __forceinline__ int s_warp_max(int v) {
 }
 
 // e_row: one warp per stored row, the exponent bound of max |W 2^k_lm| over (lm, j)
-__global__ void k_s_rowexp(const double* __restrict__ W, const float* __restrict__ lscale, int nrow, int nocc,
+template <typename T>
+__global__ void k_s_rowexp(const T* __restrict__ W, const float* __restrict__ lscale, int nrow, int nocc,
                            int nc, int* __restrict__ erow) {
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= nrow) return;
     int m = -2000;
     for (int lm = 0; lm < nc; ++lm) {
         const int k = s_klm(lscale, lm);
-        const double* w = W + ((size_t)lm * nrow + row) * nocc;
+        const T* w = W + ((size_t)lm * nrow + row) * nocc;
         for (int j = lane; j < nocc; j += 32) m = max(m, s_expo(w[j]) + k);
     }
     m = s_warp_max(m);
@@ -172,7 +195,8 @@ __global__ void k_s_rowexp(const double* __restrict__ W, const float* __restrict
 
 // f_i: one warp per (leaf, orbital i), the exponent bound of
 // max |w_lm Mcal(i, j) 2^-k_lm| over (lm, j)
-__global__ void k_s_colexp(const double* __restrict__ Mbox, const float* __restrict__ lscale, int nleaf, int nocc,
+template <typename T>
+__global__ void k_s_colexp(const T* __restrict__ Mbox, const float* __restrict__ lscale, int nleaf, int nocc,
                            int nc, int leaf_store0, int* __restrict__ fcol) {
     const long long x = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -185,7 +209,7 @@ __global__ void k_s_colexp(const double* __restrict__ Mbox, const float* __restr
         bool neg;
         s_weight(lm, a, neg);
         const int k = a - s_klm(lscale, lm);
-        const double* M = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
+        const T* M = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
         for (int j = lane; j < nocc; j += 32) m = max(m, s_expo(M[i <= j ? s_tri(i, j, nocc) : s_tri(j, i, nocc)]) + k);
     }
     m = s_warp_max(m);
@@ -213,9 +237,9 @@ __device__ __forceinline__ void s_put8(uint8_t* dst, uint32_t part_bytes, long l
 }
 
 // A panels: block (stage kc, row tile rt, leaf B), thread = panel row
-template <int S>
+template <int S, typename T>
 __global__ void __launch_bounds__(128)
-k_s_panel_A(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const float* __restrict__ lscale,
+k_s_panel_A(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const float* __restrict__ lscale,
             const int* __restrict__ erow, int nocc, int nrow, int jc, int KC, const int* __restrict__ rtA,
             const long long* __restrict__ offA, int B0, long long pan0, uint8_t* __restrict__ pan) {
     const int kc = blockIdx.x, rt = blockIdx.y, B = B0 + blockIdx.z;
@@ -224,7 +248,7 @@ k_s_panel_A(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, c
     const int r = rt * 128 + threadIdx.x;
     const int lm = kc / jc, j0 = (kc % jc) * kSK;
     const bool live = r < nr;
-    const double* w = W + ((size_t)lm * nrow + rb0 + (live ? r : 0)) * nocc;
+    const T* w = W + ((size_t)lm * nrow + rb0 + (live ? r : 0)) * nocc;
     const int t = s_klm(lscale, lm) - (live ? erow[rb0 + r] : 0) + 55;
     uint8_t* panel = pan + (size_t)(offA[B] - pan0 + (long long)rt * KC + kc) * SL<S>::a_bytes;
 #pragma unroll
@@ -240,9 +264,9 @@ k_s_panel_A(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, c
 }
 
 // B panels: block (4 stages, orbital tile ct, leaf B), thread = (orbital, stage)
-template <int S>
+template <int S, typename T>
 __global__ void __launch_bounds__(128)
-k_s_panel_B(const double* __restrict__ Mbox, const float* __restrict__ lscale, const int* __restrict__ fcol,
+k_s_panel_B(const T* __restrict__ Mbox, const float* __restrict__ lscale, const int* __restrict__ fcol,
             int nocc, int nc, int leaf_store0, int jc, int KC, int nct, int B0, uint8_t* __restrict__ pan) {
     const int kc = blockIdx.x * 4 + (threadIdx.x >> 5), ct = blockIdx.y, B = B0 + blockIdx.z;
     if (kc >= KC) return;
@@ -252,7 +276,7 @@ k_s_panel_B(const double* __restrict__ Mbox, const float* __restrict__ lscale, c
     bool neg;
     s_weight(lm, a, neg);
     const size_t P = (size_t)nocc * (nocc + 1) / 2;
-    const double* M = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
+    const T* M = Mbox + ((size_t)(leaf_store0 + B) * nc + lm) * P;
     const bool live = i < nocc;
     const int t = a - s_klm(lscale, lm) - (live ? fcol[(size_t)B * nocc + i] : 0) + 55;
     uint8_t* panel = pan + (size_t)(((long long)(B - B0) * nct + ct) * KC + kc) * SL<S>::b_bytes;
@@ -271,8 +295,9 @@ k_s_panel_B(const double* __restrict__ Mbox, const float* __restrict__ lscale, c
 
 // Step (a) operands: A[i][r] = C_ri (rows i, K = the leaf's AO rows r), one
 // exponent per (leaf, i); B[j][r] = W[lm][r][j], one exponent per (leaf, lm, j).
+template <typename T>
 __global__ void k_s_a2_expC(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos,
-                            const double* __restrict__ Ct, int nocc, int* __restrict__ eC) {
+                            const T* __restrict__ Ct, int nocc, int* __restrict__ eC) {
     const int B = blockIdx.x, i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= nocc) return;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
@@ -281,21 +306,22 @@ __global__ void k_s_a2_expC(const int* __restrict__ leaf_rowoff, const int* __re
     eC[(size_t)B * nocc + i] = m <= -1000 ? 0 : m;
 }
 
-__global__ void k_s_a2_expW(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, int nocc, int nrow,
+template <typename T>
+__global__ void k_s_a2_expW(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, int nocc, int nrow,
                             int nc, int* __restrict__ eW) {
     const int B = blockIdx.x / nc, lm = blockIdx.x % nc, j = blockIdx.y * blockDim.x + threadIdx.x;
     if (j >= nocc) return;
     const int rb0 = leaf_rowoff[B], nr = leaf_rowoff[B + 1] - rb0;
-    const double* w = W + ((size_t)lm * nrow + rb0) * nocc + j;
+    const T* w = W + ((size_t)lm * nrow + rb0) * nocc + j;
     int m = -2000;
     for (int r = 0; r < nr; ++r) m = max(m, s_expo(w[(size_t)r * nocc]));
     eW[((size_t)B * nc + lm) * nocc + j] = m <= -1000 ? 0 : m;
 }
 
 // A panels of step (a): block (stage kc, row tile ti, leaf B), thread = orbital i
-template <int S>
+template <int S, typename T>
 __global__ void __launch_bounds__(128)
-k_s_a2_panel_A(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const double* __restrict__ Ct,
+k_s_a2_panel_A(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf_aos, const T* __restrict__ Ct,
                const int* __restrict__ eC, int nocc, int nti, const int* __restrict__ kca,
                const long long* __restrict__ offAa, int B0, long long pan0, uint8_t* __restrict__ pan) {
     const int kc = blockIdx.x, ti = blockIdx.y, B = B0 + blockIdx.z;
@@ -319,9 +345,9 @@ k_s_a2_panel_A(const int* __restrict__ leaf_rowoff, const int* __restrict__ leaf
 
 // B panels of step (a): block (4 stages, column tile tj, leaf B * nc + lm),
 // thread = (orbital j, stage)
-template <int S>
+template <int S, typename T>
 __global__ void __launch_bounds__(128)
-k_s_a2_panel_B(const int* __restrict__ leaf_rowoff, const double* __restrict__ W, const int* __restrict__ eW,
+k_s_a2_panel_B(const int* __restrict__ leaf_rowoff, const T* __restrict__ W, const int* __restrict__ eW,
                int nocc, int nrow, int nc, int nct, const int* __restrict__ kca, const long long* __restrict__ offBa,
                int B0, long long pan0, uint8_t* __restrict__ pan) {
     const int B = B0 + blockIdx.z / nc, lm = blockIdx.z % nc, tj = blockIdx.y;
@@ -331,7 +357,7 @@ k_s_a2_panel_B(const int* __restrict__ leaf_rowoff, const double* __restrict__ W
     const int jl = threadIdx.x & 31, j = tj * kSN + jl;
     const bool live = j < nocc;
     const int t = 55 - (live ? eW[((size_t)B * nc + lm) * nocc + j] : 0);
-    const double* w = W + ((size_t)lm * nrow + rb0) * nocc + j;
+    const T* w = W + ((size_t)lm * nrow + rb0) * nocc + j;
     uint8_t* panel = pan + (size_t)(offBa[B] - pan0 + ((long long)lm * nct + tj) * kca[B] + kc) * SL<S>::b_bytes;
 #pragma unroll
     for (int k8 = 0; k8 < kSK; k8 += 8) {
@@ -370,7 +396,7 @@ struct SGemmA {
     const int* kca; const long long* offAa; const long long* offBa; const int* tpair;
     const int* eC; const int* eW;
     const uint8_t* panA; const uint8_t* panB;
-    double* Obox;
+    void* Obox;                              // double (FP64 form) or float (FP32 form)
     int nleaf, nocc, nc, nct, ntp, leaf_store0;
     int B0;                                  // first leaf of the batch
     long long nitems, panA0, panB0;          // offAa, offBa of leaf B0
@@ -612,7 +638,7 @@ k_s_gemm_e(SGemmE g) {
 
 // Step (a): O[B][lm][(i, j)] = sum_r C_ri W[lm][r][j] for i <= j, rows i of a
 // 128-orbital tile, columns j of a 32-orbital tile (Eq. motrans)
-template <int S>
+template <int S, typename T>
 __global__ void __launch_bounds__(kSThreads, 1)
 k_s_gemm_a(SGemmA g) {
     using C = SL<S>;
@@ -638,15 +664,30 @@ k_s_gemm_a(SGemmA g) {
         decode(it, B, lm, ti, tj);
         const int i = ti * 128 + row;
         if (i >= g.nocc) return;
-        double v[kSCols];
-        s_combine<S>(acc, v);
         const int ec = g.eC[(size_t)B * g.nocc + i];
         const int* ew = g.eW + ((size_t)B * g.nc + lm) * g.nocc;
-        double* o = g.Obox + ((size_t)(g.leaf_store0 + B) * g.nc + lm) * P + s_tri(i, i, g.nocc) - (size_t)i;
+        T* o = (T*)g.Obox + ((size_t)(g.leaf_store0 + B) * g.nc + lm) * P + s_tri(i, i, g.nocc) - (size_t)i;
+        if constexpr (sizeof(T) == 4) {
+            // an FP32 result: the group sums combined on the FP32 pipe (a few
+            // roundings at 2^-24, below the FP32 store's own), off the FP64 pipe
 #pragma unroll
-        for (int c = 0; c < kSCols; ++c) {
-            const int j = tj * kSN + part * kSCols + c;
-            if (j >= i && j < g.nocc) o[j] = v[c] * s_pow2(ec + ew[j]);
+            for (int c = 0; c < kSCols; ++c) {
+                const int j = tj * kSN + part * kSCols + c;
+                float v = 0.f;
+#pragma unroll
+                for (int d = S - 1; d >= 0; --d)
+                    v = fmaf((float)acc[d][c], __int_as_float((127 - (12 + 7 * d)) << 23), v);
+                const int k = max(-126, min(127, ec + (j < g.nocc ? ew[j] : 0)));
+                if (j >= i && j < g.nocc) o[j] = v * __int_as_float((k + 127) << 23);
+            }
+        } else {
+            double v[kSCols];
+            s_combine<S>(acc, v);
+#pragma unroll
+            for (int c = 0; c < kSCols; ++c) {
+                const int j = tj * kSN + part * kSCols + c;
+                if (j >= i && j < g.nocc) o[j] = (T)(v[c] * s_pow2(ec + ew[j]));
+            }
         }
     };
     s_gemm_body<S>(g.nitems, src, out, g.err);
@@ -834,21 +875,25 @@ cudaError_t l2p_attrs() {
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_s_gemm_e<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_s_gemm_a<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
+            e = cudaFuncSetAttribute(k_s_gemm_a<S, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_s_gemm_a<S, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<S>::smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     return cudaSuccess;
 }
 
-template <int S>
+template <int S, typename T>
 cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
+    const T* W = (const T*)a.W;
+    const T* Mbox = (const T*)a.Mbox;
     cudaError_t e0 = l2p_attrs<S>();
     if (e0 != cudaSuccess) return e0;
     const int jc = (a.nocc + kSK - 1) / kSK, KC = a.nc * jc, nct = (a.nocc + kSN - 1) / kSN;
-    k_s_rowexp<<<(a.nrow + 7) / 8, 256, 0, s>>>(a.W, a.lscale, a.nrow, a.nocc, a.nc, a.erow);
+    k_s_rowexp<T><<<(a.nrow + 7) / 8, 256, 0, s>>>(W, a.lscale, a.nrow, a.nocc, a.nc, a.erow);
     const long long ncol = (long long)a.nleaf * a.nocc;
-    k_s_colexp<<<(unsigned)((ncol + 7) / 8), 256, 0, s>>>(a.Mbox, a.lscale, a.nleaf, a.nocc, a.nc, a.leaf_store0,
+    k_s_colexp<T><<<(unsigned)((ncol + 7) / 8), 256, 0, s>>>(Mbox, a.lscale, a.nleaf, a.nocc, a.nc, a.leaf_store0,
                                                           a.fcol);
     // leaf batches whose panels fit the workspace: build, then multiply
     for (int bt = 0; bt < a.nbatch_e; ++bt) {
@@ -856,9 +901,9 @@ cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
         if (B1 <= B0) continue;
         const long long pA0 = a.offA_h[B0];
         uint8_t* panB = a.panA + (size_t)(a.offA_h[B1] - pA0) * SL<S>::a_bytes;
-        k_s_panel_A<S><<<dim3(KC, a.max_rt, B1 - B0), 128, 0, s>>>(a.leaf_rowoff, a.W, a.lscale, a.erow, a.nocc,
+        k_s_panel_A<S, T><<<dim3(KC, a.max_rt, B1 - B0), 128, 0, s>>>(a.leaf_rowoff, W, a.lscale, a.erow, a.nocc,
                                                                    a.nrow, jc, KC, a.rtA, a.offA, B0, pA0, a.panA);
-        k_s_panel_B<S><<<dim3((KC + 3) / 4, nct, B1 - B0), 128, 0, s>>>(a.Mbox, a.lscale, a.fcol, a.nocc, a.nc,
+        k_s_panel_B<S, T><<<dim3((KC + 3) / 4, nct, B1 - B0), 128, 0, s>>>(Mbox, a.lscale, a.fcol, a.nocc, a.nc,
                                                                         a.leaf_store0, jc, KC, nct, B0, panB);
         SGemmE g{};
         g.leaf_rowoff = a.leaf_rowoff; g.rtA = a.rtA; g.offA = a.offA; g.item0 = a.item0;
@@ -872,23 +917,24 @@ cudaError_t l2p_slices_typed(const SliceArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int S>
-cudaError_t full_slices_typed(const SliceArgs& a, const double* Ct, double* Obox, cudaStream_t s) {
+template <int S, typename T>
+cudaError_t full_slices_typed(const SliceArgs& a, const T* Ct, T* Obox, cudaStream_t s) {
+    const T* W = (const T*)a.W;
     cudaError_t e = l2p_attrs<S>();
     if (e != cudaSuccess) return e;
     const int nct = (a.nocc + kSN - 1) / kSN, nti = (a.nocc + 127) / 128;
-    k_s_a2_expC<<<dim3(a.nleaf, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.nocc, a.eC);
-    k_s_a2_expW<<<dim3(a.nleaf * a.nc, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, a.W, a.nocc, a.nrow, a.nc,
+    k_s_a2_expC<T><<<dim3(a.nleaf, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.nocc, a.eC);
+    k_s_a2_expW<T><<<dim3(a.nleaf * a.nc, (a.nocc + 127) / 128), 128, 0, s>>>(a.leaf_rowoff, W, a.nocc, a.nrow, a.nc,
                                                                             a.eW);
     for (int bt = 0; bt < a.nbatch_a; ++bt) {
         const int B0 = a.batch_a[bt], B1 = a.batch_a[bt + 1];
         if (B1 <= B0) continue;
         const long long pA0 = a.offAa_h[B0], pB0 = a.offBa_h[B0];
         uint8_t* panB = a.panAa + (size_t)(a.offAa_h[B1] - pA0) * SL<S>::a_bytes;
-        k_s_a2_panel_A<S><<<dim3(a.max_kca, nti, B1 - B0), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.eC, a.nocc,
+        k_s_a2_panel_A<S, T><<<dim3(a.max_kca, nti, B1 - B0), 128, 0, s>>>(a.leaf_rowoff, a.leaf_aos, Ct, a.eC, a.nocc,
                                                                          nti, a.kca, a.offAa, B0, pA0, a.panAa);
-        k_s_a2_panel_B<S><<<dim3((a.max_kca + 3) / 4, nct, (B1 - B0) * a.nc), 128, 0, s>>>(
-            a.leaf_rowoff, a.W, a.eW, a.nocc, a.nrow, a.nc, nct, a.kca, a.offBa, B0, pB0, panB);
+        k_s_a2_panel_B<S, T><<<dim3((a.max_kca + 3) / 4, nct, (B1 - B0) * a.nc), 128, 0, s>>>(
+            a.leaf_rowoff, W, a.eW, a.nocc, a.nrow, a.nc, nct, a.kca, a.offBa, B0, pB0, panB);
         SGemmA g{};
         g.kca = a.kca; g.offAa = a.offAa; g.offBa = a.offBa; g.tpair = a.tpair;
         g.eC = a.eC; g.eW = a.eW; g.panA = a.panAa; g.panB = panB; g.Obox = Obox;
@@ -896,7 +942,7 @@ cudaError_t full_slices_typed(const SliceArgs& a, const double* Ct, double* Obox
         g.B0 = B0; g.nitems = (long long)(B1 - B0) * a.nc * a.ntp; g.panA0 = pA0; g.panB0 = pB0;
         g.err = a.err;
         const int grid = (int)std::min<long long>(g.nitems, a.sm_count);
-        if (grid > 0) k_s_gemm_a<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+        if (grid > 0) k_s_gemm_a<S, T><<<grid, kSThreads, SL<S>::smem, s>>>(g);
     }
     return cudaGetLastError();
 }
@@ -908,9 +954,13 @@ int slice_tile_n() { return kSN; }
 int slice_max_stages() { return kChunk * kMaxChunks; }
 size_t slice_panel_bytes(int S, bool a) { return (size_t)S * (a ? kAPart : kBPart); }
 
-cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cudaStream_t s) {
-    if (a.S == 7) return full_slices_typed<7>(a, Ct, Obox, s);
-    if (a.S == 6) return full_slices_typed<6>(a, Ct, Obox, s);
+cudaError_t full_slices(const SliceArgs& a, const void* Ct, void* Obox, cudaStream_t s) {
+    if (a.f32) {
+        if (a.S == 4) return full_slices_typed<4, float>(a, (const float*)Ct, (float*)Obox, s);
+        return cudaErrorInvalidValue;
+    }
+    if (a.S == 7) return full_slices_typed<7, double>(a, (const double*)Ct, (double*)Obox, s);
+    if (a.S == 6) return full_slices_typed<6, double>(a, (const double*)Ct, (double*)Obox, s);
     return cudaErrorInvalidValue;
 }
 
@@ -979,8 +1029,12 @@ cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {
 }
 
 cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s) {
-    if (a.S == 7) return l2p_slices_typed<7>(a, s);
-    if (a.S == 6) return l2p_slices_typed<6>(a, s);
+    if (a.f32) {
+        if (a.S == 4) return l2p_slices_typed<4, float>(a, s);
+        return cudaErrorInvalidValue;
+    }
+    if (a.S == 7) return l2p_slices_typed<7, double>(a, s);
+    if (a.S == 6) return l2p_slices_typed<6, double>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -700,9 +700,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         pa.panB = a.pan_a2B;
         cudaError_t e2 = panel_a2(a.prec, pa, s);
         if (e2 != cudaSuccess) return e2;
-    } else if (sizeof(T) == 8 && a.slices && a.slices->full) {
-        // FP64 from integer slices on the tensor core (kernels_f64s.cu)
-        cudaError_t e2 = full_slices(*a.slices, (const double*)Ct, (double*)Ob, s);
+    } else if (a.slices && a.slices->full) {
+        // from integer slices on the tensor core, exact sums (kernels_f64s.cu)
+        cudaError_t e2 = full_slices(*a.slices, Ct, Ob, s);
         if (e2 != cudaSuccess) return e2;
     } else if constexpr (sizeof(T) == 8) {
         constexpr int BM = kFullTileFP64, BK = 8, TM = 4;
@@ -970,8 +970,8 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         pa.panB = a.pan_l2pB;
         cudaError_t e2 = panel_l2p(a.prec, pa, s);
         if (e2 != cudaSuccess) return e2;
-    } else if (sizeof(T) == 8 && a.slices) {
-        // FP64 from integer slices on the tensor core (kernels_f64s.cu)
+    } else if (a.slices) {
+        // from integer slices on the tensor core, exact sums (kernels_f64s.cu)
         cudaError_t e2 = l2p_slices(*a.slices, s);
         if (e2 != cudaSuccess) return e2;
     } else if constexpr (sizeof(T) == 8) {

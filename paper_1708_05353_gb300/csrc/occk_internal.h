@@ -166,6 +166,7 @@ struct occk_ctx {
     int last_slot = 0;                      // last run used the slot pipeline
     int l2p_split = 0;                      // FP32 step (e) K-range splits (0: automatic)
     int f64_slices = 0;                     // FP64 steps (a), (e) from integer slices on the tensor core (0: DFMA)
+    int f32_slices = 0;                     // FP32 steps (a), (e) from 4 integer slices (0: SIMT FFMA)
     int last_sliced = 0;                    // the last occk_farfield_K ran steps (a), (e) from slices
     size_t slice_budget = 0;                // largest slice-panel workspace (0: 32 GB)
     occk::DevBuf splan, spanels;            // its plan (row tiles, panel and item offsets, exponents), panels
@@ -339,7 +340,8 @@ struct SliceArgs {
     int nocc, nc, nrow, nleaf, leaf_store0, max_rt, nsplit, sm_count;
     long long nitems;                       // GEMM tiles (leaf, row tile, orbital tile, K split)
     const int* leaf_rowoff;
-    const double* W; const double* Mbox; const float* lscale;
+    int f32;                                // operands FP32 (the FP32 form) instead of FP64
+    const void* W; const void* Mbox; const float* lscale;
     int* erow; int* fcol;                   // row and column exponents (written)
     const int* rtA; const long long* offA; const long long* item0;   // plan
     uint8_t* panA;                          // panels of a leaf batch: A, then B
@@ -368,7 +370,7 @@ int slice_tile_n();                         // orbitals of one GEMM tile
 int slice_max_stages();                     // stages of one tile (exact int32 group sums)
 size_t slice_panel_bytes(int S, bool a);    // bytes of one A (a) or B panel
 cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s);
-cudaError_t full_slices(const SliceArgs& a, const double* Ct, double* Obox, cudaStream_t s);
+cudaError_t full_slices(const SliceArgs& a, const void* Ct, void* Obox, cudaStream_t s);
 // M2L with L2L, fused per level, in double-FP32 arithmetic on the FP32 pipe
 // (the sliced FP64 form); O and Mcal are FP64 before and after the call
 struct FFArgs {

@@ -81,6 +81,7 @@ _SIGS = {
     "occk_set_l2p_split": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_fp64_slices": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_slice_workspace": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+    "occk_set_fp32_slices": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_pair_screen": (ctypes.c_int, [_vp, ctypes.c_double]),
     "occk_pair_screen_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "occk_farfield_J": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp,
@@ -205,6 +206,11 @@ class Context:
         """FP64 steps (a) and (e) from integer slices on the tensor core (6
         or 7 slices; 0: the DFMA kernels)."""
         self.check(lib().occk_set_fp64_slices(self._h, int(slices)), "occk_set_fp64_slices")
+
+    def set_fp32_slices(self, slices: int = 0):
+        """FP32 steps (a) and (e) from 4 integer slices on the tensor core
+        with exact sums (0: the FP32 SIMT GEMMs)."""
+        self.check(lib().occk_set_fp32_slices(self._h, int(slices)), "occk_set_fp32_slices")
 
     def set_slice_workspace(self, nbytes: int = 0):
         """Largest slice-panel workspace of the sliced FP64 form (0: 32 GB)."""
