@@ -361,7 +361,9 @@ occk_status occk_device_status(occk_ctx* ctx, void* stream);
 
 /* Test aid for the failure path of the bounded device waits (no paper
  * counterpart).  Sets how many times the MMA-issuing thread of the
- * tensor-core panel GEMMs of steps (a) and (e) polls for a stage's operands
+ * tensor-core panel GEMMs of steps (a) and (e) (the mixed forms and the
+ * integer-slice forms of occk_set_fp64_slices / occk_set_fp32_slices) polls
+ * for a stage's operands
  * before it gives up (polls < 0 restores the default, 2^22; 0 gives up at the
  * first wait).  A wait that gives up makes the kernel raise its abort flag,
  * wait (with the default limit) for its own bulk copies and MMAs in flight,

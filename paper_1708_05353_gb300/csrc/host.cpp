@@ -1539,6 +1539,7 @@ extern "C" occk_status occk_debug_set_wait_limit(occk_ctx* ctx, long long polls)
     if (ctx->device < 0) return fail(ctx, OCCK_ERR_UNSUPPORTED, "no device bound to this context");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = occk::set_mma_wait_limit(polls);
+    if (e == cudaSuccess) e = occk::set_slice_wait_limit(polls);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occk_debug_set_wait_limit");
     return OCCK_OK;
 }

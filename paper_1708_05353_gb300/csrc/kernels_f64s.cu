@@ -87,8 +87,13 @@ __device__ __forceinline__ void s_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void s_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ bool s_wait(uint64_t* bar, uint32_t parity, const int* flag) {
-    for (uint32_t it = 0; it < kWaitS; ++it) {
+// Polls allowed to the MMA thread's wait for a stage's operands: kWaitS in
+// normal use; occk_debug_set_wait_limit lowers it so that a test can make that
+// wait give up and exercise the abort path (every other wait keeps kWaitS).
+__device__ uint32_t g_s_full_wait = kWaitS;
+
+__device__ __forceinline__ bool s_wait(uint64_t* bar, uint32_t parity, const int* flag, uint32_t limit = kWaitS) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*(const volatile int*)flag) return false;
         if (it > 64) __nanosleep(32);
@@ -473,6 +478,7 @@ __device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, 
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issue
             uint32_t gs = 0, gc = 0;
+            const uint32_t full_wait = g_s_full_wait;
             for (long long it = blockIdx.x; it < nitems && !*(volatile int*)&st.abort; it += gridDim.x) {
                 const uint8_t *A, *Bp;
                 int nk;
@@ -480,7 +486,7 @@ __device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, 
                 for (int kc = 0; kc < nk; ++kc, ++gs) {
                     const int r = (int)(gs % C::ring), q = kc % kChunk;
                     const int b = (int)(gc & 1);
-                    if (!s_wait(&st.full[r], (gs / C::ring) & 1, &st.abort) ||
+                    if (!s_wait(&st.full[r], (gs / C::ring) & 1, &st.abort, full_wait) ||
                         (q == 0 && gc >= 2 && !s_wait(&st.acce[b], ((gc >> 1) - 1) & 1, &st.abort))) {
                         st.abort = 1;
                         break;
@@ -510,7 +516,11 @@ __device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, 
                     }
                 }
             }
-            if (gc > 0) s_wait(&st.accf[(gc - 1) & 1], ((gc - 1) >> 1) & 1, &st.abort);
+            // every MMA issued is complete before TMEM is given back: the last
+            // commit (to the stage's empty barrier, also after an abort in the
+            // middle of a chunk) covers all earlier ones
+            const uint32_t gl = st.gm;
+            if (gl > 0) mbar_wait_bounded(&st.empty[(gl - 1) % C::ring], ((gl - 1) / C::ring) & 1, kWaitS);
         }
     } else {   // warps 2..17: drain the group accumulators, write the tile
         const int q4 = warp & 3, part = (warp - 2) >> 2;   // TMEM lane quarter, share of the orbitals
@@ -748,20 +758,24 @@ constexpr int kFFNcMax = 169;
 // one level: block (target, 128 pairs, chunk of LMC output components).
 // MODE 0: M2M, the target gathers its children (Eq. fmm1); MODE 3: M2L over
 // the interaction list, then the parent's finished local expansion (L2L).
-template <int LMC, int MODE>
+template <int LMC, int MODE, int PPT>
 __global__ void __launch_bounds__(128)
 k_translate_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr, const int* __restrict__ list,
                const int* __restrict__ opidx, const int* __restrict__ lmax_e, const int* __restrict__ parent,
                const int* __restrict__ l2l_opidx, const float2* __restrict__ ops, const float2* in, float2* out) {
     __shared__ float2 sop[kFFNcMax][LMC];   // [input component][output component of the chunk]
     const int tgt = tgt0 + blockIdx.x;
-    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    const int pb = blockIdx.y * blockDim.x * PPT + threadIdx.x;   // pairs pb + k * blockDim.x
     const int c0 = blockIdx.z * LMC;
     const int ncl = min(LMC, nc - c0);
-    const bool live = p < P;
-    float ah[LMC], al[LMC];
+    bool live[PPT];
 #pragma unroll
-    for (int q = 0; q < LMC; ++q) ah[q] = al[q] = 0.f;
+    for (int k = 0; k < PPT; ++k) live[k] = pb + k * (int)blockDim.x < P;
+    float ah[PPT][LMC], al[PPT][LMC];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+#pragma unroll
+        for (int q = 0; q < LMC; ++q) ah[k][q] = al[k][q] = 0.f;
     const int e0 = ptr[tgt], e1 = ptr[tgt + 1];
     const int eend = e1 + ((MODE == 3 && parent[tgt] >= first_box) ? 1 : 0);   // then the parent's expansion
     int llo = 0;
@@ -793,36 +807,51 @@ k_translate_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restr
             sop[c][q] = (q < ncl && c0 + q < ncr) ? Tm[(size_t)(c0 + q) * nc + c] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const float2* xs = (l2l ? out : in) + (size_t)(src - first_box) * nc * P + p;
+        const float2* xs = (l2l ? out : in) + (size_t)(src - first_box) * nc * P + pb;
         for (int cb = cb0; cb < cb1; cb += 4) {
-            float2 v[4];
+            float2 v[4][PPT];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = (cb + u < cb1 && live) ? xs[(size_t)(cb + u) * P] : make_float2(0.f, 0.f);
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    v[u][k] = (cb + u < cb1 && live[k]) ? xs[(size_t)(cb + u) * P + k * blockDim.x]
+                                                        : make_float2(0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (cb + u >= cb1) break;      // uniform across the block
 #pragma unroll
-                for (int q = 0; q < LMC; ++q) ff_fma(ah[q], al[q], sop[cb + u][q], v[u]);
+                for (int q = 0; q < LMC; ++q) {
+                    const float2 w = sop[cb + u][q];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) ff_fma(ah[k][q], al[k][q], w, v[u][k]);
+                }
             }
         }
     }
-    if (!live) return;
-    float2* o = out + ((size_t)(tgt - first_box) * nc + c0) * P + p;
+    float2* o = out + ((size_t)(tgt - first_box) * nc + c0) * P + pb;
 #pragma unroll
-    for (int q = 0; q < LMC; ++q)
-        if (q < ncl) {
-            const float h = __fadd_rn(ah[q], al[q]);       // renormalise (Fast2Sum)
-            o[(size_t)q * P] = make_float2(h, __fsub_rn(al[q], __fsub_rn(h, ah[q])));
-        }
+    for (int k = 0; k < PPT; ++k) {
+        if (!live[k]) continue;
+#pragma unroll
+        for (int q = 0; q < LMC; ++q)
+            if (q < ncl) {
+                const float h = __fadd_rn(ah[k][q], al[k][q]);       // renormalise (Fast2Sum)
+                o[(size_t)q * P + k * blockDim.x] = make_float2(h, __fsub_rn(al[k][q], __fsub_rn(h, ah[k][q])));
+            }
+    }
 }
+
+// pairs per thread: two for the narrow chunks (each operator element read
+// from shared memory feeds two multiply-adds), one for the wide ones
+constexpr int ff_ppt(int lmc) { return lmc <= 9 ? 2 : 1; }
 
 template <int MODE, typename... Args>
 void launch_translate_ff(int lmc, dim3 g, cudaStream_t s, Args... args) {
     switch (lmc) {
-        case 4: k_translate_ff<4, MODE><<<g, 128, 0, s>>>(args...); break;
-        case 9: k_translate_ff<9, MODE><<<g, 128, 0, s>>>(args...); break;
-        case 16: k_translate_ff<16, MODE><<<g, 128, 0, s>>>(args...); break;
-        default: k_translate_ff<25, MODE><<<g, 128, 0, s>>>(args...); break;
+        case 4: k_translate_ff<4, MODE, ff_ppt(4)><<<g, 128, 0, s>>>(args...); break;
+        case 9: k_translate_ff<9, MODE, ff_ppt(9)><<<g, 128, 0, s>>>(args...); break;
+        case 16: k_translate_ff<16, MODE, ff_ppt(16)><<<g, 128, 0, s>>>(args...); break;
+        default: k_translate_ff<25, MODE, ff_ppt(25)><<<g, 128, 0, s>>>(args...); break;
     }
 }
 
@@ -950,6 +979,11 @@ cudaError_t full_slices_typed(const SliceArgs& a, const T* Ct, T* Obox, cudaStre
 }  // namespace
 
 int slice_stage_k() { return kSK; }
+cudaError_t set_slice_wait_limit(long long polls) {
+    const uint32_t v = polls < 0 ? kWaitS : (uint32_t)std::min<long long>(polls, 0xffffffffLL);
+    return cudaMemcpyToSymbol(g_s_full_wait, &v, sizeof(v));
+}
+
 int slice_tile_n() { return kSN; }
 int slice_max_stages() { return kChunk * kMaxChunks; }
 size_t slice_panel_bytes(int S, bool a) { return (size_t)S * (a ? kAPart : kBPart); }
@@ -997,7 +1031,7 @@ cudaError_t m2m_ff(const FFArgs& f, cudaStream_t s) {
     for (int lev = f.D; lev >= 3; --lev) {
         const int t0 = f.level_off[lev - 1], nt = f.level_off[lev] - t0;
         if (nt <= 0) continue;
-        dim3 g(nt, (unsigned)((f.P + 127) / 128), nchunk);
+        dim3 g(nt, (unsigned)((f.P + 128 * ff_ppt(lmc) - 1) / (128 * ff_ppt(lmc))), nchunk);
         launch_translate_ff<0>(lmc, g, s, f.P, f.nc, f.L, f.first_box, t0, f.child_ptr, f.child_list, f.m2m_op,
                                (const int*)nullptr, f.parent, (const int*)nullptr, (const float2*)f.ops_ff,
                                (const float2*)ob, ob);
@@ -1018,7 +1052,7 @@ cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {
     for (int lev = 2; lev <= f.D; ++lev) {
         const int t0 = f.level_off[lev], nt = f.level_off[lev + 1] - t0;
         if (nt <= 0) continue;
-        dim3 g(nt, (unsigned)((f.P + 127) / 128), nchunk);
+        dim3 g(nt, (unsigned)((f.P + 128 * ff_ppt(lmc) - 1) / (128 * ff_ppt(lmc))), nchunk);
         launch_translate_ff<3>(lmc, g, s, f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op, f.lmax_e,
                                f.parent, f.l2l_op, (const float2*)f.ops_ff, reinterpret_cast<const float2*>(f.Ob),
                                reinterpret_cast<float2*>(f.Mb));

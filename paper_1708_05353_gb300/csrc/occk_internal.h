@@ -398,6 +398,7 @@ cudaError_t half_ff(const HalfFFArgs& h, cudaStream_t s);
 // Polls allowed to the MMA thread's operand wait in the panel GEMMs of steps
 // (a) and (e) on the current device (< 0 restores the default 2^22).
 cudaError_t set_mma_wait_limit(long long polls);
+cudaError_t set_slice_wait_limit(long long polls);   // the sliced GEMMs (kernels_f64s.cu)
 
 // ----- tensor-core translations, steps (b)-(d) (kernels_tc_translate.cu) --------
 struct TrArgs {

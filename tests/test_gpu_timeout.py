@@ -1,8 +1,8 @@
 """The failure path of the bounded device waits, made to run on purpose.
 
 Every wait of the tensor-core kernels on an mbarrier is bounded.  Here the
-MMA-issuing thread of the panel GEMMs (steps (a) and (e) of the mixed forms)
-is allowed zero polls for its operands, so its first wait gives up: the
+MMA-issuing thread of the panel GEMMs (steps (a) and (e) of the mixed forms
+and of the integer-slice forms) is allowed zero polls for its operands, so its first wait gives up: the
 kernel raises its abort flag, waits with the normal limit for the bulk copies
 and MMAs it has in flight, frees its TMEM and returns, and the host reads the
 device error word.  Nothing faults, traps or hangs: the wait that gives up is
@@ -50,6 +50,33 @@ def test_wait_gives_up_then_context_recovers(setup, prec):
     K1, E1 = occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
     occk.device_status(ctx)                     # clean again
     assert np.array_equal(K1.cpu().numpy(), K0) and E1 == E0
+
+
+@pytest.mark.parametrize("form", ["fp64s", "fp32s"])
+def test_slice_gemm_wait_gives_up_then_recovers(setup, form):
+    """The same failure path in the integer-slice GEMMs (steps (a) and (e) of
+    the FP64-accurate and FP32 slice forms): an abort in the middle of an
+    accumulation chunk still waits for the MMAs it issued before TMEM is
+    freed, and the context gives the clean result afterwards."""
+    occk, ctx, tree, s, C = setup
+    prec = "fp64" if form == "fp64s" else "fp32"
+    setter = ctx.set_fp64_slices if form == "fp64s" else ctx.set_fp32_slices
+    setter(7 if form == "fp64s" else 4)
+    try:
+        K0, E0 = occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
+        K0 = K0.cpu().numpy()
+        ctx.debug_set_wait_limit(0)
+        try:
+            with pytest.raises(occk.OcckError) as e:
+                occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
+            assert e.value.code == -5, str(e.value)
+        finally:
+            ctx.debug_set_wait_limit(-1)
+        K1, E1 = occk.farfield_K(ctx, tree, C, prec=prec, want_energy_host=True)
+        occk.device_status(ctx)
+        assert np.array_equal(K1.cpu().numpy(), K0) and E1 == E0
+    finally:
+        setter(0)
 
 
 def test_debug_gemm_wait_gives_up(setup):
