@@ -790,12 +790,37 @@ def main(argv=None):
         kernel_names.update({"a_half": "k_half_ff", "a_full": "k_s_gemm_a", "b_m2m": "k_translate_ff(M2M)",
                              "c_m2l": "k_translate_ff(M2L+L2L)", "e_l2p": "k_s_gemm_e"})
     achieved = fl[dom] / (stage_ms[dom] * 1e-3)
-    roof = {"bound": "alu", "kernel": kernel_names[dom], "stage": dom,
+    bound = "alu"
+    peak_source = (f"measured: independent-accumulator {peak_prec.upper()} FMA probe "
+                   f"(occk_probe_fma_peak) on this GPU in this run, {probe / 1e12:.3f} TFLOP/s; nominal "
+                   f"{sm_count} SMs at the median {sm_mhz:.0f} MHz: {nominal / 1e12:.3f} TFLOP/s")
+    if args.fp64_slices and args.prec == "fp64":
+        if dom in ("a_full", "e_l2p"):
+            # slice GEMM: S (S + 1) / 2 FP16 products per FP64 product, against
+            # the dense 16-bit tensor rate measured with cuBLAS on this machine
+            npr = args.fp64_slices * (args.fp64_slices + 1) // 2
+            bf = None
+            try:
+                bf = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops")
+            except Exception:
+                pass
+            bf = (bf or 1900.0) * 1e12
+            bound, achieved, probe, nominal = "tensor", achieved * npr, bf, 2.25e15
+            peak_source = (f"measured cuBLAS dense BF16 rate of this pool (FP16 runs at the same rate), "
+                           f"{bf / 1e12:.0f} TFLOP/s; achieved counts the {npr} slice products of each "
+                           f"FP64 multiply-add")
+        elif dom in ("a_half", "b_m2m", "c_m2l"):
+            # double-FP32 pass: 12 FP32 operations per FP64-equivalent
+            # multiply-add (error-free product 4, TwoSum 6, error folding 2)
+            p32 = ctx.probe_fma_peak("fp32")
+            probe, nominal = p32 / 12.0, sm_count * 128 * 2 * 2.07e9 * sm_mhz / 2070.0 / 12.0
+            peak_source = (f"measured FP32 FMA probe (occk_probe_fma_peak) in this run, {p32 / 1e12:.2f} "
+                           f"TFLOP/s, / 12 FP32 operations per double-FP32 multiply-add = "
+                           f"{probe / 1e12:.3f} TFLOP/s of FP64-equivalent work")
+    roof = {"bound": bound, "kernel": kernel_names[dom], "stage": dom,
             "achieved": achieved / 1e12, "peak": probe / 1e12, "unit": "TFLOP/s",
             "frac": achieved / probe, "traffic": traffic_for(kernel_names[dom]),
-            "peak_source": (f"measured: independent-accumulator {peak_prec.upper()} FMA probe "
-                            f"(occk_probe_fma_peak) on this GPU in this run, {probe / 1e12:.3f} TFLOP/s; nominal "
-                            f"{sm_count} SMs at the median {sm_mhz:.0f} MHz: {nominal / 1e12:.3f} TFLOP/s"),
+            "peak_source": peak_source,
             "frac_of_nominal": achieved / nominal,
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_tflops": {k: round(fl[k] / max(stage_ms[k], 1e-9) / 1e9, 4) for k in fl}}
