@@ -497,6 +497,20 @@ occk_status occk_set_fp64_slices(occk_ctx* ctx, int slices);
  * No paper counterpart: an implementation choice of this library. */
 occk_status occk_set_fp32_slices(occk_ctx* ctx, int slices);
 
+/* M2L (Eqs. fmmex, fmm2) of the occk_set_fp64_slices form from integer
+ * slices on the tensor core as well (on = 1, the default), for expansions of
+ * at least 25 components (L >= 4; below that the double-FP32 pass is used):
+ * per level, the sources' expansions and the operators are split into the
+ * same number of 7-bit slices after exact power-of-two scalings (per
+ * component and pair for the expansions, per output component for the
+ * operators), the slice products are summed exactly and combined in FP64, and
+ * the parent's L2L is then added in double-FP32.  Learned or set per-edge
+ * ranks use the operators restricted to each edge's rank.  The workspace is
+ * the slice panels' (occk_set_slice_workspace bounds it; the pairs are taken
+ * in batches of 128-pair tiles).  on = 0 keeps the double-FP32 M2L.
+ * OCCK_ERR_ARG for other values.  No paper counterpart. */
+occk_status occk_set_fp64_slice_m2l(occk_ctx* ctx, int on);
+
 /* Largest workspace of slice panels of the forms above, in bytes (0, the
  * default: 32 GB).  The leaves are processed in batches whose panels fit
  * (a leaf larger than the budget is a batch of its own); the result does not

@@ -117,7 +117,7 @@ extern "C" void occk_destroy(occk_ctx* c) {
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         for (occk::DevBuf* b : {&c->ct, &c->w, &c->obox, &c->mbox, &c->kb, &c->part, &c->edev,
                                 &c->scratch, &c->mlp_prm, &c->mlp_norm, &c->mlp_m, &c->mlp_v, &c->mlp_h,
-                                &c->mlp_grad, &c->mlp_ws, &c->feat, &c->pred, &c->ranks, &c->nrm, &c->gram,
+                                &c->mlp_grad, &c->mlp_ws, &c->feat, &c->pred, &c->ranks, &c->nrm, &c->gram, &c->rank_err,
                                 &c->pplan, &c->panels, &c->tpan, &c->tscale, &c->tops, &c->sob, &c->smb,
                                 &c->jbox, &c->scr_o, &c->scr_m, &c->scr_aux, &c->splan, &c->spanels}) {
             if (b->p) cudaFree(b->p);
@@ -825,6 +825,9 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
     // host plan of the sliced steps, alive until the launches below
     std::vector<long long> offA(nleaf + 1), item0(nleaf + 1), offAa(nleaf + 1), offBa(nleaf + 1);
     std::vector<int> batch_e, batch_a;
+    occk::SM2LArgs sm{};
+    std::vector<int> m_lt0(D + 2, 0), m_lnt(D + 2, 0), m_lopl0(D + 2, 0), m_lnopl(D + 2, 0), m_ltb(D + 2, 1);
+    std::vector<long long> m_lst0(D + 2, 0);
     if (sliced) {
         const int SK = occk::slice_stage_k(), SN = occk::slice_tile_n();
         const int jc = (nocc + SK - 1) / SK, KC = nc * jc, nct = (nocc + SN - 1) / SN;
@@ -875,7 +878,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         const size_t o_ff = o_eW + al16(4 * (size_t)nleaf * nc * nocc);
         const size_t o_vff = o_ff + al16(8 * nops * nc * nc);
         const size_t o_cff = o_vff + al16(8 * (size_t)t->nvals * nc);
-        const size_t plan_bytes = o_cff + al16(8 * (size_t)t->nao * nocc);
+        size_t plan_bytes = o_cff + al16(8 * (size_t)t->nao * nocc);
         // leaf batches whose panels fit a workspace of at most 32 GB (one
         // batch for the protein-sized cluster at L = 2; several at high rank)
         const size_t pa = occk::slice_panel_bytes(nslices, true);
@@ -901,6 +904,82 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         };
         cut(batch_e, e_bytes);
         cut(batch_a, a_bytes);
+        // M2L of the FP64-accurate form from slices as well, from 25
+        // components on (below that the 32-wide tiles are mostly padding):
+        // per level the distinct operators, each edge's operator within them,
+        // and room for every (target, output chunk)'s stage list
+        const int nq = (nc + SN - 1) / SN, ncs = (nc + SK - 1) / SK;
+        const int nvar = lmax_policy != 0 ? L + 1 : 1;
+        const int ntile = (int)((P + 127) / 128);
+        const size_t nm2l = t->m2l_tgt.size();
+        bool use_m2l = prec == OCCK_FP64 && ctx->slice_m2l != 0 && nc >= 25 && D >= 2 && nm2l > 0;
+        std::vector<int> m_bop(nm2l, 0), m_opl, opmap(t->ops.size(), -1);
+        std::vector<long long> m_sto;
+        size_t max_opl = 0, max_st = 0, max_tq = 0, max_nb = 0;
+        for (int lev = 2; use_m2l && lev <= D; ++lev) {
+            const int t0 = t->level_off[lev], nt = t->level_off[lev + 1] - t0;
+            m_lt0[lev] = t0;
+            m_lnt[lev] = nt;
+            m_lopl0[lev] = (int)m_opl.size();
+            m_lst0[lev] = (long long)m_sto.size();
+            long long st = 0;
+            for (int tl = 0; tl < nt; ++tl) {
+                const int ne = t->m2l_ptr[t0 + tl + 1] - t->m2l_ptr[t0 + tl];
+                if ((long long)ne * ncs > occk::slice_max_stages()) use_m2l = false;   // exact int32 sums
+                for (int qc = 0; qc < nq; ++qc) {
+                    m_sto.push_back(st);
+                    st += (long long)ne * ncs;
+                }
+                for (int e2 = t->m2l_ptr[t0 + tl]; e2 < t->m2l_ptr[t0 + tl + 1]; ++e2) {
+                    const int op = t->m2l_op[e2];
+                    if (opmap[op] < 0) {
+                        opmap[op] = (int)m_opl.size() - m_lopl0[lev];
+                        m_opl.push_back(op);
+                    }
+                    m_bop[e2] = opmap[op];
+                }
+            }
+            m_lnopl[lev] = (int)m_opl.size() - m_lopl0[lev];
+            for (int k = m_lopl0[lev]; k < (int)m_opl.size(); ++k) opmap[m_opl[k]] = -1;
+            max_opl = std::max(max_opl, (size_t)m_lnopl[lev]);
+            max_st = std::max(max_st, (size_t)st);
+            max_tq = std::max(max_tq, (size_t)nt * nq);
+            max_nb = std::max(max_nb, (size_t)nt);
+        }
+        size_t o_bop = plan_bytes, o_opl = o_bop, o_sto = o_bop;
+        if (use_m2l) {
+            o_opl = o_bop + al16(4 * nm2l);
+            o_sto = o_opl + al16(4 * m_opl.size());
+            plan_bytes = o_sto + al16(8 * m_sto.size());
+            // workspace: operator panels, stage lists, exponents, then the
+            // expansions' panels of as many pair tiles as the budget allows
+            auto al1k = [](size_t x) { return (x + 1023) / 1024 * 1024; };
+            const size_t w_b = al1k(pbb * max_opl * nvar * nq * ncs);
+            const size_t w_st = al1k(8 * max_st), w_nk = al1k(4 * max_tq), w_ex = al1k(8 * (size_t)nc);
+            const size_t w_gp = al1k(4 * P);
+            const size_t fixed = w_b + w_st + w_nk + w_ex + w_gp;
+            size_t wa = 0;
+            for (int lev = 2; lev <= D; ++lev) {
+                const size_t per_tile = pa * (size_t)m_lnt[lev] * ncs;
+                const size_t room = budget > fixed + per_tile ? budget - fixed : per_tile;
+                m_ltb[lev] = (int)std::max<size_t>(1, std::min<size_t>(ntile, room / std::max<size_t>(per_tile, 1)));
+                wa = std::max(wa, per_tile * m_ltb[lev]);
+            }
+            need_bytes = std::max(need_bytes, fixed + wa);
+            sm.S = nslices; sm.nq = nq; sm.ncs = ncs; sm.nvar = nvar; sm.ntile = ntile;
+            sm.lt0 = m_lt0.data(); sm.lnt = m_lnt.data(); sm.lopl0 = m_lopl0.data(); sm.lnopl = m_lnopl.data();
+            sm.lst0 = m_lst0.data(); sm.ltb = m_ltb.data();
+            // device pointers are set once both buffers exist (below)
+            sm.capB = (long long)(max_opl * nvar * nq * ncs);
+            sm.capA = (long long)(wa / pa);
+            sm.panB = nullptr;
+            sm.stab = reinterpret_cast<int2*>(w_b);                  // offsets for now
+            sm.nk = reinterpret_cast<int*>(w_b + w_st);
+            sm.ec = reinterpret_cast<int*>(w_b + w_st + w_nk);
+            sm.fq = reinterpret_cast<int*>(w_b + w_st + w_nk + 4 * (size_t)nc);
+            sm.gp = reinterpret_cast<int*>(w_b + w_st + w_nk + w_ex);
+            sm.panA = reinterpret_cast<uint8_t*>(fixed);
+        }
         if ((e = ensure(ctx->splan, plan_bytes)) != cudaSuccess ||
             (e = ensure(ctx->spanels, need_bytes)) != cudaSuccess)
             return e == cudaErrorMemoryAllocation ? fail(ctx, OCCK_ERR_OOM, "slice panels of steps (a) and (e)")
@@ -916,6 +995,24 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         if ((e = cudaMemcpy(ctx->splan.p, hp.data(), o_eC, cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(ctx, e, "slice plan upload");
         char* x = (char*)ctx->splan.p;
+        if (use_m2l) {
+            if ((e = cudaMemcpy(x + o_bop, m_bop.data(), 4 * nm2l, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(x + o_opl, m_opl.data(), 4 * m_opl.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(x + o_sto, m_sto.data(), 8 * m_sto.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(ctx, e, "slice plan upload (M2L)");
+            char* w0 = (char*)ctx->spanels.p;
+            sm.edge_bop = (const int*)(x + o_bop);
+            sm.oplist = (const int*)(x + o_opl);
+            sm.stoff = (const long long*)(x + o_sto);
+            sm.panB = (uint8_t*)w0;
+            sm.stab = (int2*)(w0 + (size_t)sm.stab);
+            sm.nk = (int*)(w0 + (size_t)sm.nk);
+            sm.ec = (int*)(w0 + (size_t)sm.ec);
+            sm.fq = (int*)(w0 + (size_t)sm.fq);
+            sm.gp = (int*)(w0 + (size_t)sm.gp);
+            sm.panA = (uint8_t*)(w0 + (size_t)sm.panA);
+            sa.m2l = &sm;
+        }
         // step (a) from slices while a leaf's K range fits the exact int32
         // group sums (about 4000 AO rows); the DFMA kernel otherwise
         sa.full = max_kca <= occk::slice_max_stages() ? 1 : 0;
@@ -1007,7 +1104,8 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         if ((e = ensure(ctx->feat, sizeof(float) * (size_t)nm2l * OCCK_MLP_NIN)) != cudaSuccess ||
             (e = ensure(ctx->pred, sizeof(float) * (size_t)nm2l * OCCK_MLP_NOUT)) != cudaSuccess ||
             (e = ensure(ctx->ranks, sizeof(int) * (size_t)nm2l)) != cudaSuccess ||
-            (e = ensure(ctx->nrm, sizeof(double) * (size_t)nbox * (L + 1))) != cudaSuccess)
+            (e = ensure(ctx->nrm, sizeof(double) * (size_t)nbox * (L + 1))) != cudaSuccess ||
+            (e = ensure(ctx->rank_err, sizeof(double) * (size_t)nm2l * (L + 1))) != cudaSuccess)
             return cuda_fail(ctx, e, "selector workspace");
         a.learned = 1;
         a.mlp_prm = (const float*)ctx->mlp_prm.p;
@@ -1017,6 +1115,7 @@ extern "C" occk_status occk_farfield_K(occk_ctx* ctx, const occk_tree* tc, int n
         a.pred = (float*)ctx->pred.p;
         a.ranks = (int*)ctx->ranks.p;
         a.nrm = (double*)ctx->nrm.p;
+        a.rank_err = (double*)ctx->rank_err.p;
         a.tau = ctx->tau;
         a.nm2l = nm2l;
         a.m2l_tgt = d.m2l_tgt;
@@ -1571,6 +1670,13 @@ extern "C" occk_status occk_set_fp32_slices(occk_ctx* ctx, int slices) {
             b->bytes = 0;
         }
     }
+    return OCCK_OK;
+}
+
+extern "C" occk_status occk_set_fp64_slice_m2l(occk_ctx* ctx, int on) {
+    if (!ctx) return OCCK_ERR_ARG;
+    if (on != 0 && on != 1) return fail(ctx, OCCK_ERR_ARG, "on must be 0 or 1");
+    ctx->slice_m2l = on;
     return OCCK_OK;
 }
 

@@ -420,12 +420,25 @@ __device__ __forceinline__ void s_tmem_ld8(uint32_t taddr, uint32_t* r) {
 }
 __device__ __forceinline__ void s_tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Stage kc of an item whose panels lie one after another along K
+template <int S>
+struct SContig {
+    __device__ __forceinline__ bool operator()(long long, int kc, const uint8_t* A, const uint8_t* B,
+                                               const uint8_t*& a, const uint8_t*& b) const {
+        a = A + (size_t)kc * SL<S>::a_bytes;
+        b = B + (size_t)kc * SL<S>::b_bytes;
+        return true;
+    }
+};
+
 // One CTA per SM walks items it = blockIdx.x, + gridDim.x, ...:
-// src(it, A, B, nk) gives an item's first A and B panels (consecutive along K)
-// and its number of stages; out(it, row, part, acc) receives the exact group
-// sums of one output row and kSCols columns (part) at the end of the item.
-template <int S, typename Src, typename Out>
-__device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, int* err) {
+// src(it, A, B, nk) gives an item's first A and B panels and its number of
+// stages; at(it, kc, A, B, a, b) the panels of stage kc (false: an address
+// outside the workspace, which aborts the CTA before any copy is issued);
+// out(it, row, part, acc) receives the exact group sums of one output row and
+// kSCols columns (part) at the end of the item.
+template <int S, typename Src, typename Out, typename At = SContig<S>>
+__device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, int* err, At at = At()) {
     using C = SL<S>;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ SState st;
@@ -468,9 +481,14 @@ __device__ __forceinline__ void s_gemm_body(long long nitems, Src src, Out out, 
                         st.abort = 1;
                         break;
                     }
+                    const uint8_t *a, *b;
+                    if (!at(it, kc, A, Bp, a, b)) {
+                        st.abort = 1;
+                        break;
+                    }
                     s_expect_tx(&st.full[r], (uint32_t)C::stage);
-                    s_bulk_g2s(stA(r), A + (size_t)kc * C::a_bytes, C::a_bytes, &st.full[r]);
-                    s_bulk_g2s(stB(r), Bp + (size_t)kc * C::b_bytes, C::b_bytes, &st.full[r]);
+                    s_bulk_g2s(stA(r), a, C::a_bytes, &st.full[r]);
+                    s_bulk_g2s(stB(r), b, C::b_bytes, &st.full[r]);
                     st.gp = gs + 1;
                 }
             }
@@ -757,7 +775,8 @@ constexpr int kFFNcMax = 169;
 
 // one level: block (target, 128 pairs, chunk of LMC output components).
 // MODE 0: M2M, the target gathers its children (Eq. fmm1); MODE 3: M2L over
-// the interaction list, then the parent's finished local expansion (L2L).
+// the interaction list, then the parent's finished local expansion (L2L);
+// MODE 4: the L2L alone, added to the expansion already in out.
 template <int LMC, int MODE, int PPT>
 __global__ void __launch_bounds__(128)
 k_translate_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restrict__ ptr, const int* __restrict__ list,
@@ -775,15 +794,22 @@ k_translate_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restr
 #pragma unroll
     for (int k = 0; k < PPT; ++k)
 #pragma unroll
-        for (int q = 0; q < LMC; ++q) ah[k][q] = al[k][q] = 0.f;
-    const int e0 = ptr[tgt], e1 = ptr[tgt + 1];
-    const int eend = e1 + ((MODE == 3 && parent[tgt] >= first_box) ? 1 : 0);   // then the parent's expansion
+        for (int q = 0; q < LMC; ++q) {
+            ah[k][q] = al[k][q] = 0.f;
+            if (MODE == 4 && live[k] && q < ncl) {
+                const float2 x = out[((size_t)(tgt - first_box) * nc + c0 + q) * P + pb + k * blockDim.x];
+                ah[k][q] = x.x;
+                al[k][q] = x.y;
+            }
+        }
+    const int e1 = ptr[tgt + 1], e0 = MODE == 4 ? e1 : ptr[tgt];
+    const int eend = e1 + ((MODE >= 3 && parent[tgt] >= first_box) ? 1 : 0);   // then the parent's expansion
     int llo = 0;
     while ((llo + 1) * (llo + 1) <= c0) ++llo;
     int lhi = 0;
     while ((lhi + 1) * (lhi + 1) <= c0 + ncl - 1) ++lhi;
     for (int e = e0; e < eend; ++e) {
-        const bool l2l = MODE == 3 && e == e1;
+        const bool l2l = MODE >= 3 && e == e1;
         int src, op, Le = L;
         if (MODE == 0) {
             src = list[e];
@@ -839,6 +865,207 @@ k_translate_ff(int P, int nc, int L, int first_box, int tgt0, const int* __restr
                 o[(size_t)q * P + k * blockDim.x] = make_float2(h, __fsub_rn(al[k][q], __fsub_rn(h, ah[k][q])));
             }
     }
+}
+
+// ---------------------------------------------------------------------------
+// M2L of the FP64-accurate form from integer slices on the tensor core
+// (Eqs. fmmex, fmm2), per level:  Mcal[t][q][p] = sum over the edges (t, s, op)
+// of sum_c T_op[q][c] O[s][c][p].  A GEMM with rows = pairs p (128 per tile),
+// columns = output components q (32 per chunk) and K = (edge, input component
+// c) gathered stage by stage: A panels hold the sliced expansions of every box
+// of the level for a batch of pair tiles, B panels the sliced operators.  All
+// scaling is by powers of two, exact: component c of the level's expansions is
+// scaled by 2^-ec[c] (their largest exponent), pair p then by 2^-gp[p] (the
+// largest over boxes and components), and row q of the operators by
+// 2^(ec[c] - fq[q]); the product of the two scalings is undone per (p, q) in
+// the epilogue.  The expansions arrive in double-FP32 (hi, lo) and leave in it.
+// ---------------------------------------------------------------------------
+__global__ void k_m2l_init_exp(int* __restrict__ ec, int* __restrict__ fq, int nc) {
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) ec[c] = fq[c] = -2000;
+}
+
+// ec[c] = largest exponent of component c over the level's boxes and pairs:
+// block (box, component), threads over the pairs
+__global__ void k_m2l_ecomp(const float2* __restrict__ O, int b0s, int nc, size_t P, int* __restrict__ ec) {
+    const int b = blockIdx.x / nc, c = blockIdx.x % nc;
+    const float2* x = O + ((size_t)(b0s + b) * nc + c) * P;
+    int m = -2000;
+    for (size_t p = threadIdx.x; p < P; p += blockDim.x) m = max(m, s_expo(x[p].x));
+    m = s_warp_max(m);
+    if ((threadIdx.x & 31) == 0 && m > -1000) atomicMax(&ec[c], m);
+}
+
+// gp[p] = largest exponent of pair p over the level's boxes and components,
+// relative to ec (0 for a pair that is zero everywhere)
+__global__ void k_m2l_pexp(const float2* __restrict__ O, int b0s, int nb, int nc, size_t P,
+                           const int* __restrict__ ec, int* __restrict__ gp) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int m = -2000;
+    for (int b = 0; b < nb; ++b)
+        for (int c = 0; c < nc; ++c) {
+            const int e = s_expo(O[((size_t)(b0s + b) * nc + c) * P + p].x);
+            if (e > -1000) m = max(m, e - ec[c]);
+        }
+    gp[p] = m <= -1000 ? 0 : m;
+}
+
+// fq[q] = largest exponent of row q of the level's operators scaled by 2^ec[c]
+__global__ void k_m2l_fq(const double* __restrict__ ops, const int* __restrict__ oplist, int nc,
+                         const int* __restrict__ ec, int* __restrict__ fq) {
+    const double* T = ops + (size_t)oplist[blockIdx.x] * nc * nc;
+    for (int x = threadIdx.x; x < nc * nc; x += blockDim.x) {
+        const int q = x / nc, c = x - q * nc;
+        const int e = s_expo(T[x]);
+        if (e > -1000 && ec[c] > -1000) atomicMax(&fq[q], e + ec[c]);
+    }
+}
+
+// B panels: block (K stage cs, output chunk qc, local operator x rank
+// variant), thread = output component of the chunk.  Variant v of a learned
+// rank selection is the operator restricted to l, l' <= v.
+template <int S>
+__global__ void __launch_bounds__(32)
+k_m2l_panel_B(const double* __restrict__ ops, const int* __restrict__ oplist, int nvar, int L, int nc, int nq,
+              int ncs, const int* __restrict__ ec, const int* __restrict__ fq, uint8_t* __restrict__ pan) {
+    const int cs = blockIdx.x, qc = blockIdx.y, lop = blockIdx.z / nvar, v = blockIdx.z % nvar;
+    const int n = threadIdx.x, q = qc * kSN + n;
+    const int Lv = nvar > 1 ? v : L, ncv = min(nc, (Lv + 1) * (Lv + 1));
+    const double* T = ops + (size_t)oplist[lop] * nc * nc;
+    const int f = q < nc && fq[q] > -1000 ? fq[q] : 0;
+    uint8_t* panel = pan + (size_t)((((long long)blockIdx.z * nq + qc) * ncs) + cs) * SL<S>::b_bytes;
+#pragma unroll
+    for (int k8 = 0; k8 < kSK; k8 += 8) {
+        long long x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = cs * kSK + k8 + u;
+            x[u] = (q < ncv && c < ncv && ec[c] > -1000) ? s_fixed(T[(size_t)q * nc + c], 55 + ec[c] - f) : 0;
+        }
+        s_put8<S>(panel + s_off(n, k8), kBPart, x);
+    }
+}
+
+// Stage list of every (target, output chunk) of the level: thread per pair
+// (local target, chunk); entry k = (A panel of the source and K stage, B panel
+// of the operator variant, chunk and K stage).  Chunks beyond an edge's rank
+// take nothing from it.
+__global__ void k_m2l_stages(const int* __restrict__ m2l_ptr, const int* __restrict__ m2l_src,
+                             const int* __restrict__ edge_bop, const int* __restrict__ lmax_e, int t0, int nt, int L,
+                             int nq, int ncs, int nvar, int sb0, const long long* __restrict__ stoff,
+                             int2* __restrict__ stab, int* __restrict__ nk) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nt * nq) return;
+    const int tl = x / nq, qc = x - tl * nq, t = t0 + tl;
+    int2* o = stab + stoff[x];
+    int k = 0;
+    for (int e = m2l_ptr[t]; e < m2l_ptr[t + 1]; ++e) {
+        const int Le = lmax_e ? lmax_e[e] : L, nce = (Le + 1) * (Le + 1);
+        if (qc * kSN >= nce) continue;
+        const int ncse = min(ncs, (nce + kSK - 1) / kSK);
+        const int a0 = (m2l_src[e] - sb0) * ncs, b0 = ((edge_bop[e] * nvar + (nvar > 1 ? Le : 0)) * nq + qc) * ncs;
+        for (int cs = 0; cs < ncse; ++cs) o[k++] = make_int2(a0 + cs, b0 + cs);
+    }
+    nk[x] = k;
+}
+
+// A panels of a batch of pair tiles: block (K stage cs, tile of the batch, box
+// of the level), thread = pair row
+template <int S>
+__global__ void __launch_bounds__(128)
+k_m2l_panel_A(const float2* __restrict__ O, int b0s, int nb, int nc, size_t P, int ncs, int T0,
+              const int* __restrict__ ec, const int* __restrict__ gp, uint8_t* __restrict__ pan) {
+    const int cs = blockIdx.x, tl = blockIdx.y, b = blockIdx.z;
+    const size_t p = (size_t)(T0 + tl) * 128 + threadIdx.x;
+    const bool live = p < P;
+    const int g = live ? gp[p] : 0;
+    const float2* x = O + (size_t)(b0s + b) * nc * P + (live ? p : 0);
+    uint8_t* panel = pan + (size_t)(((long long)tl * nb + b) * ncs + cs) * SL<S>::a_bytes;
+#pragma unroll
+    for (int k8 = 0; k8 < kSK; k8 += 8) {
+        long long v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = cs * kSK + k8 + u;
+            long long r = 0;
+            if (live && c < nc && ec[c] > -1000) {
+                const float2 h = x[(size_t)c * P];
+                r = s_fixed((double)h.x + (double)h.y, 55 - ec[c] - g);   // hi + lo, rounded once
+            }
+            v[u] = r;
+        }
+        s_put8<S>(panel + s_off(threadIdx.x, k8), kAPart, v);
+    }
+}
+
+struct SGemmM {
+    const int2* stab; const long long* stoff; const int* nk;
+    const uint8_t* panA; const uint8_t* panB;
+    long long capA, capB;                  // panels in the workspace (bounds of the stage entries)
+    const int* gp; const int* fq;
+    float2* Mb;                            // local expansions, (hi, lo)
+    size_t P;
+    int nc, nq, ncs, nb, nt, t0, first_box, T0, tb, qc_outer;
+    long long nitems;
+    int* err;
+};
+
+// items: tile of the batch outermost, so that the CTAs in flight share the
+// tile's A panels in L2; then (target, output chunk) with the chunk
+// innermost, or with per-edge ranks (ten times the operator panels) the chunk
+// outermost, so that one chunk's B panels stay in L2 too (measured best
+// each way); x = target * nq + chunk indexes the stage lists
+template <int S>
+__global__ void __launch_bounds__(kSThreads, 1)
+k_s_gemm_m2l(SGemmM g) {
+    using C = SL<S>;
+    const long long per_tile = (long long)g.nt * g.nq;
+    auto sub = [&](long long it, long long& tl) {
+        tl = it / per_tile;
+        const int r = (int)(it - tl * per_tile);
+        if (!g.qc_outer) return r;
+        const int qc = r / g.nt;
+        return (r - qc * g.nt) * g.nq + qc;
+    };
+    auto src = [&](long long it, const uint8_t*& A, const uint8_t*& Bp, int& nk) {
+        long long tl;
+        const int x = sub(it, tl);
+        A = g.panA;
+        Bp = g.panB;
+        nk = g.nk[x];
+    };
+    auto at = [&](long long it, int kc, const uint8_t*, const uint8_t*, const uint8_t*& a, const uint8_t*& b) {
+        long long tl;
+        const int x = sub(it, tl);
+        const int2 en = g.stab[g.stoff[x] + kc];
+        const long long ai = tl * g.nb * g.ncs + en.x, bi = en.y;
+        if (en.x < 0 || en.y < 0 || ai >= g.capA || bi >= g.capB) return false;
+        a = g.panA + (size_t)ai * C::a_bytes;
+        b = g.panB + (size_t)bi * C::b_bytes;
+        return true;
+    };
+    auto out = [&](long long it, int row, int part, const int (&acc)[S][kSCols]) {
+        long long tl;
+        const int x = sub(it, tl);
+        const int t = g.t0 + x / g.nq, qc = x % g.nq;
+        const size_t p = (size_t)(g.T0 + tl) * 128 + row;
+        if (p >= g.P) return;
+        double v[kSCols];
+        s_combine<S>(acc, v);
+        const int e = g.gp[p];
+        float2* o = g.Mb + (size_t)(t - g.first_box) * g.nc * g.P + p;
+#pragma unroll
+        for (int c = 0; c < kSCols; ++c) {
+            const int q = qc * kSN + part * kSCols + c;
+            if (q < g.nc) {
+                const int f = g.fq[q] > -1000 ? g.fq[q] : 0;
+                const double y = v[c] * s_pow2(e + f);
+                const float h = __double2float_rn(y);
+                o[(size_t)q * g.P] = make_float2(h, __double2float_rn(y - (double)h));
+            }
+        }
+    };
+    s_gemm_body<S>(g.nitems, src, out, g.err, at);
 }
 
 // pairs per thread: two for the narrow chunks (each operator element read
@@ -1018,6 +1245,61 @@ cudaError_t half_ff(const HalfFFArgs& h, cudaStream_t s) {
 
 static int ff_lmc(int nc) { return nc <= 4 ? 4 : nc <= 9 ? 9 : nc <= 16 ? 16 : 25; }
 
+// One level of the sliced M2L: exponents, operator panels and stage lists,
+// then per batch of pair tiles the expansions' panels and the GEMM
+template <int S>
+cudaError_t m2l_slices_level_t(const FFArgs& f, int lev, cudaStream_t s) {
+    const SM2LArgs& m = *f.sm;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_s_gemm_m2l<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SL<S>::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int t0 = m.lt0[lev], nt = m.lnt[lev], nb = nt;   // sources and targets: the level's boxes
+    const int b0s = t0 - f.first_box;
+    const size_t P = (size_t)f.P;
+    const auto* O = reinterpret_cast<const float2*>(f.Ob);
+    k_m2l_init_exp<<<1, 256, 0, s>>>(m.ec, m.fq, f.nc);
+    k_m2l_ecomp<<<nb * f.nc, 256, 0, s>>>(O, b0s, f.nc, P, m.ec);
+    k_m2l_pexp<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(O, b0s, nb, f.nc, P, m.ec, m.gp);
+    const int nopl = m.lnopl[lev];
+    const int* oplist = m.oplist + m.lopl0[lev];
+    if (nopl > 0) {
+        k_m2l_fq<<<nopl, 256, 0, s>>>(f.ops, oplist, f.nc, m.ec, m.fq);
+        k_m2l_panel_B<S><<<dim3(m.ncs, m.nq, nopl * m.nvar), 32, 0, s>>>(f.ops, oplist, m.nvar, f.L, f.nc, m.nq,
+                                                                        m.ncs, m.ec, m.fq, m.panB);
+    }
+    const long long* stoff = m.stoff + m.lst0[lev];
+    k_m2l_stages<<<(nt * m.nq + 127) / 128, 128, 0, s>>>(f.m2l_ptr, f.m2l_src, m.edge_bop, f.lmax_e, t0, nt, f.L,
+                                                         m.nq, m.ncs, m.nvar, t0, stoff, m.stab, m.nk);
+    const int tb = std::max(1, m.ltb[lev]);
+    for (int T0 = 0; T0 < m.ntile; T0 += tb) {
+        const int nbt = std::min(tb, m.ntile - T0);
+        k_m2l_panel_A<S><<<dim3(m.ncs, nbt, nb), 128, 0, s>>>(O, b0s, nb, f.nc, P, m.ncs, T0, m.ec, m.gp, m.panA);
+        SGemmM g{};
+        g.stab = m.stab; g.stoff = stoff; g.nk = m.nk;
+        g.panA = m.panA; g.panB = m.panB; g.capA = m.capA; g.capB = m.capB;
+        g.gp = m.gp; g.fq = m.fq; g.Mb = reinterpret_cast<float2*>(f.Mb); g.P = P;
+        g.nc = f.nc; g.nq = m.nq; g.ncs = m.ncs; g.nb = nb; g.nt = nt; g.t0 = t0; g.first_box = f.first_box;
+        g.T0 = T0; g.tb = nbt; g.qc_outer = m.nvar > 1 ? 1 : 0;
+        g.nitems = (long long)nbt * nt * m.nq;
+        g.err = f.err;
+        const int grid = (int)std::min<long long>(g.nitems, std::max(f.sm_count, 1));
+        k_s_gemm_m2l<S><<<grid, kSThreads, SL<S>::smem, s>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t m2l_slices_level(const FFArgs& f, int lev, cudaStream_t s) {
+    switch (f.sm->S) {
+        case 7: return m2l_slices_level_t<7>(f, lev, s);
+        case 6: return m2l_slices_level_t<6>(f, lev, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t m2m_ff(const FFArgs& f, cudaStream_t s) {
     // the leaves' multipoles (FP64 from step (a)) to (hi, lo); M2M writes
     // the parents' in (hi, lo)
@@ -1039,6 +1321,11 @@ cudaError_t m2m_ff(const FFArgs& f, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t ff_join(const FFArgs& f, cudaStream_t s) {
+    k_ff_join<<<4 * std::max(f.sm_count, 1), 256, 0, s>>>(f.Ob, (size_t)f.nstore * f.nc * f.P);
+    return cudaGetLastError();
+}
+
 cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {
     const size_t n = (size_t)f.nstore * f.nc * f.P;
     const int blocks = 4 * std::max(f.sm_count, 1);
@@ -1053,6 +1340,17 @@ cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s) {
         const int t0 = f.level_off[lev], nt = f.level_off[lev + 1] - t0;
         if (nt <= 0) continue;
         dim3 g(nt, (unsigned)((f.P + 128 * ff_ppt(lmc) - 1) / (128 * ff_ppt(lmc))), nchunk);
+        if (f.sm) {
+            // M2L from slices on the tensor core, then the parent's L2L added
+            // in double-FP32
+            cudaError_t e = m2l_slices_level(f, lev, s);
+            if (e != cudaSuccess) return e;
+            if (lev >= 3)
+                launch_translate_ff<4>(lmc, g, s, f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op,
+                                       f.lmax_e, f.parent, f.l2l_op, (const float2*)f.ops_ff,
+                                       reinterpret_cast<const float2*>(f.Ob), reinterpret_cast<float2*>(f.Mb));
+            continue;
+        }
         launch_translate_ff<3>(lmc, g, s, f.P, f.nc, f.L, f.first_box, t0, f.m2l_ptr, f.m2l_src, f.m2l_op, f.lmax_e,
                                f.parent, f.l2l_op, (const float2*)f.ops_ff, reinterpret_cast<const float2*>(f.Ob),
                                reinterpret_cast<float2*>(f.Mb));

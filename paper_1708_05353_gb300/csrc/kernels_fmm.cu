@@ -829,8 +829,9 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
         }
         if (e2 != cudaSuccess) return e2;
     }
-    // the sliced FP64 form: M2M in double-FP32 arithmetic (not with the
-    // learned selector, whose features read the FP64 multipoles of every box)
+    // the sliced FP64 form: M2M in double-FP32 arithmetic; for the learned
+    // selector, whose features read the FP64 multipoles of every box, they
+    // are joined back to FP64 after it (and split again for M2L)
     FFArgs ffa{};
     bool m2m_ff_done = false;
     if constexpr (sizeof(T) == 8) {
@@ -843,12 +844,13 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
             ffa.child_ptr = a.child_ptr; ffa.child_list = a.child_list; ffa.m2m_op = a.m2m_op;
             ffa.ops = (const double*)tops; ffa.ops_ff = a.slices->ops_ff;
             ffa.Ob = (double*)Ob; ffa.Mb = (double*)Mb;
-            if (!a.learned) {
-                cudaError_t e2 = m2m_ff(ffa, s);
-                if (e2 != cudaSuccess) return e2;
-                m2m_ff_done = true;
-                ffa.m2m_done = 1;
-            }
+            ffa.sm = a.slices->m2l;
+            ffa.err = a.slices->err;
+            cudaError_t e2 = m2m_ff(ffa, s);
+            if (e2 == cudaSuccess && a.learned) e2 = ff_join(ffa, s);
+            if (e2 != cudaSuccess) return e2;
+            m2m_ff_done = true;
+            ffa.m2m_done = a.learned ? 0 : 1;
         }
     }
     for (int lev = D; lev >= 3 && !slots && !m2m_ff_done; --lev) {
@@ -872,7 +874,7 @@ cudaError_t run_typed(const FmmArgs& a, cudaStream_t s) {
                                        a.m2l_src, a.box_key, a.box_level, a.hlev, D, a.nrm, a.feat, s);
         if (e2 == cudaSuccess)
             e2 = mlp_predict_fp16(a.mlp_prm, (__half*)a.mlp_h, a.mlp_norm, a.feat, a.nm2l, a.pred, s);
-        if (e2 == cudaSuccess) e2 = select_ranks(a.pred, a.nm2l, a.L, a.tau, a.ranks, s);
+        if (e2 == cudaSuccess) e2 = select_ranks(a.pred, a.nm2l, a.L, a.tau, a.ranks, a.rank_err, s);
         if (e2 != cudaSuccess) return e2;
         lmax_e = a.ranks;
     }

@@ -352,24 +352,25 @@ __global__ void k_edge_energy(const double* __restrict__ G, const double* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Rank selection by bisection on the Lagrange multiplier (one block).
+// Rank selection by bisection on the Lagrange multiplier (one block): each
+// edge takes the rank L in 2..Lmax that minimises (L+1)^4 + 10^loglam err_L.
 // pred[e][k] = log10 err at rank 2+k (k < NOUT); rank Lmax has error 0 when
 // Lmax == 2 + NOUT, else its predicted value.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int choose_rank(const float* pe, int Lmax, double loglam, double* err_out) {
+// The choice for one edge from tabulated values: er[L] = 10^(predicted log10
+// error) of rank L (-1 for a prediction that is not finite, which keeps rank
+// Lmax), cost[L] = (L+1)^4 and lam = 10^loglam, each computed once.
+__device__ __forceinline__ int choose_rank_tab(const double* er, const double* cost, int Lmax, double lam,
+                                               double* err_out) {
     int best = Lmax;
     double bestv = 1e300, besterr = 0.0;
     for (int L = 2; L <= Lmax; ++L) {
-        double err;
-        if (L - 2 < NOUT) {
-            const float y = pe[L - 2];
-            if (!isfinite(y)) return Lmax;
-            err = pow(10.0, (double)y);
-        } else {
-            err = 0.0;
+        const double err = er[L];
+        if (err < 0.0) {
+            if (err_out) *err_out = 0.0;
+            return Lmax;
         }
-        const double cost = pow((double)(L + 1), 4.0);
-        const double v = cost + pow(10.0, loglam) * err;
+        const double v = cost[L] + lam * err;
         if (v < bestv) {
             bestv = v;
             best = L;
@@ -380,9 +381,27 @@ __device__ __forceinline__ int choose_rank(const float* pe, int Lmax, double log
     return best;
 }
 
-__global__ void k_select(const float* __restrict__ pred, int nedge, int Lmax, double tau, int* __restrict__ ranks) {
+// er[e][L] for every edge, once, on the whole GPU (the bisection below reads
+// them 61 times)
+__global__ void k_rank_err(const float* __restrict__ pred, int nedge, int Lmax, double* __restrict__ er) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nedge) return;
+    double* o = er + (size_t)e * (Lmax + 1);
+    for (int L = 2; L <= Lmax; ++L) {
+        double v = 0.0;
+        if (L - 2 < NOUT) {
+            const float y = pred[(size_t)e * NOUT + L - 2];
+            v = isfinite(y) ? pow(10.0, (double)y) : -1.0;
+        }
+        o[L] = v;
+    }
+}
+
+__global__ void k_select(const double* __restrict__ er, int nedge, int Lmax, double tau, int* __restrict__ ranks) {
     __shared__ double red[1024];
-    __shared__ double lo, hi;
+    __shared__ double lo, hi, lam;
+    __shared__ double cost[64];
+    if (threadIdx.x <= Lmax && threadIdx.x < 64) cost[threadIdx.x] = pow((double)(threadIdx.x + 1), 4.0);
     if (threadIdx.x == 0) {
         lo = -10.0;
         hi = 60.0;
@@ -390,10 +409,12 @@ __global__ void k_select(const float* __restrict__ pred, int nedge, int Lmax, do
     __syncthreads();
     for (int it = 0; it < 60; ++it) {
         const double mid = 0.5 * (lo + hi);
+        if (threadIdx.x == 0) lam = pow(10.0, mid);
+        __syncthreads();
         double s = 0.0;
         for (int e = threadIdx.x; e < nedge; e += blockDim.x) {
             double err;
-            choose_rank(pred + (size_t)e * NOUT, Lmax, mid, &err);
+            choose_rank_tab(er + (size_t)e * (Lmax + 1), cost, Lmax, lam, &err);
             s += err;
         }
         red[threadIdx.x] = s;
@@ -410,8 +431,10 @@ __global__ void k_select(const float* __restrict__ pred, int nedge, int Lmax, do
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) lam = pow(10.0, hi);
+    __syncthreads();
     for (int e = threadIdx.x; e < nedge; e += blockDim.x)
-        ranks[e] = choose_rank(pred + (size_t)e * NOUT, Lmax, hi, nullptr);
+        ranks[e] = choose_rank_tab(er + (size_t)e * (Lmax + 1), cost, Lmax, lam, nullptr);
 }
 
 }  // namespace
@@ -478,9 +501,12 @@ cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L
     return cudaGetLastError();
 }
 
-cudaError_t select_ranks(const float* pred, int nedge, int Lmax, double tau, int* ranks, cudaStream_t s) {
+cudaError_t select_ranks(const float* pred, int nedge, int Lmax, double tau, int* ranks, double* er,
+                         cudaStream_t s) {
     if (nedge == 0) return cudaSuccess;
-    k_select<<<1, 1024, 0, s>>>(pred, nedge, Lmax, tau, ranks);
+    if (Lmax >= 64) return cudaErrorInvalidValue;
+    k_rank_err<<<(nedge + 255) / 256, 256, 0, s>>>(pred, nedge, Lmax, er);
+    k_select<<<1, 1024, 0, s>>>(er, nedge, Lmax, tau, ranks);
     return cudaGetLastError();
 }
 

@@ -138,7 +138,7 @@ struct occk_ctx {
     // learned rank selector
     int mlp_ready = 0, mlp_t = 0;
     double tau = 1e-6;
-    occk::DevBuf mlp_prm, mlp_norm, mlp_m, mlp_v, mlp_h, mlp_grad, mlp_ws, feat, pred, ranks, nrm, gram;
+    occk::DevBuf mlp_prm, mlp_norm, mlp_m, mlp_v, mlp_h, mlp_grad, mlp_ws, feat, pred, ranks, nrm, gram, rank_err;
     int ranks_valid = 0;
     // panel plan cache (tensor-core steps a and e)
     occk::DevBuf pplan, panels;
@@ -169,6 +169,7 @@ struct occk_ctx {
     int f32_slices = 0;                     // FP32 steps (a), (e) from 4 integer slices (0: SIMT FFMA)
     int last_sliced = 0;                    // the last occk_farfield_K ran steps (a), (e) from slices
     size_t slice_budget = 0;                // largest slice-panel workspace (0: 32 GB)
+    int slice_m2l = 1;                      // FP64-accurate form: M2L from slices too (from 25 components)
     occk::DevBuf splan, spanels;            // its plan (row tiles, panel and item offsets, exponents), panels
     // stage timers
     int timing = 0;
@@ -230,7 +231,7 @@ struct FmmArgs {
     // learned selector (lmax_policy 2); learned == 0 when unused
     int learned;
     const float* mlp_prm; void* mlp_h; const float* mlp_norm;
-    float* feat; float* pred; int* ranks; double* nrm; double tau; int nm2l;
+    float* feat; float* pred; int* ranks; double* nrm; double* rank_err; double tau; int nm2l;
     const int* m2l_tgt; const int* box_key; const int* box_level; const double* hlev;
     // occupied-pair screening (screen != 0, FP64 and FP32): pairs with
     // n^2 < screen_tau2 are dropped before M2M; the tree passes run on the
@@ -312,7 +313,8 @@ cudaError_t edge_energies(bool fp64, const void* O, int first_box, int nc, int L
                           int nedge,
                           const int* tgt, const int* src, const double* ops, const int* opidx, double* G,
                           double* out, cudaStream_t s);
-cudaError_t select_ranks(const float* pred, int nedge, int Lmax, double tau, int* ranks, cudaStream_t s);
+cudaError_t select_ranks(const float* pred, int nedge, int Lmax, double tau, int* ranks, double* er,
+                         cudaStream_t s);   // er: [nedge][Lmax+1] workspace
 
 // ----- panel tensor-core GEMMs (kernels_tc2.cu) -----------------------------
 struct PanelArgs {
@@ -335,12 +337,14 @@ int panel_bytes(int prec);
 cudaError_t panel_l2p(int prec, const PanelArgs& a, cudaStream_t s);
 cudaError_t panel_a2(int prec, const PanelArgs& a, cudaStream_t s);
 // ----- FP64 steps (a) and (e) from integer slices on the tensor core (kernels_f64s.cu) -----
+struct SM2LArgs;
 struct SliceArgs {
     int S;                                  // slices per operand (6 or 7)
     int nocc, nc, nrow, nleaf, leaf_store0, max_rt, nsplit, sm_count;
     long long nitems;                       // GEMM tiles (leaf, row tile, orbital tile, K split)
     const int* leaf_rowoff;
     int f32;                                // operands FP32 (the FP32 form) instead of FP64
+    const SM2LArgs* m2l;                    // M2L from slices too (nullptr: double-FP32)
     const void* W; const void* Mbox; const float* lscale;
     int* erow; int* fcol;                   // row and column exponents (written)
     const int* rtA; const long long* offA; const long long* item0;   // plan
@@ -373,6 +377,22 @@ cudaError_t l2p_slices(const SliceArgs& a, cudaStream_t s);
 cudaError_t full_slices(const SliceArgs& a, const void* Ct, void* Obox, cudaStream_t s);
 // M2L with L2L, fused per level, in double-FP32 arithmetic on the FP32 pipe
 // (the sliced FP64 form); O and Mcal are FP64 before and after the call
+// M2L of the FP64-accurate form from integer slices (kernels_f64s.cu): the
+// host plan per level and the device workspace (inside the slice panels)
+struct SM2LArgs {
+    int S, nq, ncs, nvar, ntile;
+    const int* lt0; const int* lnt;         // host, per level: first target (box id), targets
+    const int* lopl0; const int* lnopl;     // host, per level: first entry in oplist, distinct operators
+    const long long* lst0;                  // host, per level: first entry in stoff
+    const int* ltb;                         // host, per level: pair tiles per batch
+    const int* edge_bop;                    // device [nm2l]: the edge's operator within its level
+    const int* oplist;                      // device: distinct operators of each level
+    const long long* stoff;                 // device: first stage entry of each (target, chunk)
+    int2* stab; int* nk; int* ec; int* fq; int* gp;   // device workspace
+    uint8_t* panB; uint8_t* panA;
+    long long capA, capB;                   // panels that fit
+};
+
 struct FFArgs {
     int P, nc, L, D, first_box, nstore, leaf_store0, nops, sm_count;
     int m2m_done;                           // m2m_ff ran: the multipoles are (hi, lo) already
@@ -382,9 +402,12 @@ struct FFArgs {
     const int* child_ptr; const int* child_list; const int* m2m_op;
     const double* ops; float2* ops_ff;      // FP64 operators; their (hi, lo) copy (written)
     double* Ob; double* Mb;
+    const SM2LArgs* sm;                     // M2L from slices (nullptr: double-FP32)
+    int* err;                               // device error word of the slice GEMM
 };
 cudaError_t m2m_ff(const FFArgs& f, cudaStream_t s);   // (b) in double-FP32; splits the leaves first
 cudaError_t m2l_ff(const FFArgs& f, cudaStream_t s);
+cudaError_t ff_join(const FFArgs& f, cudaStream_t s);  // every stored box's multipoles back to FP64
 // step (a), first half, in double-FP32 arithmetic (the sliced FP64 form)
 struct HalfFFArgs {
     int nao, nocc, nrow, nc, nvals, lmc, nth;

@@ -81,6 +81,7 @@ _SIGS = {
     "occk_set_l2p_split": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_fp64_slices": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_slice_workspace": (ctypes.c_int, [_vp, ctypes.c_longlong]),
+    "occk_set_fp64_slice_m2l": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_fp32_slices": (ctypes.c_int, [_vp, ctypes.c_int]),
     "occk_set_pair_screen": (ctypes.c_int, [_vp, ctypes.c_double]),
     "occk_pair_screen_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
@@ -211,6 +212,10 @@ class Context:
         """FP32 steps (a) and (e) from 4 integer slices on the tensor core
         with exact sums (0: the FP32 SIMT GEMMs)."""
         self.check(lib().occk_set_fp32_slices(self._h, int(slices)), "occk_set_fp32_slices")
+
+    def set_fp64_slice_m2l(self, on: bool = True):
+        """M2L of the FP64-accurate sliced form from slices too (L >= 4)."""
+        self.check(lib().occk_set_fp64_slice_m2l(self._h, int(bool(on))), "occk_set_fp64_slice_m2l")
 
     def set_slice_workspace(self, nbytes: int = 0):
         """Largest slice-panel workspace of the sliced FP64 form (0: 32 GB)."""

@@ -15,7 +15,10 @@ inside the plain FP64 bar (1e-10); the tests hold it to 1e-11 (7 slices) and
 several full 128-row and 32-orbital tiles (the 60-carbon chain, 241 orbitals,
 at L = 2 and L = 6), the benchmark's protein-sized cluster, a long K range at
 L = 10 (121 components, 23 exact chunks per step (e) tile) and a small system
-whose step (e) tiles are split along K to fill the GPU.
+whose step (e) tiles are split along K to fill the GPU.  From L = 4 on, M2L
+(Eqs. fmmex, fmm2) runs from slices too, with the parent's L2L added in
+double-FP32; it is compared with the double-FP32 M2L, with fixed and
+per-edge ranks, and the batching of its pair tiles is bit-exact.
 """
 import os
 
@@ -174,10 +177,60 @@ def test_sliced_learned_selector(ctx):
     assert d < 1e-11 and abs(E7 - E0) <= 1e-11 * abs(E0)
 
 
+@pytest.mark.parametrize("name,L", [("chain60", 6), ("chain20", 10)])
+def test_sliced_m2l_matches_double_fp32(ctx, name, L):
+    """M2L from slices (the default from L = 4) against the double-FP32 M2L
+    of the same form: both are FP64-accurate, so K agrees far inside the
+    slices' own truncation."""
+    from paper_1708_05353_gb300 import occk
+    s = inputs.alkane(60, lmax=L) if name == "chain60" else SYSTEMS["chain20"]()
+    tree, C = _build(ctx, s, L)
+    K1, E1 = _run(ctx, tree, C, 7)
+    ctx.set_fp64_slice_m2l(False)
+    try:
+        K0, E0 = _run(ctx, tree, C, 7)
+    finally:
+        ctx.set_fp64_slice_m2l(True)
+    d = float((K1 - K0).abs().max() / K0.abs().max())
+    print(f"{name} L={L}: M2L from slices vs double-FP32 {d:.2e}, |dE| {abs(E1 - E0):.2e}")
+    assert d < 1e-11 and abs(E1 - E0) <= 1e-12 * abs(E0)
+    with pytest.raises(occk.OcckError):
+        ctx.check(occk.lib().occk_set_fp64_slice_m2l(ctx._h, 2), "occk_set_fp64_slice_m2l")
+
+
+def test_sliced_m2l_per_edge_ranks_match_double_fp32(ctx):
+    """Per-edge ranks at L = 4: the M2L from slices uses each edge's
+    operator restricted to its rank, like the double-FP32 M2L."""
+    from oracle import tree as otree
+    from paper_1708_05353_gb300 import occk
+    s = inputs.small_sp(natom=6, nocc=4, spacing=3.0, depth=3)
+    L = 4
+    tr = otree.build_tree(s.basis, 3, 8.0)
+    ranks = np.random.default_rng(11).integers(0, L + 1, size=len(tr["m2l_tgt"]))
+    tree = occk.Tree(ctx, s.basis, depth=3)
+    tree.pair_multipoles(L)
+    tree.set_edge_lmax(ranks)
+    C = torch.tensor(s.C, dtype=torch.float64, device="cuda:0")
+    out = {}
+    ctx.set_fp64_slices(7)
+    try:
+        for on in (True, False):
+            ctx.set_fp64_slice_m2l(on)
+            K, E = occk.farfield_K(ctx, tree, C, prec="fp64", lmax_policy=1, want_energy_host=True)
+            out[on] = (K.clone(), E)
+    finally:
+        ctx.set_fp64_slice_m2l(True)
+        ctx.set_fp64_slices(0)
+    d = float((out[True][0] - out[False][0]).abs().max() / out[False][0].abs().max())
+    print(f"per-edge ranks: M2L from slices vs double-FP32 {d:.2e}")
+    assert d < 1e-11 and abs(out[True][1] - out[False][1]) <= 1e-12 * abs(out[False][1])
+
+
 def test_sliced_leaf_batches_are_bit_identical(ctx):
     """With a small slice workspace the leaves run in many batches (panels
-    built and multiplied batch by batch); every output tile is computed the
-    same way, so K and E are bit for bit those of one batch."""
+    built and multiplied batch by batch), and so do the M2L's pair tiles;
+    every output tile is computed the same way, so K and E are bit for bit
+    those of one batch."""
     from paper_1708_05353_gb300 import occk
     s = SYSTEMS["chain60"]()
     tree, C = _build(ctx, s, 6)
