@@ -949,7 +949,10 @@ k_m2l_panel_B(const double* __restrict__ ops, const int* __restrict__ oplist, in
 // Stage list of every (target, output chunk) of the level: thread per pair
 // (local target, chunk); entry k = (A panel of the source and K stage, B panel
 // of the operator variant, chunk and K stage).  Chunks beyond an edge's rank
-// take nothing from it.
+// take nothing from it.  Where the chunk and the stage both lie inside the
+// edge's rank the restricted operator equals the full one there, so the full
+// operator's panel (variant L) serves: only the boundary stages read panels of
+// the rank's own variant, and most stages share the full operators' panels.
 __global__ void k_m2l_stages(const int* __restrict__ m2l_ptr, const int* __restrict__ m2l_src,
                              const int* __restrict__ edge_bop, const int* __restrict__ lmax_e, int t0, int nt, int L,
                              int nq, int ncs, int nvar, int sb0, const long long* __restrict__ stoff,
@@ -963,8 +966,12 @@ __global__ void k_m2l_stages(const int* __restrict__ m2l_ptr, const int* __restr
         const int Le = lmax_e ? lmax_e[e] : L, nce = (Le + 1) * (Le + 1);
         if (qc * kSN >= nce) continue;
         const int ncse = min(ncs, (nce + kSK - 1) / kSK);
-        const int a0 = (m2l_src[e] - sb0) * ncs, b0 = ((edge_bop[e] * nvar + (nvar > 1 ? Le : 0)) * nq + qc) * ncs;
-        for (int cs = 0; cs < ncse; ++cs) o[k++] = make_int2(a0 + cs, b0 + cs);
+        const int a0 = (m2l_src[e] - sb0) * ncs;
+        const int bv = ((edge_bop[e] * nvar + (nvar > 1 ? Le : 0)) * nq + qc) * ncs;
+        const int bf = ((edge_bop[e] * nvar + (nvar > 1 ? L : 0)) * nq + qc) * ncs;
+        const bool qin = (qc + 1) * kSN <= nce;
+        for (int cs = 0; cs < ncse; ++cs)
+            o[k++] = make_int2(a0 + cs, (qin && (cs + 1) * kSK <= nce ? bf : bv) + cs);
     }
     nk[x] = k;
 }
