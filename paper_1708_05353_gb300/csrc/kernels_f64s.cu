@@ -46,6 +46,11 @@
 // alternate, so the drain of one chunk overlaps the MMAs of the next) and
 // write the tile.  Every wait is bounded; on a timeout the CTA raises the
 // error word, waits (bounded) for its copies in flight, frees TMEM and returns.
+//
+// From 25 components on, M2L runs on the same engine with its K gathered stage
+// by stage from the interaction list (rows = occupied pairs, columns = output
+// components, K = (edge, input component)); the scalings there are per level
+// (see the M2L section below), and the parent's L2L is added in double-FP32.
 #include <algorithm>
 #include <cstdio>
 
