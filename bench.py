@@ -786,16 +786,19 @@ def main(argv=None):
                     "c_m2l": "k_translate(M2L+L2L)" if fused_cd else "k_translate(M2L)",
                     "d_l2l": "k_translate(L2L)", "e_l2p": "k_l2p_r32" if args.prec == "fp64" else "k_l2p",
                     "reduce": "k_reduce_K"}
+    sliced_m2l = bool(args.fp64_slices) and args.prec == "fp64" and (L + 1) ** 2 >= 25
     if args.fp64_slices and args.prec == "fp64":
         kernel_names.update({"a_half": "k_half_ff", "a_full": "k_s_gemm_a", "b_m2m": "k_translate_ff(M2M)",
-                             "c_m2l": "k_translate_ff(M2L+L2L)", "e_l2p": "k_s_gemm_e"})
+                             "c_m2l": ("k_s_gemm_m2l(M2L)+k_translate_ff(L2L)" if sliced_m2l
+                                       else "k_translate_ff(M2L+L2L)"),
+                             "e_l2p": "k_s_gemm_e"})
     achieved = fl[dom] / (stage_ms[dom] * 1e-3)
     bound = "alu"
     peak_source = (f"measured: independent-accumulator {peak_prec.upper()} FMA probe "
                    f"(occk_probe_fma_peak) on this GPU in this run, {probe / 1e12:.3f} TFLOP/s; nominal "
                    f"{sm_count} SMs at the median {sm_mhz:.0f} MHz: {nominal / 1e12:.3f} TFLOP/s")
     if args.fp64_slices and args.prec == "fp64":
-        if dom in ("a_full", "e_l2p"):
+        if dom in ("a_full", "e_l2p") or (dom == "c_m2l" and sliced_m2l):
             # slice GEMM: S (S + 1) / 2 FP16 products per FP64 product, against
             # the dense 16-bit tensor rate measured with cuBLAS on this machine
             npr = args.fp64_slices * (args.fp64_slices + 1) // 2

@@ -1010,6 +1010,68 @@ k_m2l_panel_A(const float2* __restrict__ O, int b0s, int nb, int nc, size_t P, i
     }
 }
 
+// 2^E as an FP32 number (0 below the normal range)
+__device__ __forceinline__ float s_pow2f(int E) {
+    return E < -126 ? 0.f : __int_as_float((min(E, 127) + 127) << 23);
+}
+
+// x += a exactly in double-FP32: TwoSum(h, a), the error into l
+__device__ __forceinline__ void s_ff_add(float& h, float& l, float a) {
+    const float sum = __fadd_rn(h, a);
+    const float bb = __fsub_rn(sum, h);
+    l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bb)), __fsub_rn(a, bb)));
+    h = sum;
+}
+
+// x 2^E for any E down to -252 (two exact steps, one final rounding into the
+// subnormal range); 0 below
+__device__ __forceinline__ float s_ldexpf(float x, int E) {
+    if (E >= -126) return x * s_pow2f(E);
+    if (E >= -252) return (x * s_pow2f(E + 126)) * s_pow2f(-126);
+    return 0.f;
+}
+
+// an unsigned integer below 2^23 as an exact FP32 number (magic-number trick)
+__device__ __forceinline__ float s_u2f(long long u) { return __int_as_float(0x4B000000 | (int)u) - 8388608.f; }
+
+// The exact group sums of one column as (hi, lo) FP32 numbers times 2^k,
+// without FP64 arithmetic.  X 2^(12+7(S-1)) = vh 2^SH + vl (SH = 7(S-1) - 14,
+// vh and vl the 64-bit integers of s_combine) is first formed exactly as
+// M 2^SH + R (|M| < 2^47, 0 <= R < 2^SH) and its magnitude cut into
+// non-negative chunks of at most 21 bits, which convert exactly; summed
+// smallest first with TwoSum (no cancellation, all of one sign) they give
+// hi + lo within about 2^-47 of |X|, and the scaling by 2^(k - 12 - 7(S-1))
+// comes last.
+template <int S>
+__device__ __forceinline__ float2 s_combine_ff(const int (&acc)[S][kSCols], int c, int k) {
+    constexpr int SH = 7 * (S - 1) - 14;
+    long long vh = 0, vl = 0;
+#pragma unroll
+    for (int d = 0; d < S; ++d) {
+        if (d < 3) vh += (long long)acc[d][c] << (7 * (2 - d));
+        else vl += (long long)acc[d][c] << (7 * (S - 1 - d));
+    }
+    long long M = vh + (vl >> SH), R = vl & ((1LL << SH) - 1);
+    const bool neg = M < 0;
+    if (neg) {
+        M = -M;
+        if (R) {
+            M -= 1;
+            R = (1LL << SH) - R;
+        }
+    }
+    float h = s_u2f(R & 0x3FFF), l = 0.f;
+    s_ff_add(h, l, s_u2f(R >> 14) * s_pow2f(14));
+    s_ff_add(h, l, s_u2f(M & 0x1FFFFF) * s_pow2f(SH));
+    s_ff_add(h, l, s_u2f((M >> 21) & 0x1FFFFF) * s_pow2f(SH + 21));
+    s_ff_add(h, l, s_u2f(M >> 42) * s_pow2f(SH + 42));
+    const float hh = __fadd_rn(h, l);                    // renormalise (Fast2Sum)
+    const float ll = __fsub_rn(l, __fsub_rn(hh, h));
+    const int E = k - (12 + 7 * (S - 1));
+    const float x = s_ldexpf(hh, E), y = s_ldexpf(ll, E);
+    return neg ? make_float2(-x, -y) : make_float2(x, y);
+}
+
 struct SGemmM {
     const int2* stab; const long long* stoff; const int* nk;
     const uint8_t* panA; const uint8_t* panB;
@@ -1062,19 +1124,12 @@ k_s_gemm_m2l(SGemmM g) {
         const int t = g.t0 + x / g.nq, qc = x % g.nq;
         const size_t p = (size_t)(g.T0 + tl) * 128 + row;
         if (p >= g.P) return;
-        double v[kSCols];
-        s_combine<S>(acc, v);
         const int e = g.gp[p];
         float2* o = g.Mb + (size_t)(t - g.first_box) * g.nc * g.P + p;
 #pragma unroll
         for (int c = 0; c < kSCols; ++c) {
             const int q = qc * kSN + part * kSCols + c;
-            if (q < g.nc) {
-                const int f = g.fq[q] > -1000 ? g.fq[q] : 0;
-                const double y = v[c] * s_pow2(e + f);
-                const float h = __double2float_rn(y);
-                o[(size_t)q * g.P] = make_float2(h, __double2float_rn(y - (double)h));
-            }
+            if (q < g.nc) o[(size_t)q * g.P] = s_combine_ff<S>(acc, c, e + (g.fq[q] > -1000 ? g.fq[q] : 0));
         }
     };
     s_gemm_body<S>(g.nitems, src, out, g.err, at);
