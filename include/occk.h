@@ -466,8 +466,10 @@ occk_status occk_set_l2p_split(occk_ctx* ctx, int nsplit);
  * half transform W = O^{rj,X} (Eq. motrans, first line) and the M2M, M2L and
  * L2L passes (Eqs. fmm1, fmmex, fmm2, fmm3) run in double-FP32 arithmetic on
  * the FP32 pipe (each value hi + lo, each multiply-add an error-free FMA
- * product and TwoSum; M2M stays FP64 with the learned selector, whose features
- * read the FP64 multipoles).  The reductions and the energy stay FP64.  The result differs
+ * product and TwoSum; with the learned selector the multipoles are joined back
+ * to FP64 after M2M for its features); from L = 4 M2L itself runs from slices
+ * on the tensor core as well (occk_set_fp64_slice_m2l).  The reductions and
+ * the energy stay FP64.  The result differs
  * from the DFMA form by the slices' truncation, relative to the largest
  * entries of each row and column about 2^-49 per product for 7 slices and
  * 2^-42 for 6 (measured on K: about 1.6e-12 and 1.3e-10 of max|K|; E within
