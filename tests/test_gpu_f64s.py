@@ -151,8 +151,9 @@ def test_sliced_per_edge_ranks(ctx):
 
 def test_sliced_learned_selector(ctx):
     """The learned selector (lmax_policy 2) reads the FP64 multipoles of every
-    box, so the sliced form keeps the FP64 M2M there; with the same network the
-    chosen ranks and K follow the DFMA form."""
+    box: the sliced form joins its double-FP32 M2M's multipoles back to FP64
+    for it, and at L = 6 runs the M2L from slices with the chosen ranks; with
+    the same network the chosen ranks are the DFMA form's and K follows it."""
     from oracle import mlp
     from paper_1708_05353_gb300 import occk
     rng = np.random.default_rng(5)
